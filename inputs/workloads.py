@@ -1,0 +1,91 @@
+"""Named synthetic workloads.
+
+``bubble``  -- dry rising thermal: 10 x 10 x 10 km box, 8^3 elements, N = 4
+               (33^3 nodes), isentropic theta_0 = 300 K, +2 K cosine bubble of
+               radius 2 km centred at (5, 5, 2) km, no-flux walls on all six
+               faces, no Coriolis, no heating, dt = 0.02 s.
+``tc``      -- tropical-cyclone-shaped box: 1024 x 1024 x 20 km, 128 x 128 x 16
+               elements, N = 4, doubly periodic laterally with no-flux bottom
+               and top (512 x 512 x 65 nodes), stable sounding N_BV = 0.01 1/s,
+               f = 5e-5 1/s, modified-Rankine vortex (15 m/s at 50 km) and the
+               ring-plus-32-cells heating (seed 2504), dt = 0.1 s.
+               ``scale`` shrinks the element counts (and the box with them, so
+               the spacing stays that of the full case).
+
+Each workload is a dict: mesh parameters (nel, N, lo, hi, periodic),
+physics (g, R, cp, cv, p_a, f), dt, the state q [5, Np] (rho', rho u, rho v,
+rho w, Theta'), the reference state on node levels (rho0 [n_z],
+Theta0 [n_z]) and the heating S_theta [Np] in K/s (or None).
+"""
+
+import numpy as np
+
+from . import atmosphere as atm
+from . import grid
+
+PHYS = dict(g=9.81, R=287.0, cp=1004.5, cv=717.5, p_a=1.0e5)
+
+
+def _levels(ax_z):
+    return np.asarray(ax_z)
+
+
+def bubble(nel=(8, 8, 8), N=4, state="initial", seed=1):
+    lo, hi = (0.0, 0.0, 0.0), (10.0e3, 10.0e3, 10.0e3)
+    periodic = (False, False, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.isentropic_sounding(ax[2])
+    n_xy = ax[0].size * ax[1].size
+    if state == "initial":
+        q = atm.bubble_state(X, Y, Z, ax[2], rho0, Th0, n_xy)
+    elif state == "random":
+        q = atm.smooth_random_state(X, Y, Z, lo, hi, periodic, seed)
+    else:
+        raise ValueError(state)
+    return dict(name="bubble", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=0.0), dt=0.02, q=q, rho0=rho0, Theta0=Th0, S_theta=None)
+
+
+def tc(nel=(128, 128, 16), N=4, state="initial", seed=1, heating_seed=2504):
+    hx = 1024.0e3 / 128 * nel[0]
+    hy = 1024.0e3 / 128 * nel[1]
+    hz = 20.0e3 / 16 * nel[2]
+    lo, hi = (-hx / 2, -hy / 2, 0.0), (hx / 2, hy / 2, hz)
+    periodic = (True, True, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.stable_sounding(ax[2], nbv=0.01)
+    n_xy = ax[0].size * ax[1].size
+    centre = (0.0, 0.0)
+    if state == "initial":
+        q = atm.vortex_state(X, Y, Z, rho0, n_xy, centre)
+    elif state == "random":
+        q = atm.smooth_random_state(X, Y, Z, lo, hi, periodic, seed)
+        q += atm.vortex_state(X, Y, Z, rho0, n_xy, centre)
+    else:
+        raise ValueError(state)
+    S = atm.heating(X, Y, Z, centre, seed=heating_seed)
+    return dict(name="tc", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=5.0e-5), dt=0.1, q=q, rho0=rho0, Theta0=Th0, S_theta=S)
+
+
+def box(nel, N, lo, hi, periodic, f=1.0e-4, seed=7, heating_amp=1.0e-3, sounding="stable"):
+    """Generic box with a seeded smooth random state (for parity sweeps over
+    orders, sizes and boundary types)."""
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    if sounding == "stable":
+        rho0, Th0 = atm.stable_sounding(ax[2] - lo[2], nbv=0.01)
+    else:
+        rho0, Th0 = atm.isentropic_sounding(ax[2] - lo[2])
+    q = atm.smooth_random_state(X, Y, Z, lo, hi, periodic, seed)
+    S = heating_amp * atm.smooth_random_state(X, Y, Z, lo, hi, (True, True, True), seed + 1000,
+                                              amps=(1.0, 0, 0, 0, 0))[0]
+    return dict(name="box", nel=tuple(nel), N=N, lo=tuple(lo), hi=tuple(hi),
+                periodic=tuple(periodic), phys=dict(PHYS, f=f), dt=0.02, q=q, rho0=rho0,
+                Theta0=Th0, S_theta=S)
+
+
+def dof_counts(nel, N, periodic):
+    """(unique-node DOF, element-local DOF): 5 variables times the unique
+    global nodes, and the paper's convention N_e (N+1)^3 x 5 (Sec. 5.2)."""
+    n = [N * nel[d] + (0 if periodic[d] else 1) for d in range(3)]
+    return 5 * n[0] * n[1] * n[2], 5 * nel[0] * nel[1] * nel[2] * (N + 1) ** 3

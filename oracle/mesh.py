@@ -1,0 +1,143 @@
+"""Hexahedral CG mesh of a box: elements, the local-to-global map and metrics.
+
+Sec. 2.2: the domain is split into N_e disjoint hexahedra; inside each element
+the state is expanded in (N+1)^3 tensor-product LGL nodes (Eqs. 4-5), the
+reference coordinates (xi, eta, zeta) in E = [-1, 1]^3 map to physical x via
+metric terms, and neighbouring elements share the nodes of their common faces,
+edges and corners (the CG space of Eq. 6).  ``intma`` is the paper's
+local-to-global node map (Alg. 1, Alg. 3).
+
+Conventions (they are the library's data layout, so both sides use them):
+
+* element e = ex + nel_x (ey + nel_y ez);
+* local node (a, b, c) in [0, N]^3 is stored at [e, c, b, a] (xi fastest);
+* global nodes per direction: n_d = N nel_d, or N nel_d + 1 when direction d
+  is not periodic; global node I = gx + n_x (gy + n_y gz) with
+  g_d = (N e_d + a_d) mod n_d;
+* the physical point of a node is the affine image A @ (box point) of the
+  box point lo + (e_d + (xi_a + 1) / 2) (hi - lo) / nel_d; A = identity is
+  the axis-aligned box.
+
+Metric terms are computed per node from the node coordinates with the
+derivative matrix, the general isoparametric recipe (Eq. 5, Eq. 8), even
+though every mesh here is affine.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lgl
+
+
+def apply_D(D, f, axis):
+    """Reference derivative along one local direction of element arrays laid
+    out [..., c, b, a] (Alg. 2: q_xi(i,j,k) = sum_l dphi/dxi(l,i) q(l,j,k)).
+    axis 0 -> xi (last array axis), 1 -> eta, 2 -> zeta."""
+    ax = f.ndim - 1 - axis
+    g = np.moveaxis(f, ax, -1)
+    g = g @ D.T  # out[..., i] = sum_l D[i, l] g[..., l]
+    return np.moveaxis(g, -1, ax)
+
+
+@dataclass
+class Mesh:
+    N: int
+    nel: tuple
+    periodic: tuple
+    lo: np.ndarray
+    hi: np.ndarray
+    A: np.ndarray
+    n: tuple                      # global nodes per direction (nx, ny, nz)
+    Np: int
+    xi: np.ndarray                # LGL points
+    w: np.ndarray                 # LGL weights
+    D: np.ndarray                 # derivative matrix
+    intma: np.ndarray             # [Ne, N+1, N+1, N+1] -> global node
+    xyz: np.ndarray               # [3, Ne, c, b, a] physical node coordinates
+    gidx: tuple                   # (gx, gy, gz) integer indices of global nodes
+    dxi_dx: np.ndarray = field(repr=False, default=None)  # [3 (xi_j), 3 (x_i), Ne, c, b, a]
+    detJ: np.ndarray = field(repr=False, default=None)    # [Ne, c, b, a]
+    w3: np.ndarray = field(repr=False, default=None)      # [c, b, a] tensor weights
+
+    @property
+    def Ne(self):
+        return int(np.prod(self.nel))
+
+    def wall_nodes(self, d):
+        """Boolean mask over global nodes lying on a wall normal to direction
+        d (empty when d is periodic)."""
+        if self.periodic[d]:
+            return np.zeros(self.Np, dtype=bool)
+        g = self.gidx[d]
+        return (g == 0) | (g == self.n[d] - 1)
+
+    def elements_containing(self, nodes):
+        """Sorted element ids whose local nodes include any of the global
+        node ids in ``nodes``."""
+        hit = np.isin(self.intma.reshape(self.Ne, -1), np.asarray(nodes)).any(axis=1)
+        return np.nonzero(hit)[0]
+
+
+def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+               periodic=(False, False, False), A=None):
+    """Build the CG mesh of a box of nel = (nel_x, nel_y, nel_z) order-N
+    hexahedra (Sec. 2.2) and its per-node metric terms."""
+    nel = tuple(int(v) for v in nel)
+    periodic = tuple(bool(p) for p in periodic)
+    if min(nel) < 1 or N < 1:
+        raise ValueError("need nel >= 1 and N >= 1")
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    A = np.eye(3) if A is None else np.asarray(A, dtype=np.float64)
+    n = tuple(N * nel[d] + (0 if periodic[d] else 1) for d in range(3))
+    Np = n[0] * n[1] * n[2]
+
+    xi = lgl.lgl_points(N)
+    w = lgl.lgl_weights(N, xi)
+    D = lgl.derivative_matrix(xi)
+
+    ex, ey, ez = np.meshgrid(np.arange(nel[0]), np.arange(nel[1]), np.arange(nel[2]),
+                             indexing="ij")
+    # element order e = ex + nel_x (ey + nel_y ez)
+    ex = ex.transpose(2, 1, 0).reshape(-1)
+    ey = ey.transpose(2, 1, 0).reshape(-1)
+    ez = ez.transpose(2, 1, 0).reshape(-1)
+    a = np.arange(N + 1)
+    # broadcast to [Ne, c, b, a]
+    gx = (N * ex[:, None, None, None] + a[None, None, None, :]) % n[0]
+    gy = (N * ey[:, None, None, None] + a[None, None, :, None]) % n[1]
+    gz = (N * ez[:, None, None, None] + a[None, :, None, None]) % n[2]
+    intma = gx + n[0] * (gy + n[1] * gz)
+
+    h = (hi - lo) / np.asarray(nel, dtype=np.float64)
+    bx = lo[0] + (ex[:, None, None, None] + (xi[None, None, None, :] + 1.0) / 2.0) * h[0]
+    by = lo[1] + (ey[:, None, None, None] + (xi[None, None, :, None] + 1.0) / 2.0) * h[1]
+    bz = lo[2] + (ez[:, None, None, None] + (xi[None, :, None, None] + 1.0) / 2.0) * h[2]
+    shape = (len(ex), N + 1, N + 1, N + 1)
+    box = np.stack([np.broadcast_to(bx, shape), np.broadcast_to(by, shape),
+                    np.broadcast_to(bz, shape)])
+    xyz = np.einsum("ij,j...->i...", A, box)
+
+    I = np.arange(Np)
+    gidx = (I % n[0], (I // n[0]) % n[1], I // (n[0] * n[1]))
+
+    m = Mesh(N=N, nel=nel, periodic=periodic, lo=lo, hi=hi, A=A, n=n, Np=Np,
+             xi=xi, w=w, D=D, intma=intma, xyz=xyz, gidx=gidx)
+    _metrics(m)
+    return m
+
+
+def _metrics(m):
+    """Per-node Jacobian matrix dx_i/dxi_j from the node coordinates with D,
+    its determinant J (Eq. 8) and inverse dxi_j/dx_i (Eq. 5)."""
+    jac = np.empty((3, 3) + m.xyz.shape[1:])  # [x_i, xi_j, ...]
+    for i in range(3):
+        for j in range(3):
+            jac[i, j] = apply_D(m.D, m.xyz[i], j)
+    jm = np.moveaxis(jac, (0, 1), (-2, -1))    # [..., i, j]
+    m.detJ = np.linalg.det(jm)
+    inv = np.linalg.inv(jm)                    # [..., j, i] = dxi_j/dx_i
+    m.dxi_dx = np.moveaxis(inv, (-2, -1), (0, 1))
+    w = m.w
+    m.w3 = w[:, None, None] * w[None, :, None] * w[None, None, :]
