@@ -1,0 +1,429 @@
+"""Throughput of the explicit CG Euler path on GB300: RK-stage GDOF/s.
+
+Default workload (the cyclone box): 1024 x 1024 x 20 km, 128 x 128 x 16
+order-4 elements, doubly periodic sides, no-flux bottom and top
+(512 x 512 x 65 = 17,039,360 nodes), stable sounding, f-plane, vortex and
+ring-plus-cells heating, FP64, dt = 0.1 s.  One bench step is one SSP-RK3
+step = three passes of the whole hot path (each pass: primitives, fluxes,
+sum-factorised derivatives, DSS, inverse mass, sources, walls, stage
+update), so
+
+    value = 5 * Np * 3 * K * world / max-over-ranks(time of K steps) / 1e9
+
+in unique-node DOF (the paper's element-local convention, N_e (N+1)^3 x 5,
+is reported beside it).  Inputs are resident in HBM before the timed region;
+each state buffer (682 MB) is larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xg|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the only reference there is)
+on a bounded sample of the same workload.  Under torchrun every rank runs an
+independent replica (the path needs no exchange on one box) and rank 0
+prints one JSON line.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")  # the CPU oracle is timed on one core
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK-stage GDOF/s vs plain FP64 at stated L2 error; % of HBM roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", "xg_kernels.cuh")
+KERNELS = ("k_line_x", "k_line_y", "k_line_z")
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
+# 2 flop x 2.07 GHz (maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def flops_per_node(kernel, N):
+    """Algorithmic FP64 flops per unique node of each kernel (FMA = 2),
+    counted from the arithmetic each performs for N-th order elements:
+    a 1-D segment contraction costs (N+1) rows x (1 mul + N fma) =
+    (N+1)(2N+1) flops per flux component and covers N unique nodes, and a
+    face node adds one more addition per component."""
+    contraction = 5 * (N + 1) * (2 * N + 1) / N + 5.0 / N
+    if kernel == "k_line_x":
+        # rho, 1/rho, u v w, Theta'/Theta0, 12-term series (11 fma + 2 mul),
+        # Theta, 1 fma + 3 mul of the x-fluxes
+        return 1 + 1 + 3 + 1 + 24 + 1 + 5 + contraction
+    if kernel == "k_line_y":
+        return 5 + contraction + 5            # y-fluxes, contraction, T +=
+    if kernel == "k_line_z":
+        # z-fluxes, contraction, T + z part, sources (3 fma + rho + fma),
+        # stage update (2-3 fma/mul per variable, average over the stages)
+        return 5 + contraction + 5 + 6 + 5 * (2 + 5) / 3
+    raise KeyError(kernel)
+
+
+def traffic_per_launch(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(TRAFFIC_FILE):
+        p = line.split()
+        if len(p) >= 2 and not line.startswith("#"):
+            vals[p[0]] = p[1]
+    if vals.get("source_sha") != sha:
+        return None
+    v = vals.get(kernel)
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms, in a thread."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for k, name in enumerate(names):
+                if r[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(self.rows[0][1]),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(name, nel=None):
+    from inputs import workloads as W
+    if name == "tc":
+        return W.tc() if nel is None else W.tc(nel=tuple(nel))
+    if name == "bubble":
+        return W.bubble()
+    raise SystemExit("unknown workload " + name)
+
+
+def describe(wl):
+    from inputs import workloads as W
+    dof_u, dof_p = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])
+    per = "".join("p" if p else "w" for p in wl["periodic"])
+    return dict(workload="%s %dx%dx%d N=%d FP64 (%s)" % (wl["name"], *wl["nel"], wl["N"], per),
+                nel=list(wl["nel"]), N=wl["N"], nodes=dof_u // 5, dof_unique=dof_u,
+                dof_paper=dof_p, dt=wl["dt"], periodic=list(wl["periodic"]),
+                l2="inputs larger than L2 (each [5][Np] FP64 buffer 682 MB > 129 MB L2)",
+                parallelism="replicas")
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def cpu_sample_workload(name):
+    """A bounded sample of the workload for the oracle: the cyclone box with
+    16 x 16 x 16 elements (same spacing and order, 266,240 nodes); the
+    bubble case is small enough to run whole."""
+    from inputs import workloads as W
+    if name == "tc":
+        return W.tc(nel=(16, 16, 16))
+    return W.bubble()
+
+
+def time_oracle(wl, min_seconds=10.0, max_steps=50):
+    """SSP-RK3 steps of the oracle until min_seconds have passed; returns
+    (unique-DOF GDOF/s per stage, steps, seconds, final state)."""
+    from oracle import euler as E, mesh as M, ssprk3
+    from inputs import workloads as W
+    m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"])
+    phys = E.Physics(**wl["phys"])
+    base = E.Base(wl["rho0"], wl["Theta0"])
+    L = lambda s: E.rhs(m, s, base, wl["S_theta"], phys)
+    q = wl["q"]
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        q = ssprk3.ssprk3_step(L, q, wl["dt"])
+        steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    dof_u, _ = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])
+    return dof_u * 3 * steps / dt / 1e9, steps, dt, q
+
+
+def oracle_error_of_gpu(wl, xg, torch, dev):
+    """Largest relative L2 over variables between one GPU right-hand side and
+    the oracle's on the CPU sample."""
+    from oracle import euler as E, mesh as M
+    m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"])
+    ref = E.rhs(m, wl["q"], E.Base(wl["rho0"], wl["Theta0"]), wl["S_theta"],
+                E.Physics(**wl["phys"]))
+    ctx = make_ctx(xg, torch, wl, dev)
+    try:
+        out = torch.empty((5, xg.xg_mesh_np(ctx)), dtype=torch.float64, device=dev)
+        xg.xg_rhs(ctx, out)
+        got = out.cpu().numpy()
+    finally:
+        xg.xg_destroy(ctx)
+    err = [np.linalg.norm(got[v] - ref[v]) / max(np.linalg.norm(ref[v]), 1e-300) for v in range(5)]
+    return float(max(err))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def make_ctx(xg, torch, wl, dev):
+    ph = wl["phys"]
+    ctx = xg.xg_mesh_create(xg.mesh_desc(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"],
+                                         f=ph["f"], g=ph["g"], R=ph["R"], cp=ph["cp"],
+                                         cv=ph["cv"], p_a=ph["p_a"]))
+    q = torch.from_numpy(wl["q"]).to(dev)
+    xg.xg_set_state(ctx, q, torch.from_numpy(wl["rho0"]).to(dev),
+                    torch.from_numpy(wl["Theta0"]).to(dev))
+    if wl["S_theta"] is not None:
+        xg.xg_set_forcing(ctx, torch.from_numpy(wl["S_theta"]).to(dev))
+    torch.cuda.synchronize()
+    return ctx
+
+
+def run_xg(args, world, rank, local):
+    import torch
+    from paper_2504_08157_gb300 import build, xg
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    wl = workload(args.workload, args.nel)
+    cfg = describe(wl)
+    ctx = make_ctx(xg, torch, wl, dev)
+    stream = torch.cuda.current_stream(dev)
+    dt = wl["dt"]
+    K, Wm = args.steps, args.warmup
+
+    xg.xg_step(ctx, dt, Wm, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    xg.xg_profile(ctx, 1)
+    xg.xg_kernel_times(ctx, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xg.xg_step(ctx, dt, K, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    xg.xg_profile(ctx, 0)
+    ms = e0.elapsed_time(e1)
+    kms, klaunch = xg.xg_kernel_times(ctx, reset=True)
+    ms_max = reduce_max(ms, world)
+    dof_u, dof_p = cfg["dof_unique"], cfg["dof_paper"]
+    value = dof_u * 3 * K * world / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel (largest share of device time)
+    k = int(np.argmax(kms))
+    name = KERNELS[k]
+    avg_ms = kms[k] / max(klaunch[k], 1)
+    flops = flops_per_node(name, wl["N"]) * cfg["nodes"]
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = traffic_per_launch(name)
+    roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
+            "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+            "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "share": round(kms[k] / max(sum(kms), 1e-30), 4),
+            "kernel_ms_per_launch": {KERNELS[i]: round(kms[i] / max(klaunch[i], 1), 4)
+                                     for i in range(3)}}
+    # the same stage time against the HBM roofline (algorithmic bytes)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    stage_bytes = cfg["nodes"] * (88 + 128 + 128) / 3.0
+    stage_s = ms_max / 1e3 / (3 * K)
+    hbm_frac = stage_bytes / stage_s / 1e9 / hbm
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        np_ = xg.xg_mesh_np(ctx)
+        h_in = torch.from_numpy(wl["q"]).pin_memory()
+        h_out = torch.empty((5, np_), dtype=torch.float64).pin_memory()
+        Ke = max(1, min(K, 10))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            xg.xg_set_state(ctx, h_in, stream=stream.cuda_stream)
+            xg.xg_step(ctx, dt, 1, stream=stream.cuda_stream)
+            xg.xg_get_state(ctx, h_out, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        te = reduce_max(time.perf_counter() - t0, world)
+        barrier(world)
+        nbytes = 5 * np_ * 8
+        e2e = {"value": round(dof_u * 3 * Ke * world / te / 1e9, 4), "unit": "GDOF/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": Ke}
+    xg.xg_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sw = cpu_sample_workload(args.workload)
+        gdof, steps, secs, _ = time_oracle(sw)
+        err = oracle_error_of_gpu(sw, xg, torch, dev)
+        cpu = {"value": round(gdof, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": "%s %dx%dx%d N=%d, %d SSP-RK3 steps in %.1f s (numpy, 1 thread)"
+                         % (sw["name"], *sw["nel"], sw["N"], steps, secs),
+               "gpu_rhs_rel_l2_vs_oracle": err}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
+               "steps": K, "warmup": Wm, "ms_per_step": round(ms_max / K, 4),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "xg",
+               "config": cfg,
+               "gdof_paper_convention": round(dof_p * 3 * K * world / (ms_max / 1e3) / 1e9, 4),
+               "hbm_roofline_frac": round(hbm_frac, 4),
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": int(sum(klaunch))}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank, local):
+    """The FP64 oracle on the host cores, one bounded sample per step."""
+    if rank != 0:
+        return
+    sw = cpu_sample_workload(args.workload)
+    wl_full = workload_desc_only(args.workload)
+    K, Wm = args.steps, args.warmup
+    per_step = []
+    for i in range(Wm + K):
+        gdof, steps, secs, _ = time_oracle(sw, min_seconds=0.0, max_steps=1)
+        if i >= Wm:
+            per_step.append(secs)
+    total = sum(per_step)
+    from inputs import workloads as W
+    dof_u, _ = W.dof_counts(sw["nel"], sw["N"], sw["periodic"])
+    value = dof_u * 3 * K / total / 1e9
+    sample = "%s %dx%dx%d N=%d, one SSP-RK3 step per bench step (numpy, 1 thread)" % (
+        sw["name"], *sw["nel"], sw["N"])
+    out = {"metric": METRIC, "value": round(value, 6), "unit": "GDOF/s", "n_gpus": world,
+           "steps": K, "warmup": Wm, "ms_per_step": round(1e3 * total / K, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference", "config": wl_full,
+           "cpu_baseline": {"value": round(value, 6), "unit": "GDOF/s", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def workload_desc_only(name):
+    from inputs import workloads as W
+    if name == "tc":
+        nel, N, per, dt = (128, 128, 16), 4, (True, True, False), 0.1
+        label = "tc"
+    else:
+        nel, N, per, dt = (8, 8, 8), 4, (False, False, False), 0.02
+        label = "bubble"
+    dof_u, dof_p = W.dof_counts(nel, N, per)
+    pstr = "".join("p" if p else "w" for p in per)
+    return dict(workload="%s %dx%dx%d N=%d FP64 (%s)" % (label, *nel, N, pstr), nel=list(nel),
+                N=N, nodes=dof_u // 5, dof_unique=dof_u, dof_paper=dof_p, dt=dt,
+                periodic=list(per), parallelism="replicas")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["xg", "reference"], default="xg")
+    ap.add_argument("--workload", choices=["tc", "bubble"], default="tc")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nel", type=int, nargs=3, default=None,
+                    help="element counts of a smaller cyclone box (same spacing), for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_xg(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * xg.h -- C ABI of the GB300 (sm_103a) explicit CG Euler path after
+ * Kang, Giraldo & Camp, "A GPU-accelerated simulation of rapid
+ * intensification of a tropical cyclone with observed heating"
+ * (arXiv 2504.08157).
+ *
+ * The library evaluates, on one GPU, the explicit right-hand side of the
+ * compressible Euler equations for perturbations about a hydrostatic
+ * reference state (Sec. 2.1, Eq. 1, with the equation of state Eq. 3),
+ * written for q = (rho', rho u, rho v, rho w, Theta'), Theta = rho theta,
+ * with f-plane Coriolis and a prescribed heating S_theta, on a hexahedral
+ * continuous-Galerkin mesh of tensor-product LGL nodes (Sec. 2.2, Eqs. 4-8);
+ * assembles it by direct stiffness summation (Eqs. 9-11, Alg. 3), applies
+ * the inverse diagonal mass matrix (Eq. 12) and no-flux walls, and advances
+ * the state with three-stage SSP Runge-Kutta stages fused into the same
+ * kernels.
+ *
+ * Mesh: an axis-aligned box [lo, hi] split into nel[0] x nel[1] x nel[2]
+ * equal hexahedra of order N = order.  Direction d has n_d = N nel_d global
+ * nodes when periodic and N nel_d + 1 when bounded by no-flux walls.
+ *
+ * Data layout (all arrays FP64, row-major, no padding):
+ *   state q      [5][Np]  structure of arrays; variable v = 0 rho' (kg m^-3),
+ *                         1..3 rho u, rho v, rho w (kg m^-2 s^-1),
+ *                         4 Theta' = (rho theta)' (K kg m^-3);
+ *                         node I = gx + n_x (gy + n_y gz), x fastest.
+ *   reference    rho0[n_z], rhotheta0[n_z]: rho_0 and Theta_0 = rho_0 theta_0
+ *                on the node levels gz = 0 .. n_z-1 (the reference state
+ *                depends on z only, Sec. 2.1); p_0 = p(Theta_0) by Eq. 3.
+ *   heating      S_theta[Np] in K s^-1 (a potential-temperature tendency;
+ *                the conservative source is rho S_theta).
+ *
+ * Pointers: every array argument is either host memory (where = XG_HOST) or
+ * device memory of the context's GPU (where = XG_DEVICE), e.g. a PyTorch
+ * tensor's data_ptr().  The library copies what it is given and never keeps
+ * a caller pointer.  `stream` is a cudaStream_t passed as void*; NULL is the
+ * legacy default stream.  Work is enqueued on that stream; a call returns
+ * before the GPU finishes except where stated.
+ *
+ * Errors: every call returns an xg_status and never throws.  XG_ERR_ARG and
+ * XG_ERR_UNSUPPORTED are detected on the host before any GPU work and leave
+ * the context unchanged.  XG_ERR_CUDA is sticky: the context refuses further
+ * work (only xg_destroy).  XG_ERR_NONFINITE (xg_step) leaves the context
+ * usable with whatever state the GPU computed.
+ *
+ * Threads: a context may be used by one host thread at a time.
+ */
+#ifndef XG_H
+#define XG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XG_OK = 0,
+  XG_ERR_ARG = 1,          /* invalid argument (NULL, out of range, wrong order of calls) */
+  XG_ERR_CUDA = 2,         /* a CUDA runtime call failed; sticky */
+  XG_ERR_OOM = 3,          /* device allocation failed */
+  XG_ERR_NONFINITE = 4,    /* a NaN or Inf appeared in the state */
+  XG_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  XG_ERR_UNSUPPORTED = 6   /* valid but not supported by this build */
+} xg_status;
+
+enum { XG_HOST = 0, XG_DEVICE = 1 };
+enum { XG_FP64 = 0, XG_FP32 = 1 };
+
+/* Problem statement (Sec. 2.1-2.2, Sec. 4.1):
+ *   nel[3]      elements per direction, >= 1
+ *   order       polynomial order N of the LGL basis, 1 <= N <= 8
+ *   lo, hi      box corners in metres, hi > lo
+ *   periodic    per direction: 1 periodic, 0 no-flux walls
+ *   precision   XG_FP64 (state and arithmetic in FP64)
+ *   f_coriolis  f-plane Coriolis parameter (s^-1)
+ *   g, R, cp, cv, p_a   gravity, dry-air gas constant, heat capacities and
+ *               reference surface pressure of Eq. 1 and Eq. 3 (SI units) */
+typedef struct {
+  int nel[3];
+  int order;
+  double lo[3];
+  double hi[3];
+  int periodic[3];
+  int precision;
+  double f_coriolis;
+  double g, R, cp, cv, p_a;
+} xg_mesh_desc;
+
+typedef struct xg_ctx xg_ctx;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* xg_status_str(xg_status s);
+
+/* Sec. 2.2: build the mesh on the current CUDA device and allocate every
+ * device buffer of the path (owned by the context).  On success *out is a
+ * new context; on failure *out is NULL.  Errors: XG_ERR_ARG (NULL, nel < 1,
+ * order outside [1, 8], hi <= lo, non-positive constants),
+ * XG_ERR_UNSUPPORTED (precision other than XG_FP64, or a line of more nodes
+ * than one CTA stages in shared memory), XG_ERR_OOM, XG_ERR_CUDA. */
+xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out);
+
+/* Number of global (unique) nodes Np = n_x n_y n_z. */
+xg_status xg_mesh_np(const xg_ctx* ctx, long long* np);
+
+/* Global nodes per direction n[0..2]. */
+xg_status xg_mesh_dims(const xg_ctx* ctx, int n[3]);
+
+/* Copy the state q [5][Np] into the context.  rho0 and rhotheta0 ([n_z]
+ * each, both or neither) replace the reference state; NULL keeps the
+ * previous one (the first call must give them).  The reference arrays are
+ * read synchronously (they are small); q is copied on `stream`.
+ * Errors: XG_ERR_ARG (NULL q, only one of rho0/rhotheta0, no reference yet,
+ * a non-positive reference value), XG_ERR_CUDA. */
+xg_status xg_set_state(xg_ctx* ctx, const double* q, const double* rho0,
+                       const double* rhotheta0, int where, void* stream);
+
+/* Copy the heating S_theta [Np] (K s^-1) into the context, on `stream`;
+ * NULL sets it to zero.  Errors: XG_ERR_ARG, XG_ERR_CUDA. */
+xg_status xg_set_forcing(xg_ctx* ctx, const double* S_theta, int where, void* stream);
+
+/* Eq. 12 for the current state: dqdt [5][Np] = M^-1 DSS(w J S(q)) with the
+ * wall condition (the wall-normal momentum tendency is zero at wall nodes).
+ * Does not modify the state.  With XG_HOST the call waits for the copy.
+ * Errors: XG_ERR_ARG (NULL, no state yet), XG_ERR_CUDA. */
+xg_status xg_rhs(xg_ctx* ctx, double* dqdt, int where, void* stream);
+
+/* nsteps SSP-RK3 steps of size dt (each step three fused stage passes:
+ * q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
+ * q <- 1/3 q + 2/3 (q2 + dt L(q2))).  Waits for the GPU once at the end to
+ * read the non-finite flag.  Errors: XG_ERR_ARG (dt not finite, nsteps < 0,
+ * no state yet), XG_ERR_NONFINITE, XG_ERR_CUDA. */
+xg_status xg_step(xg_ctx* ctx, double dt, int nsteps, void* stream);
+
+/* Copy the current state to q [5][Np], on `stream` (XG_HOST waits for it).
+ * Errors: XG_ERR_ARG (NULL, no state yet), XG_ERR_CUDA. */
+xg_status xg_get_state(xg_ctx* ctx, double* q, int where, void* stream);
+
+/* Kernel timing (Sec. 5.4 measures its kernels against a roofline; this is
+ * the hook for doing the same here).  enable = 1 brackets every kernel that
+ * xg_rhs and xg_step launch with CUDA events on the launching stream; the
+ * elapsed times are folded into per-kernel totals when those calls end
+ * (enabling profiling makes xg_rhs wait for the GPU).  enable = 0 stops
+ * recording.  Errors: XG_ERR_ARG, XG_ERR_CUDA. */
+xg_status xg_profile(xg_ctx* ctx, int enable);
+
+/* Per-kernel totals since the last reset: ms[k] total device milliseconds and
+ * launches[k] launch count of kernel k = 0 (x lines: primitives, x part),
+ * 1 (y lines), 2 (z lines: z part, sources, walls, stage store).  reset != 0
+ * clears the totals after reading.  Either output may be NULL.
+ * Errors: XG_ERR_ARG. */
+xg_status xg_kernel_times(xg_ctx* ctx, double ms[3], long long launches[3], int reset);
+
+/* Free every buffer of the context (synchronises the device first).  NULL
+ * is a no-op. */
+void xg_destroy(xg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XG_H */

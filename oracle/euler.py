@@ -163,7 +163,9 @@ def rhs(mesh, q, base, S_theta, phys):
 
 def rhs_at_nodes(mesh, q, base, S_theta, phys, nodes):
     """Eq. 12 at the given global nodes only: the same steps restricted to the
-    elements that contain them (used to check large meshes by sampling)."""
+    stored elements that contain them (used to check large meshes by
+    sampling; ``mesh`` may hold just the elements around the nodes, see
+    ``mesh.elements_around``)."""
     nodes = np.asarray(nodes)
     el = mesh.elements_containing(nodes)
     S = local_tendency(mesh, q, base, S_theta, phys, elements=el)

@@ -60,9 +60,11 @@ class Mesh:
     detJ: np.ndarray = field(repr=False, default=None)    # [Ne, c, b, a]
     w3: np.ndarray = field(repr=False, default=None)      # [c, b, a] tensor weights
 
+    elem_ids: np.ndarray = field(repr=False, default=None)  # global ids of the stored elements
+
     @property
     def Ne(self):
-        return int(np.prod(self.nel))
+        return int(self.intma.shape[0])
 
     def wall_nodes(self, d):
         """Boolean mask over global nodes lying on a wall normal to direction
@@ -73,16 +75,47 @@ class Mesh:
         return (g == 0) | (g == self.n[d] - 1)
 
     def elements_containing(self, nodes):
-        """Sorted element ids whose local nodes include any of the global
-        node ids in ``nodes``."""
+        """Sorted positions (rows of intma) of the stored elements whose
+        local nodes include any of the global node ids in ``nodes``."""
         hit = np.isin(self.intma.reshape(self.Ne, -1), np.asarray(nodes)).any(axis=1)
         return np.nonzero(hit)[0]
 
 
+def elements_around(nel, N, periodic, nodes):
+    """Global ids of every element that contains one of the global nodes:
+    along each direction a node g belongs to element g // N, and also to
+    element g // N - 1 when it sits on a face (g % N == 0); indices wrap in
+    periodic directions and stop at walls."""
+    n = [N * nel[d] + (0 if periodic[d] else 1) for d in range(3)]
+    nodes = np.asarray(nodes, dtype=np.int64)
+    g = [nodes % n[0], (nodes // n[0]) % n[1], nodes // (n[0] * n[1])]
+    out = set()
+    for k in range(nodes.size):
+        choices = []
+        for d in range(3):
+            gd = int(g[d][k])
+            c = []
+            for e in (gd // N, gd // N - 1 if gd % N == 0 else None):
+                if e is None:
+                    continue
+                if periodic[d]:
+                    c.append(e % nel[d])
+                elif 0 <= e < nel[d]:
+                    c.append(e)
+            choices.append(sorted(set(c)))
+        for ex in choices[0]:
+            for ey in choices[1]:
+                for ez in choices[2]:
+                    out.add(ex + nel[0] * (ey + nel[1] * ez))
+    return np.array(sorted(out), dtype=np.int64)
+
+
 def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-               periodic=(False, False, False), A=None):
+               periodic=(False, False, False), A=None, elements=None):
     """Build the CG mesh of a box of nel = (nel_x, nel_y, nel_z) order-N
-    hexahedra (Sec. 2.2) and its per-node metric terms."""
+    hexahedra (Sec. 2.2) and its per-node metric terms.  With ``elements``
+    (global element ids) only those elements are stored; the global node
+    numbering is that of the whole box."""
     nel = tuple(int(v) for v in nel)
     periodic = tuple(bool(p) for p in periodic)
     if min(nel) < 1 or N < 1:
@@ -97,12 +130,13 @@ def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
     w = lgl.lgl_weights(N, xi)
     D = lgl.derivative_matrix(xi)
 
-    ex, ey, ez = np.meshgrid(np.arange(nel[0]), np.arange(nel[1]), np.arange(nel[2]),
-                             indexing="ij")
     # element order e = ex + nel_x (ey + nel_y ez)
-    ex = ex.transpose(2, 1, 0).reshape(-1)
-    ey = ey.transpose(2, 1, 0).reshape(-1)
-    ez = ez.transpose(2, 1, 0).reshape(-1)
+    if elements is None:
+        elements = np.arange(nel[0] * nel[1] * nel[2], dtype=np.int64)
+    elements = np.asarray(elements, dtype=np.int64)
+    ex = elements % nel[0]
+    ey = (elements // nel[0]) % nel[1]
+    ez = elements // (nel[0] * nel[1])
     a = np.arange(N + 1)
     # broadcast to [Ne, c, b, a]
     gx = (N * ex[:, None, None, None] + a[None, None, None, :]) % n[0]
@@ -123,7 +157,7 @@ def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
     gidx = (I % n[0], (I // n[0]) % n[1], I // (n[0] * n[1]))
 
     m = Mesh(N=N, nel=nel, periodic=periodic, lo=lo, hi=hi, A=A, n=n, Np=Np,
-             xi=xi, w=w, D=D, intma=intma, xyz=xyz, gidx=gidx)
+             xi=xi, w=w, D=D, intma=intma, xyz=xyz, gidx=gidx, elem_ids=elements)
     _metrics(m)
     return m
 

@@ -1,0 +1,52 @@
+"""In-tree build of the CUDA library ``libxg.so`` (sm_103a only).
+
+One translation unit (the C ABI plus the line kernels for orders 1-8),
+compiled with nvcc for ``-gencode arch=compute_103a,code=sm_103a`` and linked
+as a shared library next to this file.  The CUDA runtime is linked
+statically so the library loads without the toolkit's library path.
+"""
+
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB = os.path.join(HERE, "libxg.so")
+SOURCES = [os.path.join(HERE, "csrc", "xg_api.cu")]
+DEPENDS = SOURCES + [os.path.join(HERE, "csrc", "xg_kernels.cuh"),
+                     os.path.join(ROOT, "include", "xg.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc_path():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: set NVCC or put the CUDA toolkit on PATH")
+
+
+def up_to_date():
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(p) <= t for p in DEPENDS)
+
+
+def build(force=False, verbose=False):
+    """Compile libxg.so if any source is newer than it; returns its path."""
+    if not force and up_to_date():
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc_path(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+           "-shared", "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

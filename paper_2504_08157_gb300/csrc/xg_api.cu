@@ -1,0 +1,506 @@
+// xg_api.cu -- C ABI of the explicit CG Euler path (see include/xg.h).
+//
+// Host side: argument checks, the LGL derivative matrix (Sec. 2.2, Eq. 5),
+// the reference-state table p_0 = p(Theta_0) (Eq. 3), the binomial-series
+// coefficients of the equation of state, device buffers, and the launch
+// sequence of one SSP-RK3 stage (three line kernels).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/xg.h"
+#include "xg_kernels.cuh"
+
+using xg::LineParams;
+using xg::StageBufs;
+
+struct xg_ctx {
+  xg_mesh_desc d;
+  int n[3];
+  long long np;
+  int dev;
+  LineParams P;
+  double* A = nullptr;   // q^n (the state)
+  double* Bq = nullptr;  // stage buffer
+  double* Cq = nullptr;  // stage buffer
+  double* W = nullptr;   // [3][np] primitives v, w, p'
+  double* T = nullptr;   // [5][np] partial tendency
+  double* S = nullptr;   // [np] heating
+  double* base = nullptr;  // [4][nz]
+  int* flag = nullptr;
+  int* hflag = nullptr;  // pinned
+  bool has_state = false;
+  bool has_base = false;
+  bool has_forcing = false;
+  bool failed = false;
+  int chunk_y = 1, nchunk_y = 1, chunk_z = 1, nchunk_z = 1;
+  size_t xsmem = 0;
+  // profiling: event pairs recorded around launches since the last fold
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> ev_kernel;   // kernel id of each recorded pair
+  size_t ev_used = 0;           // pairs recorded
+  double k_ms[3] = {0, 0, 0};
+  long long k_launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+// ------------------------------------------------------------------ LGL
+// Legendre P_N and P_{N-1} at x by the three-term recurrence.
+void legendre2(int N, long double x, long double* pN, long double* pN1) {
+  long double p0 = 1.0L, p1 = x;
+  if (N == 0) { *pN = 1.0L; *pN1 = 0.0L; return; }
+  for (int k = 1; k < N; ++k) {
+    long double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  *pN = p1;
+  *pN1 = p0;
+}
+
+// LGL points: the zeros of x P_N - P_{N-1} = -(1 - x^2) P_N' / N, found by
+// Newton's method (its derivative is (N+1) P_N) from the Chebyshev-Lobatto
+// points; then the derivative matrix of the Lagrange basis,
+// D[i][j] = P_N(x_i) / (P_N(x_j) (x_i - x_j)) for i != j,
+// D[0][0] = -N(N+1)/4, D[N][N] = N(N+1)/4, else 0 on the diagonal.
+void lgl_derivative(int N, double D[xg::kMaxOrder + 1][xg::kMaxOrder + 1]) {
+  long double x[xg::kMaxOrder + 1], PN[xg::kMaxOrder + 1];
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int j = 0; j <= N; ++j) {
+    long double xj = -cosl(pi * j / N);
+    for (int it = 0; it < 100; ++it) {
+      long double pn, pn1;
+      legendre2(N, xj, &pn, &pn1);
+      long double dx = (xj * pn - pn1) / ((N + 1) * pn);
+      xj -= dx;
+      if (fabsl(dx) < 1e-30L) break;
+    }
+    x[j] = xj;
+  }
+  x[0] = -1.0L;
+  x[N] = 1.0L;
+  for (int j = 0; j <= N; ++j) {
+    long double pn1;
+    legendre2(N, x[j], &PN[j], &pn1);
+  }
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= N; ++j) {
+      long double v;
+      if (i != j) v = PN[i] / (PN[j] * (x[i] - x[j]));
+      else if (i == 0) v = -(long double)N * (N + 1) / 4.0L;
+      else if (i == N) v = (long double)N * (N + 1) / 4.0L;
+      else v = 0.0L;
+      D[i][j] = (double)v;
+    }
+}
+
+// Binomial coefficients C(gamma, k), k = 1..12, of (1+x)^gamma - 1 and the
+// largest |x| (<= 0.1) for which the truncation error after 12 terms stays
+// below 2^-56 of the sum: |R| <= |C(gamma,13)| |x|^13 / (1 - |x|) (the
+// coefficients decrease in magnitude for 1 < gamma < 2) against a sum of at
+// least 0.9 gamma |x|.
+void eos_series(double gamma, double* c, double* xmax) {
+  long double ck = 1.0L;
+  for (int k = 1; k <= xg::kEosTerms; ++k) {
+    ck = ck * ((long double)gamma - (k - 1)) / k;
+    c[k - 1] = (double)ck;
+  }
+  long double c13 = fabsl(ck * ((long double)gamma - xg::kEosTerms) / (xg::kEosTerms + 1));
+  long double bound = ldexpl(1.0L, -56) * 0.9L * gamma * 0.9L / (c13 > 0 ? c13 : 1e-300L);
+  long double xm = powl(bound, 1.0L / xg::kEosTerms);
+  *xmax = (double)(xm < 0.1L ? xm : 0.1L);
+}
+
+xg_status fail_cuda(xg_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->failed = true;
+  fprintf(stderr, "xg: %s: %s\n", what, cudaGetErrorString(e));
+  return XG_ERR_CUDA;
+}
+
+#define XG_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return fail_cuda((ctx), e_, #call); \
+  } while (0)
+
+// Records the start (end = false) or end event of kernel k's launch.
+void prof_mark(xg_ctx* c, int k, bool end, cudaStream_t st) {
+  if (!c->profiling) return;
+  const size_t i = 2 * c->ev_used + (end ? 1 : 0);
+  while (c->events.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { c->profiling = false; return; }
+    c->events.push_back(e);
+  }
+  cudaEventRecord(c->events[i], st);
+  if (end) {
+    if (c->ev_kernel.size() <= c->ev_used) c->ev_kernel.resize(c->ev_used + 1);
+    c->ev_kernel[c->ev_used] = k;
+    ++c->ev_used;
+  }
+}
+
+// Folds the recorded pairs into the per-kernel totals (the stream has been
+// synchronised by the caller).
+void prof_fold(xg_ctx* c) {
+  for (size_t p = 0; p < c->ev_used; ++p) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->events[2 * p], c->events[2 * p + 1]) == cudaSuccess) {
+      c->k_ms[c->ev_kernel[p]] += ms;
+      c->k_launches[c->ev_kernel[p]] += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+template <int N>
+void launch_stage_n(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
+  dim3 gx(c->n[1], c->n[2]);
+  prof_mark(c, 0, false, st);
+  xg::k_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->P, B);
+  prof_mark(c, 0, true, st);
+  dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
+  prof_mark(c, 1, false, st);
+  xg::k_line_y<N><<<gy, 128, 0, st>>>(c->P, B, c->chunk_y);
+  prof_mark(c, 1, true, st);
+  dim3 gz((c->n[0] + 127) / 128, c->nchunk_z, c->n[1]);
+  prof_mark(c, 2, false, st);
+  xg::k_line_z<N><<<gz, 128, 0, st>>>(c->P, B, c->chunk_z);
+  prof_mark(c, 2, true, st);
+}
+
+template <int N>
+cudaError_t configure_n(xg_ctx* c) {
+  cudaError_t e = cudaFuncSetAttribute(xg::k_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)c->xsmem);
+  return e;
+}
+
+cudaError_t launch_stage(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
+  switch (c->d.order) {
+    case 1: launch_stage_n<1>(c, B, st); break;
+    case 2: launch_stage_n<2>(c, B, st); break;
+    case 3: launch_stage_n<3>(c, B, st); break;
+    case 4: launch_stage_n<4>(c, B, st); break;
+    case 5: launch_stage_n<5>(c, B, st); break;
+    case 6: launch_stage_n<6>(c, B, st); break;
+    case 7: launch_stage_n<7>(c, B, st); break;
+    case 8: launch_stage_n<8>(c, B, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t configure(xg_ctx* c) {
+  switch (c->d.order) {
+    case 1: return configure_n<1>(c);
+    case 2: return configure_n<2>(c);
+    case 3: return configure_n<3>(c);
+    case 4: return configure_n<4>(c);
+    case 5: return configure_n<5>(c);
+    case 6: return configure_n<6>(c);
+    case 7: return configure_n<7>(c);
+    case 8: return configure_n<8>(c);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Chunk of element segments per marching thread: enough threads for about
+// 12 warps per SM sub-partition on the device, at most all segments.
+void choose_chunks(int nseg, long long columns, int sms, int* chunk, int* nchunk) {
+  long long warps = ((columns + 31) / 32);
+  long long want = (long long)sms * 4 * 12;
+  long long k = (want + warps - 1) / (warps > 0 ? warps : 1);
+  if (k < 1) k = 1;
+  if (k > nseg) k = nseg;
+  *chunk = (int)((nseg + k - 1) / k);
+  *nchunk = (nseg + *chunk - 1) / *chunk;
+}
+
+StageBufs make_bufs(xg_ctx* c, const double* q, const double* qn, double* out, double dt,
+                    double alpha, double beta, int rhs_only) {
+  StageBufs B;
+  B.q = q;
+  B.qn = qn;
+  B.out = out;
+  B.W = c->W;
+  B.T = c->T;
+  B.S = c->has_forcing ? c->S : nullptr;
+  B.base = c->base;
+  B.flag = c->flag;
+  B.dt = dt;
+  B.alpha = alpha;
+  B.beta = beta;
+  B.rhs_only = rhs_only;
+  return B;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* xg_status_str(xg_status s) {
+  switch (s) {
+    case XG_OK: return "XG_OK";
+    case XG_ERR_ARG: return "XG_ERR_ARG";
+    case XG_ERR_CUDA: return "XG_ERR_CUDA";
+    case XG_ERR_OOM: return "XG_ERR_OOM";
+    case XG_ERR_NONFINITE: return "XG_ERR_NONFINITE";
+    case XG_ERR_TIMEOUT: return "XG_ERR_TIMEOUT";
+    case XG_ERR_UNSUPPORTED: return "XG_ERR_UNSUPPORTED";
+  }
+  return "XG_UNKNOWN";
+}
+
+xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
+  if (!out) return XG_ERR_ARG;
+  *out = nullptr;
+  if (!d) return XG_ERR_ARG;
+  for (int k = 0; k < 3; ++k) {
+    if (d->nel[k] < 1) return XG_ERR_ARG;
+    if (!(std::isfinite(d->lo[k]) && std::isfinite(d->hi[k]) && d->hi[k] > d->lo[k])) return XG_ERR_ARG;
+    if (d->periodic[k] != 0 && d->periodic[k] != 1) return XG_ERR_ARG;
+  }
+  if (d->order < 1 || d->order > xg::kMaxOrder) return XG_ERR_ARG;
+  if (!(finite_pos(d->R) && finite_pos(d->cp) && finite_pos(d->cv) && finite_pos(d->p_a))) return XG_ERR_ARG;
+  if (!(std::isfinite(d->g) && d->g >= 0.0 && std::isfinite(d->f_coriolis))) return XG_ERR_ARG;
+  const double gamma = d->cp / d->cv;
+  if (!(gamma > 1.0 && gamma < 2.0)) return XG_ERR_ARG;
+  if (d->precision != XG_FP64) return XG_ERR_UNSUPPORTED;
+  const int N = d->order;
+  int n[3];
+  for (int k = 0; k < 3; ++k) {
+    long long nk = (long long)N * d->nel[k] + (d->periodic[k] ? 0 : 1);
+    if (nk > (1 << 24)) return XG_ERR_UNSUPPORTED;
+    n[k] = (int)nk;
+  }
+  const long long np = (long long)n[0] * n[1] * n[2];
+  // one x-line per CTA: its fluxes and segment derivatives in shared memory
+  const size_t xsmem = sizeof(double) * (5 * (size_t)(n[0] + 1) + 5 * (size_t)d->nel[0] * (N + 1));
+  if (xsmem > 220 * 1024) return XG_ERR_UNSUPPORTED;
+  if (n[1] > 65535 || n[2] > 65535) return XG_ERR_UNSUPPORTED;  // grid y/z limits
+
+  xg_ctx* c = new (std::nothrow) xg_ctx();
+  if (!c) return XG_ERR_OOM;
+  c->d = *d;
+  c->n[0] = n[0]; c->n[1] = n[1]; c->n[2] = n[2];
+  c->np = np;
+  c->xsmem = xsmem;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) { fail_cuda(c, e, "cudaGetDevice"); delete c; return XG_ERR_CUDA; }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (sms <= 0) sms = 1;
+
+  LineParams& P = c->P;
+  memset(&P, 0, sizeof(P));
+  double D[xg::kMaxOrder + 1][xg::kMaxOrder + 1];
+  lgl_derivative(N, D);
+  for (int k = 0; k < 3; ++k) {
+    P.n[k] = n[k];
+    P.nseg[k] = d->nel[k];
+    P.per[k] = d->periodic[k];
+    const double h = (d->hi[k] - d->lo[k]) / d->nel[k];
+    for (int a = 0; a <= N; ++a) {
+      const double face = (a == 0 || a == N) ? 0.5 : 1.0;
+      for (int l = 0; l <= N; ++l) P.Dm[k][a][l] = -(2.0 / h) * face * D[a][l];
+    }
+  }
+  P.np = np;
+  eos_series(gamma, P.eos_c, &P.eos_xmax);
+  P.gamma = gamma;
+  P.f = d->f_coriolis;
+  P.g = d->g;
+  choose_chunks(d->nel[1], (long long)n[0] * n[2], sms, &c->chunk_y, &c->nchunk_y);
+  choose_chunks(d->nel[2], (long long)n[0] * n[1], sms, &c->chunk_z, &c->nchunk_z);
+
+  const size_t vec = sizeof(double) * (size_t)np;
+  struct { double** p; size_t bytes; } allocs[] = {
+      {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->W, 3 * vec},
+      {&c->T, 5 * vec}, {&c->S, vec}, {&c->base, sizeof(double) * 4 * (size_t)n[2]}};
+  for (auto& a : allocs) {
+    e = cudaMalloc((void**)a.p, a.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      xg_destroy(c);
+      return e == cudaErrorMemoryAllocation ? XG_ERR_OOM : XG_ERR_CUDA;
+    }
+  }
+  e = cudaMalloc((void**)&c->flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hflag, sizeof(int));
+  if (e == cudaSuccess) e = configure(c);
+  if (e != cudaSuccess) {
+    fail_cuda(c, e, "xg_mesh_create");
+    xg_destroy(c);
+    return XG_ERR_CUDA;
+  }
+  *out = c;
+  return XG_OK;
+}
+
+xg_status xg_mesh_np(const xg_ctx* c, long long* np) {
+  if (!c || !np) return XG_ERR_ARG;
+  *np = c->np;
+  return XG_OK;
+}
+
+xg_status xg_mesh_dims(const xg_ctx* c, int n[3]) {
+  if (!c || !n) return XG_ERR_ARG;
+  n[0] = c->n[0]; n[1] = c->n[1]; n[2] = c->n[2];
+  return XG_OK;
+}
+
+xg_status xg_set_state(xg_ctx* c, const double* q, const double* rho0, const double* rhotheta0,
+                       int where, void* stream) {
+  if (!c || !q) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
+  if ((rho0 == nullptr) != (rhotheta0 == nullptr)) return XG_ERR_ARG;
+  if (!rho0 && !c->has_base) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nz = c->n[2];
+  if (rho0) {
+    double* hb = (double*)malloc(sizeof(double) * 6 * (size_t)nz);
+    if (!hb) return XG_ERR_OOM;
+    double* r0 = hb + 4 * nz;
+    double* t0 = hb + 5 * nz;
+    if (where == XG_DEVICE) {
+      cudaError_t e = cudaMemcpyAsync(r0, rho0, sizeof(double) * nz, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(t0, rhotheta0, sizeof(double) * nz, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { free(hb); return fail_cuda(c, e, "xg_set_state reference copy"); }
+    } else {
+      memcpy(r0, rho0, sizeof(double) * nz);
+      memcpy(t0, rhotheta0, sizeof(double) * nz);
+    }
+    const double gamma = c->d.cp / c->d.cv;
+    for (int k = 0; k < nz; ++k) {
+      if (!(finite_pos(r0[k]) && finite_pos(t0[k]))) { free(hb); return XG_ERR_ARG; }
+      hb[k] = r0[k];
+      hb[nz + k] = t0[k];
+      hb[2 * nz + k] = c->d.p_a * pow(c->d.R * t0[k] / c->d.p_a, gamma);  // Eq. 3
+      hb[3 * nz + k] = 1.0 / t0[k];
+    }
+    cudaError_t e = cudaMemcpyAsync(c->base, hb, sizeof(double) * 4 * nz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free(hb);
+    if (e != cudaSuccess) return fail_cuda(c, e, "xg_set_state reference upload");
+    c->has_base = true;
+  }
+  XG_CUDA(c, cudaMemcpyAsync(c->A, q, sizeof(double) * 5 * (size_t)c->np,
+                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  c->has_state = true;
+  return XG_OK;
+}
+
+xg_status xg_set_forcing(xg_ctx* c, const double* S, int where, void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!S) {
+    c->has_forcing = false;
+    return XG_OK;
+  }
+  XG_CUDA(c, cudaMemcpyAsync(c->S, S, sizeof(double) * (size_t)c->np,
+                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  c->has_forcing = true;
+  return XG_OK;
+}
+
+xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
+  if (!c || !dqdt) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
+  if (!c->has_state) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dst = where == XG_DEVICE ? dqdt : c->Bq;
+  StageBufs B = make_bufs(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1);
+  XG_CUDA(c, launch_stage(c, B, st));
+  if (where == XG_HOST) {
+    XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
+                               cudaMemcpyDeviceToHost, st));
+  }
+  if (where == XG_HOST || c->profiling) {
+    XG_CUDA(c, cudaStreamSynchronize(st));
+    prof_fold(c);
+  }
+  return XG_OK;
+}
+
+xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!std::isfinite(dt) || nsteps < 0) return XG_ERR_ARG;
+  if (!c->has_state) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+  for (int it = 0; it < nsteps; ++it) {
+    StageBufs s1 = make_bufs(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0);
+    XG_CUDA(c, launch_stage(c, s1, st));
+    StageBufs s2 = make_bufs(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0);
+    XG_CUDA(c, launch_stage(c, s2, st));
+    StageBufs s3 = make_bufs(c, c->Cq, c->A, c->A, dt, 1.0 / 3.0, 2.0 / 3.0, 0);
+    XG_CUDA(c, launch_stage(c, s3, st));
+  }
+  XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  XG_CUDA(c, cudaStreamSynchronize(st));
+  prof_fold(c);
+  return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
+}
+
+xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
+  if (!c || !q) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
+  if (!c->has_state) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  XG_CUDA(c, cudaMemcpyAsync(q, c->A, sizeof(double) * 5 * (size_t)c->np,
+                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (where == XG_HOST) XG_CUDA(c, cudaStreamSynchronize(st));
+  return XG_OK;
+}
+
+xg_status xg_profile(xg_ctx* c, int enable) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  c->profiling = enable != 0;
+  return XG_OK;
+}
+
+xg_status xg_kernel_times(xg_ctx* c, double ms[3], long long launches[3], int reset) {
+  if (!c) return XG_ERR_ARG;
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = c->k_ms[k];
+    if (launches) launches[k] = c->k_launches[k];
+    if (reset) { c->k_ms[k] = 0.0; c->k_launches[k] = 0; }
+  }
+  return XG_OK;
+}
+
+void xg_destroy(xg_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  cudaFree(c->A);
+  cudaFree(c->Bq);
+  cudaFree(c->Cq);
+  cudaFree(c->W);
+  cudaFree(c->T);
+  cudaFree(c->S);
+  cudaFree(c->base);
+  cudaFree(c->flag);
+  if (c->hflag) cudaFreeHost(c->hflag);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,422 @@
+// xg_kernels.cuh -- FP64 line kernels of the explicit CG Euler path (sm_103a).
+//
+// The right-hand side of Sec. 2.1 (Eq. 1 restated for q = (rho', rho u,
+// rho v, rho w, Theta'), pressure from Eq. 3) is evaluated by the collocated
+// strong form of Sec. 2.2 (Eqs. 7-8) with DSS (Eqs. 9-11, Alg. 3) and the
+// inverse diagonal mass (Eq. 12).  On an axis-aligned box of equal elements
+// the metric is the same constant diagonal in every element, and the mass
+// is the tensor product M_I = J W_x(gx) W_y(gy) W_z(gz) of assembled 1-D LGL
+// weights.  The assembled divergence then splits into three 1-D operators:
+// along each grid line, a node interior to an element takes that element's
+// derivative (D F)_a, and a node on a shared face takes
+// (w_N (D F^left)_N + w_0 (D F^right)_0) / (w_N + w_0) =
+// ((D F^left)_N + (D F^right)_0) / 2 (w_0 = w_N); the transverse weights
+// cancel against M.  This is the paper's gather/assembly/scatter of
+// Alg. 1-3, reached without element-local storage and without atomics.
+//
+// One stage = three kernels over the SoA state:
+//   k_line_x  one CTA per x-line: pointwise primitives (u, v, w, p') of every
+//             node, x-fluxes staged in shared memory, one thread per element
+//             segment for the 1-D contraction (Alg. 2), face averaging;
+//             writes the x part of the tendency to T and (v, w, p') to W.
+//   k_line_y  one thread per (x, z) column marching along y over a chunk of
+//             element segments, carrying the shared face node's flux and
+//             one-sided derivative; adds the y part into T.
+//   k_line_z  one thread per (x, y) column marching along z; adds the z part,
+//             the sources (-rho' g k, -f k x rho u, rho S_theta), applies
+//             no-flux walls and either stores dq/dt or the fused SSP-RK
+//             stage combination out = alpha q^n + beta (q + dt L(q)).
+//
+// Every arithmetic step is FP64.  The derivative matrices come pre-scaled by
+// -2/h_d (chain rule of the affine map, sign of the divergence) with rows 0
+// and N halved for the face average; wall nodes undo the halving.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace xg {
+
+constexpr int kMaxOrder = 8;
+constexpr int kEosTerms = 12;
+
+// Launch-time constants of one mesh (passed by value as a kernel parameter).
+struct LineParams {
+  int n[3];       // global nodes per direction
+  int nseg[3];    // elements per direction
+  int per[3];     // 1 = periodic
+  long long np;   // n[0] n[1] n[2]
+  // Dm[d][a][l] = -(2/h_d) D[a][l] (x 1/2 for a = 0 and a = N)
+  double Dm[3][kMaxOrder + 1][kMaxOrder + 1];
+  // (1 + x)^gamma - 1 = sum_{k=1..12} eos_c[k-1] x^k for |x| < eos_xmax
+  double eos_c[kEosTerms];
+  double eos_xmax;
+  double gamma;
+  double f, g;    // Coriolis parameter, gravity
+};
+
+// Buffers and stage coefficients of one launch.
+struct StageBufs {
+  const double* q;      // [5][np] state the tendency is taken of
+  const double* qn;     // [5][np] q^n of the RK combination (alpha != 0)
+  double* out;          // [5][np] new state, or dq/dt when rhs_only
+  double* W;            // [3][np] v, w, p' (written by k_line_x)
+  double* T;            // [5][np] x + y parts of the tendency
+  const double* S;      // [np] heating S_theta (K/s)
+  const double* base;   // [4][nz]: rho0, Theta0, p0, 1/Theta0 per level
+  int* flag;            // set to 1 when a non-finite value is stored
+  double dt, alpha, beta;
+  int rhs_only;
+};
+
+// (1 + x)^gamma - 1: the binomial series (Horner) for small |x|, where the
+// truncation error after 12 terms is below 2^-56 relative (bound checked on
+// the host), else expm1(gamma log1p(x)).
+__device__ __forceinline__ double eos_phi(const LineParams& P, double x) {
+  if (fabs(x) < P.eos_xmax) {
+    double acc = P.eos_c[kEosTerms - 1];
+#pragma unroll
+    for (int k = kEosTerms - 2; k >= 0; --k) acc = fma(acc, x, P.eos_c[k]);
+    return acc * x;
+  }
+  return expm1(P.gamma * log1p(x));
+}
+
+__device__ __forceinline__ bool is_nonfinite(double v) {
+  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+
+// rows[a] = sum_l Dm[d][a][l] f[l], a = 0..N  ((N+1)^2 FP64 operations).
+template <int N, int D>
+__device__ __forceinline__ void contract(const LineParams& P, const double (&f)[N + 1],
+                                         double (&rows)[N + 1]) {
+#pragma unroll
+  for (int a = 0; a <= N; ++a) {
+    double acc = P.Dm[D][a][0] * f[0];
+#pragma unroll
+    for (int l = 1; l <= N; ++l) acc = fma(P.Dm[D][a][l], f[l], acc);
+    rows[a] = acc;
+  }
+}
+
+template <int N, int D>
+__device__ __forceinline__ double contract_row_N(const LineParams& P, const double (&f)[N + 1]) {
+  double acc = P.Dm[D][N][0] * f[0];
+#pragma unroll
+  for (int l = 1; l <= N; ++l) acc = fma(P.Dm[D][N][l], f[l], acc);
+  return acc;
+}
+
+// ---------------------------------------------------------------- x lines
+// grid (n_y, n_z), block kXThreads, dynamic shared memory
+// 8 * (5 (n_x + 1) + 5 nseg_x (N + 1)) bytes.
+constexpr int kXThreads = 128;
+
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const StageBufs B) {
+  extern __shared__ double sm[];
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nseg = P.nseg[0];
+  const int y = blockIdx.x, z = blockIdx.y;
+  const long long np = P.np;
+  const long long row = (long long)nx * (y + (long long)ny * z);
+  const int ld = nx + 1;
+  double* F = sm;             // [5][ld] x-fluxes at the line's nodes (+ periodic wrap slot)
+  double* R = sm + 5 * ld;    // [5][nseg][N+1] one-sided derivatives of every segment
+  const double rho0 = __ldg(B.base + z);
+  const double Th0 = __ldg(B.base + nz + z);
+  const double p0 = __ldg(B.base + 2 * nz + z);
+  const double iTh0 = __ldg(B.base + 3 * nz + z);
+  const double* __restrict__ q = B.q;
+
+  // pointwise primitives and x-fluxes, one node per thread (coalesced)
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const long long I = row + i;
+    const double rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
+    const double tp = q[4 * np + I];
+    const double ir = 1.0 / (rho0 + rp);
+    const double u = mu * ir, v = mv * ir, w = mw * ir;
+    const double pp = p0 * eos_phi(P, tp * iTh0);
+    const double Th = Th0 + tp;
+    B.W[I] = v;
+    B.W[np + I] = w;
+    B.W[2 * np + I] = pp;
+    F[i] = mu;
+    F[ld + i] = fma(mu, u, pp);
+    F[2 * ld + i] = mv * u;
+    F[3 * ld + i] = mw * u;
+    F[4 * ld + i] = Th * u;
+    if (P.per[0] && i == 0) {
+      F[nx] = F[0];
+      F[ld + nx] = F[ld];
+      F[2 * ld + nx] = F[2 * ld];
+      F[3 * ld + nx] = F[3 * ld];
+      F[4 * ld + nx] = F[4 * ld];
+    }
+  }
+  __syncthreads();
+
+  // one element segment per thread: (N+1)^2 contraction per flux component
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double f[N + 1], rows[N + 1];
+#pragma unroll
+      for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
+      contract<N, 0>(P, f, rows);
+#pragma unroll
+      for (int a = 0; a <= N; ++a) R[(c * nseg + s) * (N + 1) + a] = rows[a];
+    }
+  }
+  __syncthreads();
+
+  // assemble: face nodes add both one-sided halves, wall nodes double theirs
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const int s = i / N, a = i - s * N;
+    const long long I = row + i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double* Rc = R + c * nseg * (N + 1);
+      double v;
+      if (s == nseg) {                     // last wall node
+        v = Rc[(nseg - 1) * (N + 1) + N];
+        v = v + v;
+      } else if (a != 0) {
+        v = Rc[s * (N + 1) + a];
+      } else {
+        const double r0 = Rc[s * (N + 1)];
+        const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
+        v = r0 + (left >= 0 ? Rc[left * (N + 1) + N] : r0);
+      }
+      B.T[c * np + I] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- y lines
+// grid (ceil(n_x / blockDim), nchunk, n_z); each thread marches `chunk`
+// element segments along y at its (x, z).
+template <int N>
+__device__ __forceinline__ void flux_y(const LineParams& P, const double* __restrict__ q,
+                                       const double* __restrict__ W, long long np, long long I,
+                                       double Th0, double (&f)[5]) {
+  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+  const double v = W[I], pp = W[2 * np + I];
+  f[0] = mv;
+  f[1] = mu * v;
+  f[2] = fma(mv, v, pp);
+  f[3] = mw * v;
+  f[4] = (Th0 + tp) * v;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageBufs B, int chunk) {
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nseg = P.nseg[1];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int z = blockIdx.z;
+  const int s0 = blockIdx.y * chunk;
+  const int s1 = min(nseg, s0 + chunk);
+  if (s0 >= s1) return;
+  const long long np = P.np;
+  const long long col = x + (long long)nx * ny * z;
+  const double Th0 = __ldg(B.base + nz + z);
+  const double* __restrict__ q = B.q;
+  const double* __restrict__ W = B.W;
+  auto nodeI = [&](int gy) -> long long { return col + (long long)nx * (gy == ny ? 0 : gy); };
+
+  double carry[5];
+  bool has_left = (s0 > 0) || P.per[1];
+  if (has_left) {
+    const int sp = s0 > 0 ? s0 - 1 : nseg - 1;
+    double fl[5][N + 1];
+#pragma unroll
+    for (int l = 0; l <= N; ++l) {
+      double f[5];
+      flux_y<N>(P, q, W, np, nodeI(sp * N + l), Th0, f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) carry[c] = contract_row_N<N, 1>(P, fl[c]);
+  }
+
+  double fc[5][N + 1];
+  {
+    double f[5];
+    flux_y<N>(P, q, W, np, nodeI(s0 * N), Th0, f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
+  }
+  for (int s = s0; s < s1; ++s) {
+#pragma unroll
+    for (int l = 1; l <= N; ++l) {
+      double f[5];
+      flux_y<N>(P, q, W, np, nodeI(s * N + l), Th0, f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double rows[N + 1];
+      contract<N, 1>(P, fc[c], rows);
+      double* Tc = B.T + c * np;
+      const long long I0 = nodeI(s * N);
+      Tc[I0] += rows[0] + (has_left ? carry[c] : rows[0]);
+#pragma unroll
+      for (int a = 1; a < N; ++a) {
+        const long long I = nodeI(s * N + a);
+        Tc[I] += rows[a];
+      }
+      carry[c] = rows[N];
+      fc[c][0] = fc[c][N];
+    }
+    has_left = true;
+  }
+  if (!P.per[1] && s1 == nseg) {
+    const long long I = nodeI(nseg * N);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) B.T[c * np + I] += carry[c] + carry[c];
+  }
+}
+
+// ---------------------------------------------------------------- z lines + sources + stage
+template <int N>
+__device__ __forceinline__ void flux_z(const double* __restrict__ q, const double* __restrict__ W,
+                                       long long np, long long I, double Th0, double (&f)[5]) {
+  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+  const double w = W[np + I], pp = W[2 * np + I];
+  f[0] = mw;
+  f[1] = mu * w;
+  f[2] = mv * w;
+  f[3] = fma(mw, w, pp);
+  f[4] = (Th0 + tp) * w;
+}
+
+// Completes node I at level gz with the z part zpart[5]: tendency
+// L = T + zpart + sources, no-flux walls, then the stage store.
+__device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs& B, long long I,
+                                            int x, int y, int gz, const double (&zpart)[5],
+                                            bool& bad) {
+  const long long np = P.np;
+  const double* __restrict__ q = B.q;
+  const double rp = q[I], mu = q[np + I], mv = q[2 * np + I];
+  double L[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) L[c] = B.T[c * np + I] + zpart[c];
+  L[1] = fma(P.f, mv, L[1]);                     // -f k x (rho u): +f rho v
+  L[2] = fma(-P.f, mu, L[2]);                    //                 -f rho u
+  L[3] = fma(-P.g, rp, L[3]);                    // -rho' g
+  if (B.S) L[4] = fma(__ldg(B.base + gz) + rp, __ldg(B.S + I), L[4]);  // rho S_theta
+  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = 0.0;
+  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = 0.0;
+  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0;
+  if (B.rhs_only) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      B.out[c * np + I] = L[c];
+      bad |= is_nonfinite(L[c]);
+    }
+  } else if (B.alpha == 0.0) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double o = fma(B.dt, L[c], q[c * np + I]);
+      B.out[c * np + I] = o;
+      bad |= is_nonfinite(o);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double o = fma(B.alpha, B.qn[c * np + I], B.beta * fma(B.dt, L[c], q[c * np + I]));
+      B.out[c * np + I] = o;
+      bad |= is_nonfinite(o);
+    }
+  }
+}
+
+// grid (ceil(n_x / blockDim), nchunk, n_y); each thread marches `chunk`
+// element segments along z at its (x, y).
+template <int N>
+__global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageBufs B, int chunk) {
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nseg = P.nseg[2];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int y = blockIdx.z;
+  const int s0 = blockIdx.y * chunk;
+  const int s1 = min(nseg, s0 + chunk);
+  if (s0 >= s1) return;
+  const long long np = P.np;
+  const long long nxy = (long long)nx * ny;
+  const long long col = x + (long long)nx * y;
+  const double* __restrict__ q = B.q;
+  const double* __restrict__ W = B.W;
+  auto lev = [&](int gz) -> int { return gz == nz ? 0 : gz; };
+  auto th0 = [&](int gz) -> double { return __ldg(B.base + nz + gz); };
+  bool bad = false;
+
+  double carry[5];
+  bool has_left = (s0 > 0) || P.per[2];
+  if (has_left) {
+    const int sp = s0 > 0 ? s0 - 1 : nseg - 1;
+    double fl[5][N + 1];
+#pragma unroll
+    for (int l = 0; l <= N; ++l) {
+      const int gz = lev(sp * N + l);
+      double f[5];
+      flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) carry[c] = contract_row_N<N, 2>(P, fl[c]);
+  }
+
+  double fc[5][N + 1];
+  {
+    const int gz = s0 * N;
+    double f[5];
+    flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
+  }
+  for (int s = s0; s < s1; ++s) {
+#pragma unroll
+    for (int l = 1; l <= N; ++l) {
+      const int gz = lev(s * N + l);
+      double f[5];
+      flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
+    }
+    double rows[5][N + 1];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) contract<N, 2>(P, fc[c], rows[c]);
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const int gz = s * N + a;
+      double zp[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        zp[c] = a == 0 ? rows[c][0] + (has_left ? carry[c] : rows[c][0]) : rows[c][a];
+      finish_node(P, B, col + nxy * gz, x, y, gz, zp, bad);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      carry[c] = rows[c][N];
+      fc[c][0] = fc[c][N];
+    }
+    has_left = true;
+  }
+  if (!P.per[2] && s1 == nseg) {
+    const int gz = nseg * N;
+    double zp[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) zp[c] = carry[c] + carry[c];
+    finish_node(P, B, col + nxy * gz, x, y, gz, zp, bad);
+  }
+  if (bad) *B.flag = 1;
+}
+
+}  // namespace xg

@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in ``include/xg.h`` (same function names).
+
+Argument marshalling only: every step of the path runs in ``libxg.so``.
+Arrays may be torch tensors (CUDA tensors are passed as device pointers,
+CPU tensors as host pointers), numpy arrays (host) or raw integer
+addresses together with an explicit ``where``.  The stream defaults to
+torch's current stream for CUDA tensors and to the legacy stream otherwise.
+A non-OK status raises ``XgError`` carrying the status code.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxg.so")
+
+XG_OK, XG_ERR_ARG, XG_ERR_CUDA, XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, \
+    XG_ERR_UNSUPPORTED = range(7)
+XG_HOST, XG_DEVICE = 0, 1
+XG_FP64, XG_FP32 = 0, 1
+
+__all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
+           "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
+           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
+           "XG_FP64", "XG_FP32", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
+           "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
+
+
+class xg_mesh_desc(ctypes.Structure):
+    _fields_ = [("nel", ctypes.c_int * 3), ("order", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("precision", ctypes.c_int),
+                ("f_coriolis", ctypes.c_double), ("g", ctypes.c_double),
+                ("R", ctypes.c_double), ("cp", ctypes.c_double), ("cv", ctypes.c_double),
+                ("p_a", ctypes.c_double)]
+
+
+class XgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s" % (where, _status_name(status)))
+
+
+_lib = None
+
+
+def library():
+    """Load libxg.so (once).  Raises when it has not been built: there is no
+    fallback path."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libxg.so is not built (%s); run "
+                           "paper_2504_08157_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.xg_status_str.restype = ctypes.c_char_p
+    lib.xg_status_str.argtypes = [I]
+    lib.xg_mesh_create.restype = I
+    lib.xg_mesh_create.argtypes = [ctypes.POINTER(xg_mesh_desc), ctypes.POINTER(P)]
+    lib.xg_mesh_np.restype = I
+    lib.xg_mesh_np.argtypes = [P, ctypes.POINTER(LL)]
+    lib.xg_mesh_dims.restype = I
+    lib.xg_mesh_dims.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.xg_set_state.restype = I
+    lib.xg_set_state.argtypes = [P, P, P, P, I, P]
+    lib.xg_set_forcing.restype = I
+    lib.xg_set_forcing.argtypes = [P, P, I, P]
+    lib.xg_rhs.restype = I
+    lib.xg_rhs.argtypes = [P, P, I, P]
+    lib.xg_step.restype = I
+    lib.xg_step.argtypes = [P, D, I, P]
+    lib.xg_get_state.restype = I
+    lib.xg_get_state.argtypes = [P, P, I, P]
+    lib.xg_profile.restype = I
+    lib.xg_profile.argtypes = [P, I]
+    lib.xg_kernel_times.restype = I
+    lib.xg_kernel_times.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(LL), I]
+    lib.xg_destroy.restype = None
+    lib.xg_destroy.argtypes = [P]
+    _lib = lib
+    return lib
+
+
+def _status_name(s):
+    try:
+        return library().xg_status_str(int(s)).decode()
+    except Exception:  # the library itself failed to load
+        return "status %d" % int(s)
+
+
+def _check(s, where):
+    if s != XG_OK:
+        raise XgError(s, where)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, where=None, writable=False):
+    """(address, where, stream-or-None) of an array argument."""
+    if a is None:
+        return None, where, None
+    if isinstance(a, int):
+        if where is None:
+            raise ValueError("raw addresses need an explicit where")
+        return a, where, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        if a.is_cuda:
+            return a.data_ptr(), XG_DEVICE, torch.cuda.current_stream(a.device).cuda_stream
+        return a.data_ptr(), XG_HOST, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float64")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("output array is read-only")
+        return a.ctypes.data, XG_HOST, None
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def mesh_desc(nel, order, lo, hi, periodic, f=0.0, g=9.81, R=287.0, cp=1004.5, cv=717.5,
+              p_a=1.0e5, precision=XG_FP64):
+    """Fill an xg_mesh_desc (the problem statement of Sec. 2.1-2.2)."""
+    d = xg_mesh_desc()
+    for k in range(3):
+        d.nel[k] = int(nel[k])
+        d.lo[k] = float(lo[k])
+        d.hi[k] = float(hi[k])
+        d.periodic[k] = int(bool(periodic[k]))
+    d.order = int(order)
+    d.precision = int(precision)
+    d.f_coriolis, d.g, d.R, d.cp, d.cv, d.p_a = float(f), float(g), float(R), float(cp), \
+        float(cv), float(p_a)
+    return d
+
+
+def xg_status_str(s):
+    return library().xg_status_str(int(s)).decode()
+
+
+def xg_mesh_create(desc):
+    """Returns the context handle (an integer address)."""
+    out = ctypes.c_void_p()
+    _check(library().xg_mesh_create(ctypes.byref(desc), ctypes.byref(out)), "xg_mesh_create")
+    return out.value
+
+
+def xg_mesh_np(ctx):
+    n = ctypes.c_longlong()
+    _check(library().xg_mesh_np(ctx, ctypes.byref(n)), "xg_mesh_np")
+    return n.value
+
+
+def xg_mesh_dims(ctx):
+    n = (ctypes.c_int * 3)()
+    _check(library().xg_mesh_dims(ctx, n), "xg_mesh_dims")
+    return tuple(n)
+
+
+def _stream(stream, implied):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    return implied
+
+
+def xg_set_state(ctx, q, rho0=None, rhotheta0=None, where=None, stream=None):
+    pq, wq, sq = _ptr(q, where)
+    pr, wr, _ = _ptr(rho0, wq)
+    pt, wt, _ = _ptr(rhotheta0, wq)
+    if pr is not None and (wr != wq or wt != wq):
+        raise ValueError("q and the reference arrays must all be host or all device")
+    _check(library().xg_set_state(ctx, pq, pr, pt, wq, _stream(stream, sq)), "xg_set_state")
+
+
+def xg_set_forcing(ctx, S_theta, where=None, stream=None):
+    p, w, s = _ptr(S_theta, where)
+    _check(library().xg_set_forcing(ctx, p, XG_HOST if w is None else w, _stream(stream, s)),
+           "xg_set_forcing")
+
+
+def xg_rhs(ctx, dqdt, where=None, stream=None):
+    p, w, s = _ptr(dqdt, where, writable=True)
+    _check(library().xg_rhs(ctx, p, w, _stream(stream, s)), "xg_rhs")
+
+
+def xg_step(ctx, dt, nsteps, stream=None):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    _check(library().xg_step(ctx, float(dt), int(nsteps), _stream(stream, None)), "xg_step")
+
+
+def xg_get_state(ctx, q, where=None, stream=None):
+    p, w, s = _ptr(q, where, writable=True)
+    _check(library().xg_get_state(ctx, p, w, _stream(stream, s)), "xg_get_state")
+
+
+def xg_profile(ctx, enable):
+    _check(library().xg_profile(ctx, int(bool(enable))), "xg_profile")
+
+
+def xg_kernel_times(ctx, reset=False):
+    """((ms_x, ms_y, ms_z), (launches_x, launches_y, launches_z))."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_longlong * 3)()
+    _check(library().xg_kernel_times(ctx, ms, n, int(bool(reset))), "xg_kernel_times")
+    return tuple(ms), tuple(n)
+
+
+def xg_destroy(ctx):
+    if ctx:
+        library().xg_destroy(ctx)

@@ -1,0 +1,89 @@
+"""Shared helpers of the tests: oracle set-up, the GPU path through the C ABI
+(torch tensors for device memory), and the relative L2 metric."""
+
+import numpy as np
+
+from inputs import workloads as W  # noqa: F401
+from oracle import euler as E, mesh as M, ssprk3
+
+
+def rel_l2(a, b):
+    """||a - b|| / ||b|| over nodes for one variable; the absolute norm when
+    ||b|| is (numerically) zero."""
+    nb = np.linalg.norm(b)
+    d = np.linalg.norm(np.asarray(a) - np.asarray(b))
+    return d / nb if nb > 1e-300 else d
+
+
+def rel_l2_per_var(a, b):
+    return np.array([rel_l2(a[v], b[v]) for v in range(a.shape[0])])
+
+
+def oracle_of(wl, elements=None):
+    m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"], elements=elements)
+    phys = E.Physics(**wl["phys"])
+    base = E.Base(wl["rho0"], wl["Theta0"])
+    return m, phys, base
+
+
+def oracle_rhs(wl, q=None):
+    m, phys, base = oracle_of(wl)
+    return E.rhs(m, wl["q"] if q is None else q, base, wl["S_theta"], phys)
+
+
+def oracle_steps(wl, nsteps, q=None):
+    m, phys, base = oracle_of(wl)
+    L = lambda s: E.rhs(m, s, base, wl["S_theta"], phys)
+    return ssprk3.run(L, wl["q"] if q is None else q, wl["dt"], nsteps)
+
+
+class GpuRun:
+    """One library context for a workload, inputs resident on cuda:0."""
+
+    def __init__(self, wl, device="cuda:0"):
+        import torch
+        from paper_2504_08157_gb300 import xg
+        self.xg, self.torch, self.wl = xg, torch, wl
+        self.dev = torch.device(device)
+        ph = wl["phys"]
+        self.ctx = xg.xg_mesh_create(xg.mesh_desc(
+            wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"], f=ph["f"], g=ph["g"],
+            R=ph["R"], cp=ph["cp"], cv=ph["cv"], p_a=ph["p_a"]))
+        self.np = xg.xg_mesh_np(self.ctx)
+        self.set_state(wl["q"], with_base=True)
+        if wl["S_theta"] is not None:
+            xg.xg_set_forcing(self.ctx, torch.from_numpy(np.ascontiguousarray(wl["S_theta"])).to(self.dev))
+
+    def set_state(self, q, with_base=False):
+        t = self.torch
+        qd = t.from_numpy(np.ascontiguousarray(q)).to(self.dev)
+        if with_base:
+            self.xg.xg_set_state(self.ctx, qd, t.from_numpy(self.wl["rho0"]).to(self.dev),
+                                 t.from_numpy(self.wl["Theta0"]).to(self.dev))
+        else:
+            self.xg.xg_set_state(self.ctx, qd)
+        self.torch.cuda.synchronize()
+
+    def rhs(self):
+        out = self.torch.empty((5, self.np), dtype=self.torch.float64, device=self.dev)
+        self.xg.xg_rhs(self.ctx, out)
+        return out.cpu().numpy()
+
+    def step(self, nsteps, dt=None):
+        self.xg.xg_step(self.ctx, self.wl["dt"] if dt is None else dt, nsteps)
+
+    def state(self):
+        out = self.torch.empty((5, self.np), dtype=self.torch.float64, device=self.dev)
+        self.xg.xg_get_state(self.ctx, out)
+        return out.cpu().numpy()
+
+    def close(self):
+        if self.ctx:
+            self.xg.xg_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

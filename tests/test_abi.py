@@ -1,0 +1,94 @@
+"""CPU tests of the C-ABI library: it builds, loads, exports every function
+that include/xg.h declares, and rejects invalid arguments on the host before
+any GPU work (no compute calls here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_08157_gb300 import build, xg
+    build.build()
+    return xg.library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("xg_mesh_create", "xg_set_state", "xg_set_forcing", "xg_rhs", "xg_step",
+                     "xg_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    from paper_2504_08157_gb300 import xg
+    for s in range(7):
+        assert xg.xg_status_str(s).startswith("XG_")
+    assert xg.xg_status_str(99) == "XG_UNKNOWN"
+
+
+def _desc(**kw):
+    from paper_2504_08157_gb300 import xg
+    geo = dict(nel=(2, 2, 2), order=4, lo=(0, 0, 0), hi=(1e3, 1e3, 1e3), periodic=(0, 0, 0))
+    extra = {k: v for k, v in kw.items() if k not in geo}
+    geo.update({k: v for k, v in kw.items() if k in geo})
+    return xg.mesh_desc(geo["nel"], geo["order"], geo["lo"], geo["hi"], geo["periodic"], **extra)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nel=(0, 2, 2)), dict(order=0), dict(order=9), dict(hi=(1e3, 0.0, 1e3)),
+    dict(cp=-1.0), dict(cv=1004.5), dict(g=float("nan")),
+])
+def test_mesh_create_rejects_bad_arguments(lib, bad):
+    from paper_2504_08157_gb300 import xg
+    with pytest.raises(xg.XgError) as e:
+        xg.xg_mesh_create(_desc(**bad))
+    assert e.value.status == xg.XG_ERR_ARG
+
+
+def test_unsupported_precision(lib):
+    from paper_2504_08157_gb300 import xg
+    with pytest.raises(xg.XgError) as e:
+        xg.xg_mesh_create(_desc(precision=xg.XG_FP32))
+    assert e.value.status == xg.XG_ERR_UNSUPPORTED
+
+
+def test_null_arguments(lib):
+    from paper_2504_08157_gb300 import xg
+    P = ctypes.c_void_p
+    assert lib.xg_mesh_create(None, None) == xg.XG_ERR_ARG
+    out = P()
+    assert lib.xg_mesh_create(None, ctypes.byref(out)) == xg.XG_ERR_ARG and not out.value
+    assert lib.xg_set_state(None, None, None, None, 0, None) == xg.XG_ERR_ARG
+    assert lib.xg_set_forcing(None, None, 0, None) == xg.XG_ERR_ARG
+    assert lib.xg_rhs(None, None, 0, None) == xg.XG_ERR_ARG
+    assert lib.xg_step(None, 0.1, 1, None) == xg.XG_ERR_ARG
+    assert lib.xg_get_state(None, None, 0, None) == xg.XG_ERR_ARG
+    n = ctypes.c_longlong()
+    assert lib.xg_mesh_np(None, ctypes.byref(n)) == xg.XG_ERR_ARG
+    lib.xg_destroy(None)  # no-op
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2504_08157_gb300 import xg
+    monkeypatch.setattr(xg, "_lib", None)
+    monkeypatch.setattr(xg, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError):
+        xg.library()
