@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libxg.so")
 SOURCES = [os.path.join(HERE, "csrc", "xg_api.cu")]
-DEPENDS = SOURCES + [os.path.join(HERE, "csrc", "xg_kernels.cuh"),
+DEPENDS = SOURCES + [os.path.join(HERE, "csrc", "xg_kernels.cuh"), os.path.join(HERE, "csrc", "xg_setup.h"),
                      os.path.join(ROOT, "include", "xg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
