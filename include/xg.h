@@ -153,6 +153,38 @@ xg_status xg_kernel_times(xg_ctx* ctx, double ms[3], long long launches[3], int 
  * is a no-op. */
 void xg_destroy(xg_ctx* ctx);
 
+/* Size of the fixed device scratch used by xg_rhs_noalloc (16 MiB). */
+#define XG_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The right-hand side of xg_rhs without a context and without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot or must not call cudaMalloc -- for example code
+ * running inside an application whose device memory has been handed to its
+ * own caching allocator or memory pool (a cudaMalloc there may fail or split
+ * the pool), plug-ins and callbacks that are not allowed to allocate, and
+ * latency-bound loops where an allocation would stall the device.
+ *
+ * The caller passes every input and output as device memory of the current
+ * device: q [5][Np], rho0 and rhotheta0 [n_z], S_theta [Np] (NULL = no
+ * heating), dqdt [5][Np] (layouts as above).  The intermediate arrays the
+ * kernels need live in one fixed array of XG_NOALLOC_SCRATCH_BYTES per
+ * device, which every device that loads this library keeps until the
+ * process exits; meshes whose 8 Np + 4 n_z + 32 doubles do not fit (about
+ * 262,000 nodes) are rejected with XG_ERR_UNSUPPORTED and a message on
+ * stderr.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (different streams or
+ * threads) race: serialise them.  Work is enqueued on `stream` and the call
+ * returns without waiting; the reference values must be positive (this
+ * entry point cannot check device data without waiting for it).
+ * Errors: XG_ERR_ARG (NULL pointer, invalid description), XG_ERR_UNSUPPORTED
+ * (mesh too large for the scratch, or a description this build cannot run),
+ * XG_ERR_CUDA. */
+xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, const double* rho0,
+                         const double* rhotheta0, const double* S_theta, double* dqdt,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 """In-tree build of the CUDA library ``libxg.so`` (sm_103a only).
 
-One translation unit (the C ABI plus the line kernels for orders 1-8),
+Two translation units (the C ABI with the line kernels for orders 1-8, and
+the allocation-free right-hand side),
 compiled with nvcc for ``-gencode arch=compute_103a,code=sm_103a`` and linked
 as a shared library next to this file.  The CUDA runtime is linked
 statically so the library loads without the toolkit's library path.
@@ -14,7 +15,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libxg.so")
-SOURCES = [os.path.join(HERE, "csrc", "xg_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "xg_api.cu"), os.path.join(HERE, "csrc", "xg_noalloc.cu")]
 DEPENDS = SOURCES + [os.path.join(HERE, "csrc", "xg_kernels.cuh"), os.path.join(HERE, "csrc", "xg_setup.h"),
                      os.path.join(ROOT, "include", "xg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -23,7 +23,7 @@ XG_FP64, XG_FP32 = 0, 1
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
+           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -79,6 +79,8 @@ def library():
     lib.xg_profile.argtypes = [P, I]
     lib.xg_kernel_times.restype = I
     lib.xg_kernel_times.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(LL), I]
+    lib.xg_rhs_noalloc.restype = I
+    lib.xg_rhs_noalloc.argtypes = [ctypes.POINTER(xg_mesh_desc), P, P, P, P, P, P]
     lib.xg_destroy.restype = None
     lib.xg_destroy.argtypes = [P]
     _lib = lib
@@ -216,6 +218,17 @@ def xg_kernel_times(ctx, reset=False):
     n = (ctypes.c_longlong * 3)()
     _check(library().xg_kernel_times(ctx, ms, n, int(bool(reset))), "xg_kernel_times")
     return tuple(ms), tuple(n)
+
+
+def xg_rhs_noalloc(desc, q, rho0, rhotheta0, S_theta, dqdt, stream=None):
+    """Context-free right-hand side that allocates no device memory (all
+    arrays are device memory of the current device)."""
+    pq, wq, sq = _ptr(q)
+    ptrs = [_ptr(a) for a in (rho0, rhotheta0, S_theta, dqdt)]
+    if wq != XG_DEVICE or any(p[0] is not None and p[1] != XG_DEVICE for p in ptrs):
+        raise ValueError("xg_rhs_noalloc takes device arrays only")
+    _check(library().xg_rhs_noalloc(ctypes.byref(desc), pq, ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                    ptrs[3][0], _stream(stream, sq)), "xg_rhs_noalloc")
 
 
 def xg_destroy(ctx):
