@@ -50,22 +50,30 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def flops_per_node(kernel, N):
-    """Algorithmic FP64 flops per unique node of each kernel (FMA = 2),
-    counted from the arithmetic each performs for N-th order elements:
-    a 1-D segment contraction costs (N+1) rows x (1 mul + N fma) =
-    (N+1)(2N+1) flops per flux component and covers N unique nodes, and a
-    face node adds one more addition per component."""
-    contraction = 5 * (N + 1) * (2 * N + 1) / N + 5.0 / N
+    """Algorithmic FP64 flops per unique node of each kernel (FMA = 2), from
+    the arithmetic each performs for N-th order elements (one segment of
+    N+1 nodes covers N unique nodes):
+
+    * x: the even/odd contraction of one flux component over a segment,
+      2P adds + P (4P + 2e) + e (2P - 1) with P = (N+1)//2, e = [N even];
+      face sums 5/N; pointwise rho (1), 1/rho (4 fma), u v w (3),
+      Theta'/Theta0 (1), 8-term series (7 fma + 1 mul), p0 * (1), Theta (1),
+      x-fluxes (1 fma + 3 mul).
+    * y, z: N rows of N+1 fma started from the running tendency, row N
+      (1 mul + N fma) and the face addition: 2N^2 + 4N + 2 per component and
+      segment; fluxes (3 mul + 1 fma + 1 add).  z adds the sources (3 fma,
+      1 add, 1 fma) and the stage update (5 fma in stage 1, 5 x (2 fma +
+      1 mul) in stages 2-3, averaged)."""
+    P, e = (N + 1) // 2, 1 if N % 2 == 0 else 0
+    eo = 2 * P + P * (4 * P + 2 * e) + e * (2 * P - 1)
+    folded = 2 * N * N + 4 * N + 2
     if kernel == "k_line_x":
-        # rho, 1/rho, u v w, Theta'/Theta0, 12-term series (11 fma + 2 mul),
-        # Theta, 1 fma + 3 mul of the x-fluxes
-        return 1 + 1 + 3 + 1 + 24 + 1 + 5 + contraction
+        pointwise = 1 + 8 + 3 + 1 + 15 + 1 + 1 + 1 + 5
+        return pointwise + 5.0 * eo / N + 5.0 / N
     if kernel == "k_line_y":
-        return 5 + contraction + 5            # y-fluxes, contraction, T +=
+        return 6 + 5.0 * folded / N
     if kernel == "k_line_z":
-        # z-fluxes, contraction, T + z part, sources (3 fma + rho + fma),
-        # stage update (2-3 fma/mul per variable, average over the stages)
-        return 5 + contraction + 5 + 6 + 5 * (2 + 5) / 3
+        return 6 + 5.0 * folded / N + 9 + (10 + 25 + 25) / 3.0
     raise KeyError(kernel)
 
 

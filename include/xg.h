@@ -149,6 +149,12 @@ xg_status xg_profile(xg_ctx* ctx, int enable);
  * Errors: XG_ERR_ARG. */
 xg_status xg_kernel_times(xg_ctx* ctx, double ms[3], long long launches[3], int reset);
 
+/* Applies the library's FP64 reciprocal (the one used for 1/rho: a
+ * hardware estimate refined by Newton-Raphson steps) to n device values
+ * x[i] > 0 (normal numbers), writing out[i], on `stream`.  Exposed so that
+ * tests can hold it against IEEE division.  Errors: XG_ERR_ARG, XG_ERR_CUDA. */
+xg_status xg_reciprocal(const double* x, double* out, long long n, void* stream);
+
 /* Free every buffer of the context (synchronises the device first).  NULL
  * is a no-op. */
 void xg_destroy(xg_ctx* ctx);

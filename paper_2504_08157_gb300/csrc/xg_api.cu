@@ -52,6 +52,13 @@ struct xg_ctx {
 
 namespace {
 
+// Reciprocal self-check: out[i] = rcp_newton(x[i]) (positive normal x).
+__global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = xg::rcp_newton(x[i]);
+}
+
 xg_status fail_cuda(xg_ctx* c, cudaError_t e, const char* what) {
   if (c) c->failed = true;
   fprintf(stderr, "xg: %s: %s\n", what, cudaGetErrorString(e));
@@ -205,8 +212,7 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
   if (sms <= 0) sms = 1;
 
   xg::fill_line_params(d, geo, &c->P);
-  xg::choose_chunks(d->nel[1], (long long)n[0] * n[2], sms, &c->chunk_y, &c->nchunk_y);
-  xg::choose_chunks(d->nel[2], (long long)n[0] * n[1], sms, &c->chunk_z, &c->nchunk_z);
+  xg::plan_marches(d, geo, sms, &c->chunk_y, &c->nchunk_y, &c->chunk_z, &c->nchunk_z);
 
   const size_t vec = sizeof(double) * (size_t)np;
   struct { double** p; size_t bytes; } allocs[] = {
@@ -369,6 +375,17 @@ xg_status xg_kernel_times(xg_ctx* c, double ms[3], long long launches[3], int re
     if (launches) launches[k] = c->k_launches[k];
     if (reset) { c->k_ms[k] = 0.0; c->k_launches[k] = 0; }
   }
+  return XG_OK;
+}
+
+xg_status xg_reciprocal(const double* x, double* out, long long n, void* stream) {
+  if (!x || !out || n < 0) return XG_ERR_ARG;
+  if (n == 0) return XG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long blocks = (n + 255) / 256;
+  k_rcp_check<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, out, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(nullptr, e, "xg_reciprocal");
   return XG_OK;
 }
 

@@ -29,7 +29,13 @@
 //
 // Every arithmetic step is FP64.  The derivative matrices come pre-scaled by
 // -2/h_d (chain rule of the affine map, sign of the divergence) with rows 0
-// and N halved for the face average; wall nodes undo the halving.
+// and N halved for the face average; wall nodes undo the halving.  The FP64
+// pipe (2 DFMA/clk/SM on GB300) bounds these kernels, so the arithmetic is
+// arranged to spend few FP64 instructions: the running tendency is the
+// starting value of each contraction's FMA chain (no separate additions), the
+// x contraction uses the even/odd split of the centro-antisymmetric LGL
+// derivative matrix, 1/rho is one hardware reciprocal estimate refined by
+// two Newton steps, and the equation of state is a short binomial series.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,7 +44,8 @@
 namespace xg {
 
 constexpr int kMaxOrder = 8;
-constexpr int kEosTerms = 12;
+constexpr int kMaxPairs = (kMaxOrder + 1) / 2;
+constexpr int kEosTerms = 8;
 
 // Launch-time constants of one mesh (passed by value as a kernel parameter).
 struct LineParams {
@@ -48,7 +55,16 @@ struct LineParams {
   long long np;   // n[0] n[1] n[2]
   // Dm[d][a][l] = -(2/h_d) D[a][l] (x 1/2 for a = 0 and a = N)
   double Dm[3][kMaxOrder + 1][kMaxOrder + 1];
-  // (1 + x)^gamma - 1 = sum_{k=1..12} eos_c[k-1] x^k for |x| < eos_xmax
+  // even/odd split of Dm (pairs l < N-l):  for i < (N+1)/2
+  //   (Dm f)_i   = sum_l EA[i][l] o_l + (sum_l EB[i][l] e_l + EBm[i] f_mid)
+  //   (Dm f)_N-i = sum_l EA[i][l] o_l - (...)
+  // with e_l = f_l + f_{N-l}, o_l = f_l - f_{N-l}; for even N the middle row
+  //   (Dm f)_{N/2} = sum_l EM[l] o_l.
+  double EA[3][kMaxPairs][kMaxPairs];
+  double EB[3][kMaxPairs][kMaxPairs];
+  double EBm[3][kMaxPairs];
+  double EM[3][kMaxPairs];
+  // (1 + x)^gamma - 1 = sum_{k=1..8} eos_c[k-1] x^k for |x| < eos_xmax
   double eos_c[kEosTerms];
   double eos_xmax;
   double gamma;
@@ -70,7 +86,7 @@ struct StageBufs {
 };
 
 // (1 + x)^gamma - 1: the binomial series (Horner) for small |x|, where the
-// truncation error after 12 terms is below 2^-56 relative (bound checked on
+// truncation error after 8 terms is below 2^-56 relative (bound checked on
 // the host), else expm1(gamma log1p(x)).
 __device__ __forceinline__ double eos_phi(const LineParams& P, double x) {
   if (fabs(x) < P.eos_xmax) {
@@ -82,25 +98,68 @@ __device__ __forceinline__ double eos_phi(const LineParams& P, double x) {
   return expm1(P.gamma * log1p(x));
 }
 
+// 1/a for positive normal a: the hardware reciprocal estimate refined by two
+// Newton-Raphson steps r <- r + r (1 - a r) (quadratic convergence; the
+// estimate's error squared twice is far below the FP64 rounding, and the
+// last FMA step leaves the result within an ulp).
+__device__ __forceinline__ double rcp_newton(double a) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+  double e = fma(-a, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-a, r, 1.0);
+  return fma(r, e, r);
+}
+
 __device__ __forceinline__ bool is_nonfinite(double v) {
   return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
 
-// rows[a] = sum_l Dm[d][a][l] f[l], a = 0..N  ((N+1)^2 FP64 operations).
+// rows[a] = sum_l Dm[d][a][l] f[l], a = 0..N, by the even/odd split
+// (2P + P (2P + [N even] + 2) + [N even] P FP64 operations, P = (N+1)/2:
+// 20 instead of 25 at N = 4).
 template <int N, int D>
-__device__ __forceinline__ void contract(const LineParams& P, const double (&f)[N + 1],
-                                         double (&rows)[N + 1]) {
+__device__ __forceinline__ void contract_eo(const LineParams& P, const double (&f)[N + 1],
+                                            double (&rows)[N + 1]) {
+  constexpr int Pp = (N + 1) / 2;
+  double e[Pp], o[Pp];
 #pragma unroll
-  for (int a = 0; a <= N; ++a) {
-    double acc = P.Dm[D][a][0] * f[0];
+  for (int l = 0; l < Pp; ++l) {
+    e[l] = f[l] + f[N - l];
+    o[l] = f[l] - f[N - l];
+  }
 #pragma unroll
-    for (int l = 1; l <= N; ++l) acc = fma(P.Dm[D][a][l], f[l], acc);
-    rows[a] = acc;
+  for (int i = 0; i < Pp; ++i) {
+    double s = P.EA[D][i][0] * o[0];
+#pragma unroll
+    for (int l = 1; l < Pp; ++l) s = fma(P.EA[D][i][l], o[l], s);
+    double t = P.EB[D][i][0] * e[0];
+#pragma unroll
+    for (int l = 1; l < Pp; ++l) t = fma(P.EB[D][i][l], e[l], t);
+    if (N % 2 == 0) t = fma(P.EBm[D][i], f[N / 2], t);
+    rows[i] = s + t;
+    rows[N - i] = s - t;
+  }
+  if (N % 2 == 0) {
+    double m = P.EM[D][0] * o[0];
+#pragma unroll
+    for (int l = 1; l < Pp; ++l) m = fma(P.EM[D][l], o[l], m);
+    rows[N / 2] = m;
   }
 }
 
+// start + sum_l Dm[d][a][l] f[l] as one FMA chain (N+1 operations).
 template <int N, int D>
-__device__ __forceinline__ double contract_row_N(const LineParams& P, const double (&f)[N + 1]) {
+__device__ __forceinline__ double row_from(const LineParams& P, int a, const double (&f)[N + 1],
+                                           double start) {
+  double acc = start;
+#pragma unroll
+  for (int l = 0; l <= N; ++l) acc = fma(P.Dm[D][a][l], f[l], acc);
+  return acc;
+}
+
+template <int N, int D>
+__device__ __forceinline__ double row_N(const LineParams& P, const double (&f)[N + 1]) {
   double acc = P.Dm[D][N][0] * f[0];
 #pragma unroll
   for (int l = 1; l <= N; ++l) acc = fma(P.Dm[D][N][l], f[l], acc);
@@ -109,7 +168,7 @@ __device__ __forceinline__ double contract_row_N(const LineParams& P, const doub
 
 // ---------------------------------------------------------------- x lines
 // grid (n_y, n_z), block kXThreads, dynamic shared memory
-// 8 * (5 (n_x + 1) + 5 nseg_x (N + 1)) bytes.
+// 8 * (5 (n_x + 1) + 5 nseg_x) bytes.
 constexpr int kXThreads = 128;
 
 template <int N>
@@ -121,8 +180,10 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
   const long long np = P.np;
   const long long row = (long long)nx * (y + (long long)ny * z);
   const int ld = nx + 1;
-  double* F = sm;             // [5][ld] x-fluxes at the line's nodes (+ periodic wrap slot)
-  double* R = sm + 5 * ld;    // [5][nseg][N+1] one-sided derivatives of every segment
+  // F [5][ld]: x-fluxes of the line's nodes (+ periodic wrap slot); later
+  // each segment's one-sided rows 0..N-1 in place.  RN [5][nseg]: row N.
+  double* F = sm;
+  double* RN = sm + 5 * ld;
   const double rho0 = __ldg(B.base + z);
   const double Th0 = __ldg(B.base + nz + z);
   const double p0 = __ldg(B.base + 2 * nz + z);
@@ -134,7 +195,7 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
     const long long I = row + i;
     const double rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
     const double tp = q[4 * np + I];
-    const double ir = 1.0 / (rho0 + rp);
+    const double ir = rcp_newton(rho0 + rp);
     const double u = mu * ir, v = mv * ir, w = mw * ir;
     const double pp = p0 * eos_phi(P, tp * iTh0);
     const double Th = Th0 + tp;
@@ -156,19 +217,33 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
   }
   __syncthreads();
 
-  // one element segment per thread: (N+1)^2 contraction per flux component
-  for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+  // one element segment per thread: even/odd contraction per flux component;
+  // every segment is read before any is overwritten (the loop below keeps
+  // each thread's segments in registers when nseg <= blockDim, the usual
+  // case; otherwise segments are processed in rounds with a barrier)
+  for (int s0 = 0; s0 < nseg; s0 += blockDim.x) {
+    const int s = s0 + threadIdx.x;
+    double rows[5][N + 1];
+    if (s < nseg) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double f[N + 1], rows[N + 1];
+      for (int c = 0; c < 5; ++c) {
+        double f[N + 1];
 #pragma unroll
-      for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
-      contract<N, 0>(P, f, rows);
-#pragma unroll
-      for (int a = 0; a <= N; ++a) R[(c * nseg + s) * (N + 1) + a] = rows[a];
+        for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
+        contract_eo<N, 0>(P, f, rows[c]);
+      }
     }
+    __syncthreads();
+    if (s < nseg) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) F[c * ld + s * N + a] = rows[c][a];
+        RN[c * nseg + s] = rows[c][N];
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   // assemble: face nodes add both one-sided halves, wall nodes double theirs
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -176,17 +251,16 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
     const long long I = row + i;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const double* Rc = R + c * nseg * (N + 1);
       double v;
       if (s == nseg) {                     // last wall node
-        v = Rc[(nseg - 1) * (N + 1) + N];
+        v = RN[c * nseg + nseg - 1];
         v = v + v;
       } else if (a != 0) {
-        v = Rc[s * (N + 1) + a];
+        v = F[c * ld + i];
       } else {
-        const double r0 = Rc[s * (N + 1)];
+        const double r0 = F[c * ld + i];
         const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
-        v = r0 + (left >= 0 ? Rc[left * (N + 1) + N] : r0);
+        v = r0 + (left >= 0 ? RN[c * nseg + left] : r0);
       }
       B.T[c * np + I] = v;
     }
@@ -196,10 +270,8 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
 // ---------------------------------------------------------------- y lines
 // grid (ceil(n_x / blockDim), nchunk, n_z); each thread marches `chunk`
 // element segments along y at its (x, z).
-template <int N>
-__device__ __forceinline__ void flux_y(const LineParams& P, const double* __restrict__ q,
-                                       const double* __restrict__ W, long long np, long long I,
-                                       double Th0, double (&f)[5]) {
+__device__ __forceinline__ void flux_y(const double* __restrict__ q, const double* __restrict__ W,
+                                       long long np, long long I, double Th0, double (&f)[5]) {
   const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
   const double v = W[I], pp = W[2 * np + I];
   f[0] = mv;
@@ -234,42 +306,48 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
 #pragma unroll
     for (int l = 0; l <= N; ++l) {
       double f[5];
-      flux_y<N>(P, q, W, np, nodeI(sp * N + l), Th0, f);
+      flux_y(q, W, np, nodeI(sp * N + l), Th0, f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
     }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = contract_row_N<N, 1>(P, fl[c]);
+    for (int c = 0; c < 5; ++c) carry[c] = row_N<N, 1>(P, fl[c]);
   }
 
   double fc[5][N + 1];
   {
     double f[5];
-    flux_y<N>(P, q, W, np, nodeI(s0 * N), Th0, f);
+    flux_y(q, W, np, nodeI(s0 * N), Th0, f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
   }
+  double* __restrict__ T = B.T;
   for (int s = s0; s < s1; ++s) {
 #pragma unroll
     for (int l = 1; l <= N; ++l) {
       double f[5];
-      flux_y<N>(P, q, W, np, nodeI(s * N + l), Th0, f);
+      flux_y(q, W, np, nodeI(s * N + l), Th0, f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
     }
+    // the segment's running x parts, all loaded before any store
+    double tv[5][N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const long long I = nodeI(s * N + a);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) tv[c][a] = T[c * np + I];
+    }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      double rows[N + 1];
-      contract<N, 1>(P, fc[c], rows);
-      double* Tc = B.T + c * np;
-      const long long I0 = nodeI(s * N);
-      Tc[I0] += rows[0] + (has_left ? carry[c] : rows[0]);
+      // the running x part is the start of each row's FMA chain
+      double t0 = tv[c][0];
+      if (!has_left) t0 = row_from<N, 1>(P, 0, fc[c], t0);   // wall: the row counts twice
+      t0 = row_from<N, 1>(P, 0, fc[c], t0);
+      T[c * np + nodeI(s * N)] = has_left ? t0 + carry[c] : t0;
 #pragma unroll
-      for (int a = 1; a < N; ++a) {
-        const long long I = nodeI(s * N + a);
-        Tc[I] += rows[a];
-      }
-      carry[c] = rows[N];
+      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = row_from<N, 1>(P, a, fc[c], tv[c][a]);
+      carry[c] = row_N<N, 1>(P, fc[c]);
       fc[c][0] = fc[c][N];
     }
     has_left = true;
@@ -277,12 +355,11 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
   if (!P.per[1] && s1 == nseg) {
     const long long I = nodeI(nseg * N);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) B.T[c * np + I] += carry[c] + carry[c];
+    for (int c = 0; c < 5; ++c) T[c * np + I] += carry[c] + carry[c];
   }
 }
 
 // ---------------------------------------------------------------- z lines + sources + stage
-template <int N>
 __device__ __forceinline__ void flux_z(const double* __restrict__ q, const double* __restrict__ W,
                                        long long np, long long I, double Th0, double (&f)[5]) {
   const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
@@ -294,17 +371,13 @@ __device__ __forceinline__ void flux_z(const double* __restrict__ q, const doubl
   f[4] = (Th0 + tp) * w;
 }
 
-// Completes node I at level gz with the z part zpart[5]: tendency
-// L = T + zpart + sources, no-flux walls, then the stage store.
+// Completes node I at level gz given L[5] = T + z part (the assembled flux
+// divergence): sources, no-flux walls, then the stage store.
 __device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs& B, long long I,
-                                            int x, int y, int gz, const double (&zpart)[5],
-                                            bool& bad) {
+                                            int x, int y, int gz, double (&L)[5], bool& bad) {
   const long long np = P.np;
   const double* __restrict__ q = B.q;
   const double rp = q[I], mu = q[np + I], mv = q[2 * np + I];
-  double L[5];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) L[c] = B.T[c * np + I] + zpart[c];
   L[1] = fma(P.f, mv, L[1]);                     // -f k x (rho u): +f rho v
   L[2] = fma(-P.f, mu, L[2]);                    //                 -f rho u
   L[3] = fma(-P.g, rp, L[3]);                    // -rho' g
@@ -352,6 +425,7 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
   const long long col = x + (long long)nx * y;
   const double* __restrict__ q = B.q;
   const double* __restrict__ W = B.W;
+  const double* __restrict__ T = B.T;
   auto lev = [&](int gz) -> int { return gz == nz ? 0 : gz; };
   auto th0 = [&](int gz) -> double { return __ldg(B.base + nz + gz); };
   bool bad = false;
@@ -365,19 +439,19 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
     for (int l = 0; l <= N; ++l) {
       const int gz = lev(sp * N + l);
       double f[5];
-      flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+      flux_z(q, W, np, col + nxy * gz, th0(gz), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
     }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = contract_row_N<N, 2>(P, fl[c]);
+    for (int c = 0; c < 5; ++c) carry[c] = row_N<N, 2>(P, fl[c]);
   }
 
   double fc[5][N + 1];
   {
     const int gz = s0 * N;
     double f[5];
-    flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+    flux_z(q, W, np, col + nxy * gz, th0(gz), f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
   }
@@ -386,35 +460,46 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
     for (int l = 1; l <= N; ++l) {
       const int gz = lev(s * N + l);
       double f[5];
-      flux_z<N>(q, W, np, col + nxy * gz, th0(gz), f);
+      flux_z(q, W, np, col + nxy * gz, th0(gz), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
     }
-    double rows[5][N + 1];
+    // the segment's x + y parts, all loaded before any store
+    double tv[5][N];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) contract<N, 2>(P, fc[c], rows[c]);
+    for (int a = 0; a < N; ++a) {
+      const long long I = col + nxy * (s * N + a);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) tv[c][a] = T[c * np + I];
+    }
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const int gz = s * N + a;
-      double zp[5];
+      const long long I = col + nxy * gz;
+      double L[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c)
-        zp[c] = a == 0 ? rows[c][0] + (has_left ? carry[c] : rows[c][0]) : rows[c][a];
-      finish_node(P, B, col + nxy * gz, x, y, gz, zp, bad);
+      for (int c = 0; c < 5; ++c) {
+        double t = tv[c][a];
+        if (a == 0 && !has_left) t = row_from<N, 2>(P, 0, fc[c], t);  // wall: the row counts twice
+        t = row_from<N, 2>(P, a, fc[c], t);
+        L[c] = (a == 0 && has_left) ? t + carry[c] : t;
+      }
+      finish_node(P, B, I, x, y, gz, L, bad);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      carry[c] = rows[c][N];
+      carry[c] = row_N<N, 2>(P, fc[c]);
       fc[c][0] = fc[c][N];
     }
     has_left = true;
   }
   if (!P.per[2] && s1 == nseg) {
     const int gz = nseg * N;
-    double zp[5];
+    const long long I = col + nxy * gz;
+    double L[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) zp[c] = carry[c] + carry[c];
-    finish_node(P, B, col + nxy * gz, x, y, gz, zp, bad);
+    for (int c = 0; c < 5; ++c) L[c] = T[c * np + I] + (carry[c] + carry[c]);
+    finish_node(P, B, I, x, y, gz, L, bad);
   }
   if (bad) *B.flag = 1;
 }

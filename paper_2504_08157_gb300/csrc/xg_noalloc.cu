@@ -114,8 +114,7 @@ extern "C" xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, cons
   xg::LineParams P;
   xg::fill_line_params(d, geo, &P);
   int chunk_y, nchunk_y, chunk_z, nchunk_z;
-  xg::choose_chunks(d->nel[1], (long long)geo.n[0] * geo.n[2], sms, &chunk_y, &nchunk_y);
-  xg::choose_chunks(d->nel[2], (long long)geo.n[0] * geo.n[1], sms, &chunk_z, &nchunk_z);
+  xg::plan_marches(d, geo, sms, &chunk_y, &nchunk_y, &chunk_z, &nchunk_z);
 
   xg::StageBufs B;
   B.q = q;

@@ -63,19 +63,19 @@ inline void lgl_derivative(int N, double D[kMaxOrder + 1][kMaxOrder + 1]) {
     }
 }
 
-// Binomial coefficients C(gamma, k), k = 1..12, of (1+x)^gamma - 1 and the
-// largest |x| (<= 0.1) for which the truncation error after 12 terms stays
-// below 2^-56 of the sum: |R| <= |C(gamma,13)| |x|^13 / (1 - |x|) (the
-// coefficients decrease in magnitude for 1 < gamma < 2) against a sum of at
-// least 0.9 gamma |x|.
+// Binomial coefficients C(gamma, k), k = 1..K (K = kEosTerms), of
+// (1+x)^gamma - 1 and the largest |x| (<= 0.1) for which the truncation
+// error after K terms stays below 2^-56 of the sum:
+// |R| <= |C(gamma,K+1)| |x|^(K+1) / (1 - |x|) (the coefficients decrease in
+// magnitude for 1 < gamma < 2) against a sum of at least 0.9 gamma |x|.
 inline void eos_series(double gamma, double* c, double* xmax) {
   long double ck = 1.0L;
   for (int k = 1; k <= kEosTerms; ++k) {
     ck = ck * ((long double)gamma - (k - 1)) / k;
     c[k - 1] = (double)ck;
   }
-  long double c13 = fabsl(ck * ((long double)gamma - kEosTerms) / (kEosTerms + 1));
-  long double bound = ldexpl(1.0L, -56) * 0.9L * gamma * 0.9L / (c13 > 0 ? c13 : 1e-300L);
+  long double cK1 = fabsl(ck * ((long double)gamma - kEosTerms) / (kEosTerms + 1));
+  long double bound = ldexpl(1.0L, -56) * 0.9L * gamma * 0.9L / (cK1 > 0 ? cK1 : 1e-300L);
   long double xm = powl(bound, 1.0L / kEosTerms);
   *xmax = (double)(xm < 0.1L ? xm : 0.1L);
 }
@@ -110,7 +110,7 @@ inline xg_status check_desc(const xg_mesh_desc* d, MeshGeom* g) {
   }
   g->np = (long long)g->n[0] * g->n[1] * g->n[2];
   // one x-line per CTA: its fluxes and segment derivatives in shared memory
-  g->xsmem = sizeof(double) * (5 * (size_t)(g->n[0] + 1) + 5 * (size_t)d->nel[0] * (N + 1));
+  g->xsmem = sizeof(double) * (5 * (size_t)(g->n[0] + 1) + 5 * (size_t)d->nel[0]);
   if (g->xsmem > 220 * 1024) return XG_ERR_UNSUPPORTED;
   if (g->n[1] > 65535 || g->n[2] > 65535) return XG_ERR_UNSUPPORTED;  // grid y/z limits
   return XG_OK;
@@ -131,6 +131,17 @@ inline void fill_line_params(const xg_mesh_desc* d, const MeshGeom& g, LineParam
       const double face = (a == 0 || a == N) ? 0.5 : 1.0;
       for (int l = 0; l <= N; ++l) P->Dm[k][a][l] = -(2.0 / h) * face * D[a][l];
     }
+    // even/odd split (the LGL matrix is centro-antisymmetric,
+    // D[N-i][N-l] = -D[i][l]; the halved rows 0 and N keep that property)
+    const int Pp = (N + 1) / 2;
+    for (int i = 0; i < Pp; ++i) {
+      for (int l = 0; l < Pp; ++l) {
+        P->EA[k][i][l] = 0.5 * (P->Dm[k][i][l] - P->Dm[k][i][N - l]);
+        P->EB[k][i][l] = 0.5 * (P->Dm[k][i][l] + P->Dm[k][i][N - l]);
+      }
+      P->EBm[k][i] = (N % 2 == 0) ? P->Dm[k][i][N / 2] : 0.0;
+      P->EM[k][i] = (N % 2 == 0) ? P->Dm[k][N / 2][i] : 0.0;
+    }
   }
   P->np = g.np;
   const double gamma = d->cp / d->cv;
@@ -140,16 +151,39 @@ inline void fill_line_params(const xg_mesh_desc* d, const MeshGeom& g, LineParam
   P->g = d->g;
 }
 
-// Chunk of element segments per marching thread: enough threads for about
-// 12 warps per SM sub-partition on the device, at most all segments.
-inline void choose_chunks(int nseg, long long columns, int sms, int* chunk, int* nchunk) {
-  long long warps = ((columns + 31) / 32);
-  long long want = (long long)sms * 4 * 12;
-  long long k = (want + warps - 1) / (warps > 0 ? warps : 1);
-  if (k < 1) k = 1;
-  if (k > nseg) k = nseg;
-  *chunk = (int)((nseg + k - 1) / k);
-  *nchunk = (nseg + *chunk - 1) / *chunk;
+// Element segments per marching thread of k_line_y / k_line_z.  A launch
+// has items_per_chunk CTAs for every chunk of the line.  The kernels are
+// bound by the FP64 pipe of each SM, which its resident CTAs share, so the
+// launch lasts about as long as the SM given the most CTAs: ceil(items /
+// SMs) chunks, each one chunk of segments plus the halo segment a chunk
+// start recomputes (about a third of a segment).  The chunk count with the
+// smallest such makespan wins.
+inline void choose_chunks(int nseg, long long items_per_chunk, long long sms, bool periodic,
+                          int* chunk, int* nchunk) {
+  if (sms < 1) sms = 1;
+  double best = 1e300;
+  *chunk = nseg;
+  *nchunk = 1;
+  for (int k = 1; k <= nseg; ++k) {
+    const int c = (nseg + k - 1) / k;
+    const int nk = (nseg + c - 1) / c;
+    if (nk != k) continue;
+    const long long per_sm = (items_per_chunk * nk + sms - 1) / sms;
+    const double cost = (double)per_sm * (c + ((nk > 1 || periodic) ? 0.3 : 0.0));
+    if (cost < best - 1e-9) {
+      best = cost;
+      *chunk = c;
+      *nchunk = nk;
+    }
+  }
+}
+
+// Chunking of both marching kernels for a mesh on a device with `sms` SMs.
+inline void plan_marches(const xg_mesh_desc* d, const MeshGeom& g, int sms, int* chunk_y,
+                         int* nchunk_y, int* chunk_z, int* nchunk_z) {
+  const long long xblocks = (g.n[0] + 127) / 128;
+  choose_chunks(d->nel[1], xblocks * g.n[2], sms, d->periodic[1] != 0, chunk_y, nchunk_y);
+  choose_chunks(d->nel[2], xblocks * g.n[1], sms, d->periodic[2] != 0, chunk_z, nchunk_z);
 }
 
 }  // namespace xg

@@ -23,7 +23,7 @@ XG_FP64, XG_FP32 = 0, 1
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
+           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -81,6 +81,8 @@ def library():
     lib.xg_kernel_times.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(LL), I]
     lib.xg_rhs_noalloc.restype = I
     lib.xg_rhs_noalloc.argtypes = [ctypes.POINTER(xg_mesh_desc), P, P, P, P, P, P]
+    lib.xg_reciprocal.restype = I
+    lib.xg_reciprocal.argtypes = [P, P, LL, P]
     lib.xg_destroy.restype = None
     lib.xg_destroy.argtypes = [P]
     _lib = lib
@@ -229,6 +231,16 @@ def xg_rhs_noalloc(desc, q, rho0, rhotheta0, S_theta, dqdt, stream=None):
         raise ValueError("xg_rhs_noalloc takes device arrays only")
     _check(library().xg_rhs_noalloc(ctypes.byref(desc), pq, ptrs[0][0], ptrs[1][0], ptrs[2][0],
                                     ptrs[3][0], _stream(stream, sq)), "xg_rhs_noalloc")
+
+
+def xg_reciprocal(x, out, stream=None):
+    """The library's FP64 reciprocal applied to device values (test hook)."""
+    px, wx, sx = _ptr(x)
+    po, wo, _ = _ptr(out, writable=True)
+    if wx != XG_DEVICE or wo != XG_DEVICE:
+        raise ValueError("xg_reciprocal takes device arrays")
+    n = x.numel() if hasattr(x, "numel") else len(x)
+    _check(library().xg_reciprocal(px, po, int(n), _stream(stream, sx)), "xg_reciprocal")
 
 
 def xg_destroy(ctx):
