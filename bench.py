@@ -3,7 +3,10 @@
 Default workload (the cyclone box): 1024 x 1024 x 20 km, 128 x 128 x 16
 order-4 elements, doubly periodic sides, no-flux bottom and top
 (512 x 512 x 65 = 17,039,360 nodes), stable sounding, f-plane, vortex and
-ring-plus-cells heating, FP64, dt = 0.1 s.  One bench step is one SSP-RK3
+ring-plus-cells heating, dt = 0.1 s.  The timed arm is the FP64-accurate
+double-float path (--precision df64, the default); the same line reports
+plain native FP64 on the same workload and GPU, and the relative L2 error
+of both against the FP64 oracle.  One bench step is one SSP-RK3
 step = three passes of the whole hot path (each pass: primitives, fluxes,
 sum-factorised derivatives, DSS, inverse mass, sources, walls, stage
 update), so
@@ -42,7 +45,8 @@ sys.path.insert(0, ROOT)
 METRIC = "RK-stage GDOF/s vs plain FP64 at stated L2 error; % of HBM roofline"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", "xg_kernels.cuh")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", f)
+               for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh")]
 KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
@@ -77,12 +81,20 @@ def flops_per_node(kernel, N):
     raise KeyError(kernel)
 
 
+def kernel_source_sha():
+    """sha256 prefix over the kernel sources (a capture is valid only for them)."""
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_per_launch(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     vals = {}
     for line in open(TRAFFIC_FILE):
         p = line.split()
@@ -225,14 +237,14 @@ def time_oracle(wl, min_seconds=10.0, max_steps=50):
     return dof_u * 3 * steps / dt / 1e9, steps, dt, q
 
 
-def oracle_error_of_gpu(wl, xg, torch, dev):
-    """Largest relative L2 over variables between one GPU right-hand side and
-    the oracle's on the CPU sample."""
+def oracle_error_of_gpu(wl, xg, torch, dev, precision):
+    """Relative L2 per variable between one GPU right-hand side and the
+    oracle's on the CPU sample."""
     from oracle import euler as E, mesh as M
     m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"])
     ref = E.rhs(m, wl["q"], E.Base(wl["rho0"], wl["Theta0"]), wl["S_theta"],
                 E.Physics(**wl["phys"]))
-    ctx = make_ctx(xg, torch, wl, dev)
+    ctx = make_ctx(xg, torch, wl, dev, precision)
     try:
         out = torch.empty((5, xg.xg_mesh_np(ctx)), dtype=torch.float64, device=dev)
         xg.xg_rhs(ctx, out)
@@ -240,16 +252,16 @@ def oracle_error_of_gpu(wl, xg, torch, dev):
     finally:
         xg.xg_destroy(ctx)
     err = [np.linalg.norm(got[v] - ref[v]) / max(np.linalg.norm(ref[v]), 1e-300) for v in range(5)]
-    return float(max(err))
+    return [float("%.3e" % e) for e in err]
 
 
 # ------------------------------------------------------------------ GPU arm
 
-def make_ctx(xg, torch, wl, dev):
+def make_ctx(xg, torch, wl, dev, precision=0):
     ph = wl["phys"]
     ctx = xg.xg_mesh_create(xg.mesh_desc(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"],
                                          f=ph["f"], g=ph["g"], R=ph["R"], cp=ph["cp"],
-                                         cv=ph["cv"], p_a=ph["p_a"]))
+                                         cv=ph["cv"], p_a=ph["p_a"], precision=precision))
     q = torch.from_numpy(wl["q"]).to(dev)
     xg.xg_set_state(ctx, q, torch.from_numpy(wl["rho0"]).to(dev),
                     torch.from_numpy(wl["Theta0"]).to(dev))
@@ -257,6 +269,44 @@ def make_ctx(xg, torch, wl, dev):
         xg.xg_set_forcing(ctx, torch.from_numpy(wl["S_theta"]).to(dev))
     torch.cuda.synchronize()
     return ctx
+
+
+# Bytes each line kernel must move per node given its inputs and outputs
+# (8 bytes per value in both precisions): x reads q (5) and writes W (3) and
+# T (5); y reads 4 components of q, v and p', and reads and writes T; z reads
+# q (5), w and p', T (5), S and -- in stages 2 and 3 -- q^n (5), and writes
+# the stage output (5).
+KERNEL_BYTES_PER_NODE = {"k_line_x": 8 * (5 + 3 + 5), "k_line_y": 8 * (4 + 2 + 5 + 5),
+                         "k_line_z": 8 * (5 + 2 + 5 + 1 + 5 * 2 / 3 + 5)}
+# The method's own traffic per node and stage: q and S in,
+# q out, plus q^n in stages 2 and 3.
+STAGE_BYTES_PER_NODE = (88 + 128 + 128) / 3.0
+
+
+def timed_steps(xg, torch, ctx, dt, K, Wm, stream, world, local, sample_clocks):
+    """W warm-up steps, then K steps timed with CUDA events on `stream`
+    (barrier and synchronize on both sides), with per-kernel event times."""
+    xg.xg_step(ctx, dt, Wm, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    xg.xg_profile(ctx, 1)
+    xg.xg_kernel_times(ctx, reset=True)
+    clocks = ClockSampler(local) if sample_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xg.xg_step(ctx, dt, K, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    xg.xg_profile(ctx, 0)
+    kms, klaunch = xg.xg_kernel_times(ctx, reset=True)
+    return reduce_max(e0.elapsed_time(e1), world), kms, klaunch, clk
 
 
 def run_xg(args, world, rank, local):
@@ -270,55 +320,42 @@ def run_xg(args, world, rank, local):
     build.build()
     wl = workload(args.workload, args.nel)
     cfg = describe(wl)
-    ctx = make_ctx(xg, torch, wl, dev)
+    prec = {"fp64": xg.XG_FP64, "df64": xg.XG_DF64}[args.precision]
     stream = torch.cuda.current_stream(dev)
     dt = wl["dt"]
     K, Wm = args.steps, args.warmup
-
-    xg.xg_step(ctx, dt, Wm, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    xg.xg_profile(ctx, 1)
-    xg.xg_kernel_times(ctx, reset=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    xg.xg_step(ctx, dt, K, stream=stream.cuda_stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    xg.xg_profile(ctx, 0)
-    ms = e0.elapsed_time(e1)
-    kms, klaunch = xg.xg_kernel_times(ctx, reset=True)
-    ms_max = reduce_max(ms, world)
     dof_u, dof_p = cfg["dof_unique"], cfg["dof_paper"]
-    value = dof_u * 3 * K * world / (ms_max / 1e3) / 1e9
+    gdof = lambda ms, k: dof_u * 3 * k * world / (ms / 1e3) / 1e9
+
+    ctx = make_ctx(xg, torch, wl, dev, prec)
+    ms_max, kms, klaunch, clk = timed_steps(xg, torch, ctx, dt, K, Wm, stream, world, local, True)
+    value = gdof(ms_max, K)
 
     # roofline of the dominant kernel (largest share of device time)
     k = int(np.argmax(kms))
     name = KERNELS[k]
     avg_ms = kms[k] / max(klaunch[k], 1)
-    flops = flops_per_node(name, wl["N"]) * cfg["nodes"]
-    achieved = flops / (avg_ms / 1e3) / 1e12
-    traffic = traffic_per_launch(name)
-    roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
-            "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-            "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "share": round(kms[k] / max(sum(kms), 1e-30), 4),
-            "kernel_ms_per_launch": {KERNELS[i]: round(kms[i] / max(klaunch[i], 1), 4)
-                                     for i in range(3)}}
-    # the same stage time against the HBM roofline (algorithmic bytes)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    stage_bytes = cfg["nodes"] * (88 + 128 + 128) / 3.0
+    per_launch = {KERNELS[i]: round(kms[i] / max(klaunch[i], 1), 4) for i in range(3)}
+    if prec == xg.XG_FP64:
+        flops = flops_per_node(name, wl["N"]) * cfg["nodes"]
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic_per_launch(name),
+                "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        nbytes = KERNEL_BYTES_PER_NODE[name] * cfg["nodes"]
+        achieved = nbytes / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": "k_df_" + name[2:], "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": traffic_per_launch("k_df_" + name[2:]),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+                "bytes_per_node": KERNEL_BYTES_PER_NODE[name]}
+    roof.update({"share": round(kms[k] / max(sum(kms), 1e-30), 4), "kernel_ms_per_launch": per_launch})
     stage_s = ms_max / 1e3 / (3 * K)
-    hbm_frac = stage_bytes / stage_s / 1e9 / hbm
+    hbm_frac = cfg["nodes"] * STAGE_BYTES_PER_NODE / stage_s / 1e9 / hbm
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -342,23 +379,43 @@ def run_xg(args, world, rank, local):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": Ke}
     xg.xg_destroy(ctx)
 
-    cpu = None
+    # plain FP64 on the same workload, same GPU (the comparison the metric asks for)
+    plain = None
+    if prec != xg.XG_FP64 and not args.no_plain:
+        Kp = max(1, min(K, 10))
+        ctxp = make_ctx(xg, torch, wl, dev, xg.XG_FP64)
+        msp, kmsp, klp, _ = timed_steps(xg, torch, ctxp, dt, Kp, 3, stream, world, local, False)
+        xg.xg_destroy(ctxp)
+        plain = {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": "f64",
+                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
+                 "kernel_ms_per_launch": {KERNELS[i]: round(kmsp[i] / max(klp[i], 1), 4)
+                                          for i in range(3)}}
+
+    cpu, l2 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sw = cpu_sample_workload(args.workload)
-        gdof, steps, secs, _ = time_oracle(sw)
-        err = oracle_error_of_gpu(sw, xg, torch, dev)
-        cpu = {"value": round(gdof, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+        g, steps, secs, _ = time_oracle(sw)
+        l2 = {"df64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_DF64),
+              "fp64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP64),
+              "what": "relative L2 difference of one GPU right-hand side from the FP64 oracle "
+                      "on the CPU sample, per variable (rho', rho u, rho v, rho w, Theta'); "
+                      "at the vortex state the rho' and Theta' tendencies are residuals of "
+                      "cancelling flux derivatives, which magnifies their relative error"}
+        cpu = {"value": round(g, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
                "sample": "%s %dx%dx%d N=%d, %d SSP-RK3 steps in %.1f s (numpy, 1 thread)"
-                         % (sw["name"], *sw["nel"], sw["N"], steps, secs),
-               "gpu_rhs_rel_l2_vs_oracle": err}
+                         % (sw["name"], *sw["nel"], sw["N"], steps, secs)}
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
                "steps": K, "warmup": Wm, "ms_per_step": round(ms_max / K, 4),
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "impl": "xg",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if prec == xg.XG_FP64 else "f32x2",
+               "precision": args.precision, "data": "synthetic", "impl": "xg",
                "config": cfg,
                "gdof_paper_convention": round(dof_p * 3 * K * world / (ms_max / 1e3) / 1e9, 4),
+               "plain_fp64": plain,
+               "speedup_vs_plain_fp64": round(value / plain["value"], 3) if plain else None,
+               "l2_error_vs_oracle": l2,
                "hbm_roofline_frac": round(hbm_frac, 4),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(sum(klaunch))}
@@ -421,6 +478,11 @@ def main():
     ap.add_argument("--workload", choices=["tc", "bubble"], default="tc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "df64"], default="df64",
+                    help="df64: FP64-accurate double-float on the FP32 pipes (default); "
+                         "fp64: native FP64")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain-FP64 comparison run")
     ap.add_argument("--nel", type=int, nargs=3, default=None,
                     help="element counts of a smaller cyclone box (same spacing), for profiling")
     args = ap.parse_args()

@@ -63,14 +63,18 @@ typedef enum {
 } xg_status;
 
 enum { XG_HOST = 0, XG_DEVICE = 1 };
-enum { XG_FP64 = 0, XG_FP32 = 1 };
+enum { XG_FP64 = 0, XG_FP32 = 1, XG_DF64 = 2 };
 
 /* Problem statement (Sec. 2.1-2.2, Sec. 4.1):
  *   nel[3]      elements per direction, >= 1
  *   order       polynomial order N of the LGL basis, 1 <= N <= 8
  *   lo, hi      box corners in metres, hi > lo
  *   periodic    per direction: 1 periodic, 0 no-flux walls
- *   precision   XG_FP64 (state and arithmetic in FP64)
+ *   precision   XG_FP64: state and arithmetic in native FP64;
+ *               XG_DF64: FP64-accurate "double-float" arithmetic (each value
+ *               an unevaluated pair of floats, 48-bit significand) on the
+ *               FP32 pipes, with the state kept in that form on the device;
+ *               the ABI still takes and returns FP64 arrays
  *   f_coriolis  f-plane Coriolis parameter (s^-1)
  *   g, R, cp, cv, p_a   gravity, dry-air gas constant, heat capacities and
  *               reference surface pressure of Eq. 1 and Eq. 3 (SI units) */
@@ -94,8 +98,8 @@ const char* xg_status_str(xg_status s);
  * device buffer of the path (owned by the context).  On success *out is a
  * new context; on failure *out is NULL.  Errors: XG_ERR_ARG (NULL, nel < 1,
  * order outside [1, 8], hi <= lo, non-positive constants),
- * XG_ERR_UNSUPPORTED (precision other than XG_FP64, or a line of more nodes
- * than one CTA stages in shared memory), XG_ERR_OOM, XG_ERR_CUDA. */
+ * XG_ERR_UNSUPPORTED (precision other than XG_FP64 or XG_DF64, or a line of
+ * more nodes than one CTA stages in shared memory), XG_ERR_OOM, XG_ERR_CUDA. */
 xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out);
 
 /* Number of global (unique) nodes Np = n_x n_y n_z. */
@@ -185,8 +189,8 @@ void xg_destroy(xg_ctx* ctx);
  * returns without waiting; the reference values must be positive (this
  * entry point cannot check device data without waiting for it).
  * Errors: XG_ERR_ARG (NULL pointer, invalid description), XG_ERR_UNSUPPORTED
- * (mesh too large for the scratch, or a description this build cannot run),
- * XG_ERR_CUDA. */
+ * (mesh too large for the scratch, a precision other than XG_FP64, or a
+ * description this build cannot run), XG_ERR_CUDA. */
 xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, const double* rho0,
                          const double* rhotheta0, const double* S_theta, double* dqdt,
                          void* stream);

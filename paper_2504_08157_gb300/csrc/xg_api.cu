@@ -15,10 +15,14 @@
 
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
+#include "xg_kernels_df.cuh"
 #include "xg_setup.h"
 
+using xg::DfBufs;
+using xg::DfParams;
 using xg::LineParams;
 using xg::StageBufs;
+using xg::df;
 
 struct xg_ctx {
   xg_mesh_desc d;
@@ -26,6 +30,8 @@ struct xg_ctx {
   long long np;
   int dev;
   LineParams P;
+  DfParams Pdf;          // launch constants of the double-float kernels
+  bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
   double* A = nullptr;   // q^n (the state)
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer
@@ -57,6 +63,28 @@ __global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ o
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     out[i] = xg::rcp_newton(x[i]);
+}
+
+}  // namespace
+
+namespace xg {
+__global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_from_double(in[i]);
+}
+__global__ void k_from_df(const df* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_to_double(in[i]);
+}
+}  // namespace xg
+
+namespace {
+
+unsigned conv_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return (unsigned)(b < 16384 ? b : 16384);
 }
 
 xg_status fail_cuda(xg_ctx* c, cudaError_t e, const char* what) {
@@ -121,7 +149,41 @@ template <int N>
 cudaError_t configure_n(xg_ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(xg::k_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)c->xsmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(xg::k_df_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)c->xsmem);
   return e;
+}
+
+template <int N>
+void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
+  dim3 gx(c->n[1], c->n[2]);
+  prof_mark(c, 0, false, st);
+  xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
+  prof_mark(c, 0, true, st);
+  dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
+  prof_mark(c, 1, false, st);
+  xg::k_df_line_y<N><<<gy, 128, 0, st>>>(c->Pdf, B, c->chunk_y);
+  prof_mark(c, 1, true, st);
+  dim3 gz((c->n[0] + 127) / 128, c->nchunk_z, c->n[1]);
+  prof_mark(c, 2, false, st);
+  xg::k_df_line_z<N><<<gz, 128, 0, st>>>(c->Pdf, B, c->chunk_z);
+  prof_mark(c, 2, true, st);
+}
+
+cudaError_t launch_df_stage(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
+  switch (c->d.order) {
+    case 1: launch_df_stage_n<1>(c, B, st); break;
+    case 2: launch_df_stage_n<2>(c, B, st); break;
+    case 3: launch_df_stage_n<3>(c, B, st); break;
+    case 4: launch_df_stage_n<4>(c, B, st); break;
+    case 5: launch_df_stage_n<5>(c, B, st); break;
+    case 6: launch_df_stage_n<6>(c, B, st); break;
+    case 7: launch_df_stage_n<7>(c, B, st); break;
+    case 8: launch_df_stage_n<8>(c, B, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stage(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
@@ -171,6 +233,45 @@ StageBufs make_bufs(xg_ctx* c, const double* q, const double* qn, double* out, d
   return B;
 }
 
+// One pass of the hot path: the tendency of q, stored as dq/dt (rhs_only)
+// or combined as out = alpha qn + beta (q + dt L(q)).  Buffers are device
+// arrays of the context's precision.
+cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, double dt,
+                      double alpha, double beta, int rhs_only, cudaStream_t st) {
+  if (!c->dfm)
+    return launch_stage(c, make_bufs(c, (const double*)q, (const double*)qn, (double*)out, dt,
+                                     alpha, beta, rhs_only), st);
+  DfBufs B;
+  B.q = (const df*)q;
+  B.qn = (const df*)qn;
+  B.out = (df*)out;
+  B.W = (df*)c->W;
+  B.T = (df*)c->T;
+  B.S = c->has_forcing ? (const df*)c->S : nullptr;
+  B.base = (const df*)c->base;
+  B.flag = c->flag;
+  B.dt = xg::split_df(dt);
+  B.alpha = xg::split_df(alpha);
+  B.beta = xg::split_df(beta);
+  B.bdt = xg::split_df((double)((long double)beta * (long double)dt));
+  B.rhs_only = rhs_only;
+  return launch_df_stage(c, B, st);
+}
+
+// Device FP64 array -> the context's device representation (n values).
+cudaError_t import_values(xg_ctx* c, const double* src, void* dst, long long n, cudaStream_t st) {
+  if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+  xg::k_to_df<<<conv_blocks(n), 256, 0, st>>>(src, (df*)dst, n);
+  return cudaGetLastError();
+}
+
+// The context's device representation -> device FP64 array.
+cudaError_t export_values(xg_ctx* c, const void* src, double* dst, long long n, cudaStream_t st) {
+  if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+  xg::k_from_df<<<conv_blocks(n), 256, 0, st>>>((const df*)src, dst, n);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -212,6 +313,8 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
   if (sms <= 0) sms = 1;
 
   xg::fill_line_params(d, geo, &c->P);
+  c->dfm = d->precision == XG_DF64;
+  if (c->dfm) xg::fill_df_params(c->P, &c->Pdf);
   xg::plan_marches(d, geo, sms, &c->chunk_y, &c->nchunk_y, &c->chunk_z, &c->nchunk_z);
 
   const size_t vec = sizeof(double) * (size_t)np;
@@ -281,14 +384,28 @@ xg_status xg_set_state(xg_ctx* c, const double* q, const double* rho0, const dou
       hb[2 * nz + k] = c->d.p_a * pow(c->d.R * t0[k] / c->d.p_a, gamma);  // Eq. 3
       hb[3 * nz + k] = 1.0 / t0[k];
     }
+    if (c->dfm) {  // the same table as double-float pairs (8 bytes each, in place)
+      for (int k = 0; k < 4 * nz; ++k) {
+        const df v = xg::split_df(hb[k]);
+        memcpy(hb + k, &v, sizeof(df));
+      }
+    }
     cudaError_t e = cudaMemcpyAsync(c->base, hb, sizeof(double) * 4 * nz, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     free(hb);
     if (e != cudaSuccess) return fail_cuda(c, e, "xg_set_state reference upload");
     c->has_base = true;
   }
-  XG_CUDA(c, cudaMemcpyAsync(c->A, q, sizeof(double) * 5 * (size_t)c->np,
-                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  const long long n5 = 5 * c->np;
+  if (!c->dfm) {
+    XG_CUDA(c, cudaMemcpyAsync(c->A, q, sizeof(double) * (size_t)n5,
+                               where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  } else if (where == XG_DEVICE) {
+    XG_CUDA(c, import_values(c, q, c->A, n5, st));
+  } else {  // host data goes through the stage buffer B as FP64
+    XG_CUDA(c, cudaMemcpyAsync(c->Bq, q, sizeof(double) * (size_t)n5, cudaMemcpyHostToDevice, st));
+    XG_CUDA(c, import_values(c, c->Bq, c->A, n5, st));
+  }
   c->has_state = true;
   return XG_OK;
 }
@@ -302,8 +419,15 @@ xg_status xg_set_forcing(xg_ctx* c, const double* S, int where, void* stream) {
     c->has_forcing = false;
     return XG_OK;
   }
-  XG_CUDA(c, cudaMemcpyAsync(c->S, S, sizeof(double) * (size_t)c->np,
-                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (!c->dfm) {
+    XG_CUDA(c, cudaMemcpyAsync(c->S, S, sizeof(double) * (size_t)c->np,
+                               where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  } else if (where == XG_DEVICE) {
+    XG_CUDA(c, import_values(c, S, c->S, c->np, st));
+  } else {
+    XG_CUDA(c, cudaMemcpyAsync(c->Cq, S, sizeof(double) * (size_t)c->np, cudaMemcpyHostToDevice, st));
+    XG_CUDA(c, import_values(c, c->Cq, c->S, c->np, st));
+  }
   c->has_forcing = true;
   return XG_OK;
 }
@@ -315,8 +439,12 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
-  StageBufs B = make_bufs(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1);
-  XG_CUDA(c, launch_stage(c, B, st));
+  if (!c->dfm) {
+    XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
+  } else {
+    XG_CUDA(c, run_stage(c, c->A, nullptr, c->Cq, 0.0, 0.0, 1.0, 1, st));
+    XG_CUDA(c, export_values(c, c->Cq, dst, 5 * c->np, st));
+  }
   if (where == XG_HOST) {
     XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
                                cudaMemcpyDeviceToHost, st));
@@ -336,12 +464,9 @@ xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
   for (int it = 0; it < nsteps; ++it) {
-    StageBufs s1 = make_bufs(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0);
-    XG_CUDA(c, launch_stage(c, s1, st));
-    StageBufs s2 = make_bufs(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0);
-    XG_CUDA(c, launch_stage(c, s2, st));
-    StageBufs s3 = make_bufs(c, c->Cq, c->A, c->A, dt, 1.0 / 3.0, 2.0 / 3.0, 0);
-    XG_CUDA(c, launch_stage(c, s3, st));
+    XG_CUDA(c, run_stage(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0, st));
+    XG_CUDA(c, run_stage(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0, st));
+    XG_CUDA(c, run_stage(c, c->Cq, c->A, c->A, dt, 1.0 / 3.0, 2.0 / 3.0, 0, st));
   }
   XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   XG_CUDA(c, cudaStreamSynchronize(st));
@@ -355,8 +480,16 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
   if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  XG_CUDA(c, cudaMemcpyAsync(q, c->A, sizeof(double) * 5 * (size_t)c->np,
-                             where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  const long long n5 = 5 * c->np;
+  if (!c->dfm) {
+    XG_CUDA(c, cudaMemcpyAsync(q, c->A, sizeof(double) * (size_t)n5,
+                               where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  } else if (where == XG_DEVICE) {
+    XG_CUDA(c, export_values(c, c->A, q, n5, st));
+  } else {
+    XG_CUDA(c, export_values(c, c->A, c->Bq, n5, st));
+    XG_CUDA(c, cudaMemcpyAsync(q, c->Bq, sizeof(double) * (size_t)n5, cudaMemcpyDeviceToHost, st));
+  }
   if (where == XG_HOST) XG_CUDA(c, cudaStreamSynchronize(st));
   return XG_OK;
 }

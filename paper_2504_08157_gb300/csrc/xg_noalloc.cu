@@ -91,6 +91,7 @@ extern "C" xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, cons
   xg::MeshGeom geo;
   const xg_status st = xg::check_desc(d, &geo);
   if (st != XG_OK) return st;
+  if (d->precision != XG_FP64) return XG_ERR_UNSUPPORTED;
   const long long np = geo.np;
   const int nz = geo.n[2];
   const unsigned long long need = 8ull * (unsigned long long)np + 4ull * (unsigned long long)nz +

@@ -9,6 +9,7 @@
 
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
+#include "xg_kernels_df.cuh"
 
 namespace xg {
 
@@ -101,7 +102,7 @@ inline xg_status check_desc(const xg_mesh_desc* d, MeshGeom* g) {
   if (!(std::isfinite(d->g) && d->g >= 0.0 && std::isfinite(d->f_coriolis))) return XG_ERR_ARG;
   const double gamma = d->cp / d->cv;
   if (!(gamma > 1.0 && gamma < 2.0)) return XG_ERR_ARG;
-  if (d->precision != XG_FP64) return XG_ERR_UNSUPPORTED;
+  if (d->precision != XG_FP64 && d->precision != XG_DF64) return XG_ERR_UNSUPPORTED;
   const int N = d->order;
   for (int k = 0; k < 3; ++k) {
     long long nk = (long long)N * d->nel[k] + (d->periodic[k] ? 0 : 1);
@@ -151,13 +152,38 @@ inline void fill_line_params(const xg_mesh_desc* d, const MeshGeom& g, LineParam
   P->g = d->g;
 }
 
+// A double split into a double-float pair (host).
+inline df split_df(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+// Launch constants of the double-float line kernels, from the FP64 ones.
+inline void fill_df_params(const LineParams& P, DfParams* Q) {
+  memset(Q, 0, sizeof(*Q));
+  for (int k = 0; k < 3; ++k) {
+    Q->n[k] = P.n[k];
+    Q->nseg[k] = P.nseg[k];
+    Q->per[k] = P.per[k];
+    for (int a = 0; a <= kMaxOrder; ++a)
+      for (int l = 0; l <= kMaxOrder; ++l) Q->Dm[k][a][l] = split_df(P.Dm[k][a][l]);
+  }
+  Q->np = P.np;
+  for (int k = 0; k < 3; ++k) Q->eos_c[k] = split_df(P.eos_c[k]);
+  for (int k = 3; k < kEosTerms; ++k) Q->eos_g[k - 3] = (float)P.eos_c[k];
+  Q->eos_xmax = (float)P.eos_xmax;
+  Q->gamma = P.gamma;
+  Q->f = split_df(P.f);
+  Q->g = split_df(P.g);
+}
+
 // Element segments per marching thread of k_line_y / k_line_z.  A launch
 // has items_per_chunk CTAs for every chunk of the line.  The kernels are
 // bound by the FP64 pipe of each SM, which its resident CTAs share, so the
 // launch lasts about as long as the SM given the most CTAs: ceil(items /
 // SMs) chunks, each one chunk of segments plus the halo segment a chunk
-// start recomputes (about a third of a segment).  The chunk count with the
-// smallest such makespan wins.
+// start recomputes (about a fifth of a segment's work).  The chunk count with
+// the smallest such makespan wins.
 inline void choose_chunks(int nseg, long long items_per_chunk, long long sms, bool periodic,
                           int* chunk, int* nchunk) {
   if (sms < 1) sms = 1;
@@ -169,7 +195,7 @@ inline void choose_chunks(int nseg, long long items_per_chunk, long long sms, bo
     const int nk = (nseg + c - 1) / c;
     if (nk != k) continue;
     const long long per_sm = (items_per_chunk * nk + sms - 1) / sms;
-    const double cost = (double)per_sm * (c + ((nk > 1 || periodic) ? 0.3 : 0.0));
+    const double cost = (double)per_sm * (c + ((nk > 1 || periodic) ? 0.2 : 0.0));
     if (cost < best - 1e-9) {
       best = cost;
       *chunk = c;

@@ -19,12 +19,12 @@ LIB_PATH = os.path.join(HERE, "libxg.so")
 XG_OK, XG_ERR_ARG, XG_ERR_CUDA, XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, \
     XG_ERR_UNSUPPORTED = range(7)
 XG_HOST, XG_DEVICE = 0, 1
-XG_FP64, XG_FP32 = 0, 1
+XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
            "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
-           "XG_FP64", "XG_FP32", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
+           "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
 

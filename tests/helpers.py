@@ -40,7 +40,7 @@ def oracle_steps(wl, nsteps, q=None):
 class GpuRun:
     """One library context for a workload, inputs resident on cuda:0."""
 
-    def __init__(self, wl, device="cuda:0"):
+    def __init__(self, wl, device="cuda:0", precision=0):
         import torch
         from paper_2504_08157_gb300 import xg
         self.xg, self.torch, self.wl = xg, torch, wl
@@ -48,7 +48,7 @@ class GpuRun:
         ph = wl["phys"]
         self.ctx = xg.xg_mesh_create(xg.mesh_desc(
             wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"], f=ph["f"], g=ph["g"],
-            R=ph["R"], cp=ph["cp"], cv=ph["cv"], p_a=ph["p_a"]))
+            R=ph["R"], cp=ph["cp"], cv=ph["cv"], p_a=ph["p_a"], precision=precision))
         self.np = xg.xg_mesh_np(self.ctx)
         self.set_state(wl["q"], with_base=True)
         if wl["S_theta"] is not None:
