@@ -35,6 +35,7 @@ struct xg_ctx {
   double* A = nullptr;   // q^n (the state)
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer
+  double* Dq = nullptr;  // q^{n+1}; swapped with A after every step
   double* W = nullptr;   // [3][np] primitives v, w, p'
   double* T = nullptr;   // [5][np] partial tendency
   double* S = nullptr;   // [np] heating
@@ -161,13 +162,16 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
   prof_mark(c, 0, false, st);
   xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
   prof_mark(c, 0, true, st);
+  constexpr int K = xg::tile_segments(N);
+  const dim3 blk(xg::kTileCols, K * N + 1);
+  const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
   dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
   prof_mark(c, 1, false, st);
   xg::k_df_line_y<N><<<gy, 128, 0, st>>>(c->Pdf, B, c->chunk_y);
   prof_mark(c, 1, true, st);
-  dim3 gz((c->n[0] + 127) / 128, c->nchunk_z, c->n[1]);
+  dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);
   prof_mark(c, 2, false, st);
-  xg::k_df_line_z<N><<<gz, 128, 0, st>>>(c->Pdf, B, c->chunk_z);
+  xg::k_df_tline<N, 2><<<gz, blk, 0, st>>>(c->Pdf, B);
   prof_mark(c, 2, true, st);
 }
 
@@ -319,7 +323,7 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
 
   const size_t vec = sizeof(double) * (size_t)np;
   struct { double** p; size_t bytes; } allocs[] = {
-      {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->W, 3 * vec},
+      {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->Dq, 5 * vec}, {&c->W, 3 * vec},
       {&c->T, 5 * vec}, {&c->S, vec}, {&c->base, sizeof(double) * 4 * (size_t)n[2]}};
   for (auto& a : allocs) {
     e = cudaMalloc((void**)a.p, a.bytes);
@@ -466,7 +470,10 @@ xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   for (int it = 0; it < nsteps; ++it) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0, st));
     XG_CUDA(c, run_stage(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0, st));
-    XG_CUDA(c, run_stage(c, c->Cq, c->A, c->A, dt, 1.0 / 3.0, 2.0 / 3.0, 0, st));
+    XG_CUDA(c, run_stage(c, c->Cq, c->A, c->Dq, dt, 1.0 / 3.0, 2.0 / 3.0, 0, st));
+    double* t = c->A;  // every kernel's arrays stay distinct (no in-place stage)
+    c->A = c->Dq;
+    c->Dq = t;
   }
   XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   XG_CUDA(c, cudaStreamSynchronize(st));
@@ -529,6 +536,7 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->A);
   cudaFree(c->Bq);
   cudaFree(c->Cq);
+  cudaFree(c->Dq);
   cudaFree(c->W);
   cudaFree(c->T);
   cudaFree(c->S);

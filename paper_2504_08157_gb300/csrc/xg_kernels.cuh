@@ -25,7 +25,8 @@
 //   k_line_z  one thread per (x, y) column marching along z; adds the z part,
 //             the sources (-rho' g k, -f k x rho u, rho S_theta), applies
 //             no-flux walls and either stores dq/dt or the fused SSP-RK
-//             stage combination out = alpha q^n + beta (q + dt L(q)).
+//             stage combination out = alpha q^n + beta (q + dt L(q)) into a
+//             buffer distinct from every input.
 //
 // Every arithmetic step is FP64.  The derivative matrices come pre-scaled by
 // -2/h_d (chain rule of the affine map, sign of the divergence) with rows 0
@@ -189,6 +190,8 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
   const double p0 = __ldg(B.base + 2 * nz + z);
   const double iTh0 = __ldg(B.base + 3 * nz + z);
   const double* __restrict__ q = B.q;
+  double* __restrict__ Wo = B.W;
+  double* __restrict__ To = B.T;
 
   // pointwise primitives and x-fluxes, one node per thread (coalesced)
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -199,9 +202,9 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
     const double u = mu * ir, v = mv * ir, w = mw * ir;
     const double pp = p0 * eos_phi(P, tp * iTh0);
     const double Th = Th0 + tp;
-    B.W[I] = v;
-    B.W[np + I] = w;
-    B.W[2 * np + I] = pp;
+    Wo[I] = v;
+    Wo[np + I] = w;
+    Wo[2 * np + I] = pp;
     F[i] = mu;
     F[ld + i] = fma(mu, u, pp);
     F[2 * ld + i] = mv * u;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
         const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
         v = r0 + (left >= 0 ? RN[c * nseg + left] : r0);
       }
-      B.T[c * np + I] = v;
+      To[c * np + I] = v;
     }
   }
 }
@@ -372,11 +375,15 @@ __device__ __forceinline__ void flux_z(const double* __restrict__ q, const doubl
 }
 
 // Completes node I at level gz given L[5] = T + z part (the assembled flux
-// divergence): sources, no-flux walls, then the stage store.
-__device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs& B, long long I,
-                                            int x, int y, int gz, double (&L)[5], bool& bad) {
+// divergence): sources, no-flux walls, then the stage store.  Every array of
+// a launch is distinct (the stage output never overwrites an input), which
+// the __restrict__ qualifiers state so loads can be issued ahead of stores.
+__device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs& B,
+                                            const double* __restrict__ q,
+                                            const double* __restrict__ qn,
+                                            double* __restrict__ out, long long I, int x, int y,
+                                            int gz, double (&L)[5], bool& bad) {
   const long long np = P.np;
-  const double* __restrict__ q = B.q;
   const double rp = q[I], mu = q[np + I], mv = q[2 * np + I];
   L[1] = fma(P.f, mv, L[1]);                     // -f k x (rho u): +f rho v
   L[2] = fma(-P.f, mu, L[2]);                    //                 -f rho u
@@ -388,21 +395,21 @@ __device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs
   if (B.rhs_only) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      B.out[c * np + I] = L[c];
+      out[c * np + I] = L[c];
       bad |= is_nonfinite(L[c]);
     }
   } else if (B.alpha == 0.0) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const double o = fma(B.dt, L[c], q[c * np + I]);
-      B.out[c * np + I] = o;
+      out[c * np + I] = o;
       bad |= is_nonfinite(o);
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const double o = fma(B.alpha, B.qn[c * np + I], B.beta * fma(B.dt, L[c], q[c * np + I]));
-      B.out[c * np + I] = o;
+      const double o = fma(B.alpha, qn[c * np + I], B.beta * fma(B.dt, L[c], q[c * np + I]));
+      out[c * np + I] = o;
       bad |= is_nonfinite(o);
     }
   }
@@ -426,6 +433,8 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
   const double* __restrict__ q = B.q;
   const double* __restrict__ W = B.W;
   const double* __restrict__ T = B.T;
+  const double* __restrict__ qn = B.qn;
+  double* __restrict__ out = B.out;
   auto lev = [&](int gz) -> int { return gz == nz ? 0 : gz; };
   auto th0 = [&](int gz) -> double { return __ldg(B.base + nz + gz); };
   bool bad = false;
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
         t = row_from<N, 2>(P, a, fc[c], t);
         L[c] = (a == 0 && has_left) ? t + carry[c] : t;
       }
-      finish_node(P, B, I, x, y, gz, L, bad);
+      finish_node(P, B, q, qn, out, I, x, y, gz, L, bad);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
     double L[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[c] = T[c * np + I] + (carry[c] + carry[c]);
-    finish_node(P, B, I, x, y, gz, L, bad);
+    finish_node(P, B, q, qn, out, I, x, y, gz, L, bad);
   }
   if (bad) *B.flag = 1;
 }

@@ -2,7 +2,8 @@
 // arithmetic (xg_df.cuh) on the FP32 pipes.
 //
 // Same method, same three-kernel stage (x lines with primitives, y lines,
-// z lines with sources, walls and the SSP-RK stage), same data layout: every
+// z lines with sources, walls and the SSP-RK stage; the z kernel is tiled
+// instead of marching, see k_df_tline), same data layout: every
 // [5][Np] array holds double-float pairs (8 bytes per value, like FP64).
 // The contractions are compensated dot products (Dot2) seeded with the
 // running tendency; additions that can cancel use the accurate double-word
@@ -92,6 +93,8 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
   const df rho0 = B.base[z], Th0 = B.base[nz + z], p0 = B.base[2 * nz + z];
   const df iTh0 = B.base[3 * nz + z];
   const df* __restrict__ q = B.q;
+  df* __restrict__ Wo = B.W;
+  df* __restrict__ To = B.T;
 
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const long long I = row + i;
@@ -101,9 +104,9 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
     const df u = df_mul(mu, ir), v = df_mul(mv, ir), w = df_mul(mw, ir);
     const df pp = df_mul(p0, df_eos_phi(P, df_mul(tp, iTh0)));
     const df Th = df_add(Th0, tp);
-    B.W[I] = v;
-    B.W[np + I] = w;
-    B.W[2 * np + I] = pp;
+    Wo[I] = v;
+    Wo[np + I] = w;
+    Wo[2 * np + I] = pp;
     F[i] = mu;
     F[ld + i] = df_add(df_mul(mu, u), pp);
     F[2 * ld + i] = df_mul(mv, u);
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
         const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
         v = left >= 0 ? df_add(r0, RN[c * nseg + left]) : df_scale2(r0, 2.0f);
       }
-      B.T[c * np + I] = v;
+      To[c * np + I] = v;
     }
   }
 }
@@ -250,21 +253,11 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
 }
 
 // ---------------------------------------------------------------- z lines + sources + stage
-__device__ __forceinline__ void df_flux_z(const df* __restrict__ q, const df* __restrict__ W,
-                                          long long np, long long I, df Th0, df (&f)[5]) {
-  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
-  const df w = W[np + I], pp = W[2 * np + I];
-  f[0] = mw;
-  f[1] = df_mul(mu, w);
-  f[2] = df_mul(mv, w);
-  f[3] = df_add(df_mul(mw, w), pp);
-  f[4] = df_mul(df_add(Th0, tp), w);
-}
-
-__device__ __forceinline__ void df_finish_node(const DfParams& P, const DfBufs& B, long long I,
-                                               int x, int y, int gz, df (&L)[5], bool& bad) {
+__device__ __forceinline__ void df_finish_node(const DfParams& P, const DfBufs& B,
+                                               const df* __restrict__ q, const df* __restrict__ qn,
+                                               df* __restrict__ out, long long I, int x, int y,
+                                               int gz, df (&L)[5], bool& bad) {
   const long long np = P.np;
-  const df* __restrict__ q = B.q;
   const df rp = q[I], mu = q[np + I], mv = q[2 * np + I];
   {
     dacc A = dacc_from(L[1]);
@@ -289,7 +282,7 @@ __device__ __forceinline__ void df_finish_node(const DfParams& P, const DfBufs& 
   if (B.rhs_only) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      B.out[c * np + I] = L[c];
+      out[c * np + I] = L[c];
       bad |= df_nonfinite(L[c]);
     }
   } else if (B.alpha.h == 0.0f) {
@@ -298,116 +291,156 @@ __device__ __forceinline__ void df_finish_node(const DfParams& P, const DfBufs& 
       dacc A = dacc_from(q[c * np + I]);
       dacc_fma(A, B.dt, L[c]);
       const df o = dacc_value(A);
-      B.out[c * np + I] = o;
+      out[c * np + I] = o;
       bad |= df_nonfinite(o);
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      dacc A = dacc_prod(B.alpha, B.qn[c * np + I]);
+      dacc A = dacc_prod(B.alpha, qn[c * np + I]);
       dacc_fma(A, B.beta, q[c * np + I]);
       dacc_fma(A, B.bdt, L[c]);
       const df o = dacc_value(A);
-      B.out[c * np + I] = o;
+      out[c * np + I] = o;
       bad |= df_nonfinite(o);
     }
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(128) k_df_line_z(const DfParams P, const DfBufs B, int chunk) {
-  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const int nseg = P.nseg[2];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= nx) return;
-  const int y = blockIdx.z;
-  const int s0 = blockIdx.y * chunk;
-  const int s1 = min(nseg, s0 + chunk);
-  if (s0 >= s1) return;
-  const long long np = P.np;
-  const long long nxy = (long long)nx * ny;
-  const long long col = x + (long long)nx * y;
-  const df* __restrict__ q = B.q;
-  const df* __restrict__ W = B.W;
-  const df* __restrict__ T = B.T;
-  auto lev = [&](int gz) -> int { return gz == nz ? 0 : gz; };
-  bool bad = false;
-
-  df carry[5];
-  bool has_left = (s0 > 0) || P.per[2];
-  if (has_left) {
-    const int sp = s0 > 0 ? s0 - 1 : nseg - 1;
-    df fl[5][N + 1];
-#pragma unroll
-    for (int l = 0; l <= N; ++l) {
-      const int gz = lev(sp * N + l);
-      df f[5];
-      df_flux_z(q, W, np, col + nxy * gz, B.base[nz + gz], f);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = df_row<N, 2>(P, N, fl[c]);
-  }
-
-  df fc[5][N + 1];
-  {
-    const int gz = s0 * N;
-    df f[5];
-    df_flux_z(q, W, np, col + nxy * gz, B.base[nz + gz], f);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
-  }
-  for (int s = s0; s < s1; ++s) {
-#pragma unroll
-    for (int l = 1; l <= N; ++l) {
-      const int gz = lev(s * N + l);
-      df f[5];
-      df_flux_z(q, W, np, col + nxy * gz, B.base[nz + gz], f);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
-    }
-    df tv[5][N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const long long I = col + nxy * (s * N + a);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) tv[c][a] = T[c * np + I];
-    }
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const int gz = s * N + a;
-      const long long I = col + nxy * gz;
-      df L[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        df t = tv[c][a];
-        if (a == 0 && !has_left) t = df_row_from<N, 2>(P, 0, fc[c], t);
-        t = df_row_from<N, 2>(P, a, fc[c], t);
-        L[c] = (a == 0 && has_left) ? df_add(t, carry[c]) : t;
-      }
-      df_finish_node(P, B, I, x, y, gz, L, bad);
-    }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      carry[c] = df_row<N, 2>(P, N, fc[c]);
-      fc[c][0] = fc[c][N];
-    }
-    has_left = true;
-  }
-  if (!P.per[2] && s1 == nseg) {
-    const int gz = nseg * N;
-    const long long I = col + nxy * gz;
-    df L[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) L[c] = df_add(T[c * np + I], df_scale2(carry[c], 2.0f));
-    df_finish_node(P, B, I, x, y, gz, L, bad);
-  }
-  if (bad) *B.flag = 1;
-}
-
 // FP64 <-> double-float conversion of n values (data entering or leaving).
 __global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, long long n);
 __global__ void k_from_df(const df* __restrict__ in, double* __restrict__ out, long long n);
+
+}  // namespace xg
+
+namespace xg {
+
+// ---------------------------------------------------------------- z lines, tiled
+// (The template also covers y lines; the marching k_df_line_y measured faster
+// there, so only DIR = 2 is launched.)
+// One CTA per (32 x-columns) x (a chunk of K element segments along the line
+// direction DIR: 1 = y, 2 = z) x (the remaining coordinate), one thread per
+// node: block (32, K N + 1), warp = one plane of 32 columns, so every warp
+// does the same kind of work.  All loads of the chunk are issued up front
+// (high memory-level parallelism), the fluxes along DIR go to shared memory
+// -- the chunk's K N + 1 planes plus the N planes of the segment before it
+// (whose last row completes the chunk's first face node) -- and each thread
+// then assembles its own node: y adds its part into T, z adds its part,
+// the sources, walls and the stage store.  Thread row K N handles the
+// chunk's end face: its fluxes close the last segment, and at a wall it
+// also owns the wall node.
+template <int DIR>
+__device__ __forceinline__ void df_flux_dir(const df* __restrict__ q, const df* __restrict__ W,
+                                            long long np, long long I, df Th0, df (&f)[5]) {
+  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+  if (DIR == 1) {
+    const df v = W[I], pp = W[2 * np + I];
+    f[0] = mv;
+    f[1] = df_mul(mu, v);
+    f[2] = df_add(df_mul(mv, v), pp);
+    f[3] = df_mul(mw, v);
+    f[4] = df_mul(df_add(Th0, tp), v);
+  } else {
+    const df w = W[np + I], pp = W[2 * np + I];
+    f[0] = mw;
+    f[1] = df_mul(mu, w);
+    f[2] = df_mul(mv, w);
+    f[3] = df_add(df_mul(mw, w), pp);
+    f[4] = df_mul(df_add(Th0, tp), w);
+  }
+}
+
+constexpr int kTileCols = 32;
+
+__host__ __device__ constexpr int tile_segments(int N) { return N >= 16 ? 1 : 16 / N; }
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_df_tline(const DfParams P, const DfBufs B) {
+  constexpr int K = tile_segments(N);
+  constexpr int NS = K * N + N + 1;            // flux slots: N halo planes + K N + 1
+  __shared__ df Fs[5][NS][kTileCols];
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nd = P.n[DIR];                      // nodes along the line
+  const int nseg = P.nseg[DIR];
+  const bool per = P.per[DIR] != 0;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * kTileCols + tx;
+  const bool xin = x < nx;
+  const int s0 = blockIdx.y * K;
+  const int kc = min(K, nseg - s0);             // segments in this chunk
+  const int other = blockIdx.z;                  // z for y-lines, y for z-lines
+  const long long np = P.np;
+  const long long sd = DIR == 1 ? (long long)nx : (long long)nx * ny;
+  const long long base = DIR == 1 ? x + (long long)nx * ny * other : x + (long long)nx * other;
+  const df* __restrict__ q = B.q;
+  const df* __restrict__ W = B.W;
+  const bool has_left = s0 > 0 || per;
+  auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
+  auto th0 = [&](int g) -> df { return B.base[nz + (DIR == 2 ? g : other)]; };
+
+  // the node this thread owns: planes s0 N + ty for ty < kc N, and the end
+  // wall plane for the extra row of the last chunk of a walled line
+  const int own = s0 * N + ty;
+  const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
+  // fluxes of this thread's plane (the extra row always fills the end face)
+  if (xin && ty <= kc * N) {
+    const int g = plane(own);
+    df f[5];
+    df_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+  }
+  // halo: the N planes of the segment before the chunk
+  if (xin && has_left && ty < N) {
+    const int g = plane((s0 - 1) * N + ty);
+    df f[5];
+    df_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
+  }
+  // inputs of the node's epilogue, loaded before the barrier
+  const long long I = base + sd * (owns ? plane(own) : 0);
+  df t[5];
+  if (owns) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+  }
+  __syncthreads();
+  if (!owns) return;
+
+  // the node's segment k and local index a; the wall node is row N of the last
+  const int k = ty < kc * N ? ty / N : kc - 1;
+  const int a = ty < kc * N ? ty - k * N : N;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    df f[N + 1];
+#pragma unroll
+    for (int l = 0; l <= N; ++l) f[l] = Fs[c][N + k * N + l][tx];
+    if (a == N) {                                   // wall node: its one-sided row counts twice
+      const df r = df_row<N, DIR>(P, N, f);
+      t[c] = df_add(t[c], df_scale2(r, 2.0f));
+    } else if (a > 0) {
+      t[c] = df_row_from<N, DIR>(P, a, f, t[c]);
+    } else if (k > 0 || has_left) {                 // shared face: both one-sided halves
+      df fl[N + 1];
+#pragma unroll
+      for (int l = 0; l <= N; ++l) fl[l] = Fs[c][k * N + l][tx];
+      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
+      t[c] = df_add(t[c], df_row<N, DIR>(P, N, fl));
+    } else {                                        // wall at the line start
+      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
+      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
+    }
+  }
+  if (DIR == 1) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) B.T[c * np + I] = t[c];
+  } else {
+    bool bad = false;
+    const int yy = other, gz = plane(own);
+    df_finish_node(P, B, q, B.qn, B.out, I, x, yy, gz, t, bad);
+    if (bad) *B.flag = 1;
+  }
+}
 
 }  // namespace xg
