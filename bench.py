@@ -320,7 +320,7 @@ def run_xg(args, world, rank, local):
     build.build()
     wl = workload(args.workload, args.nel)
     cfg = describe(wl)
-    prec = {"fp64": xg.XG_FP64, "df64": xg.XG_DF64}[args.precision]
+    prec = {"fp64": xg.XG_FP64, "df64": xg.XG_DF64, "fp32": xg.XG_FP32}[args.precision]
     stream = torch.cuda.current_stream(dev)
     dt = wl["dt"]
     K, Wm = args.steps, args.warmup
@@ -346,16 +346,19 @@ def run_xg(args, world, rank, local):
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic_per_launch(name),
                 "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
-        nbytes = KERNEL_BYTES_PER_NODE[name] * cfg["nodes"]
+        vb = 8 if prec == xg.XG_DF64 else 4          # bytes per stored value
+        kname = ("k_df_" if prec == xg.XG_DF64 else "k_f_") + name[2:]
+        nbytes = KERNEL_BYTES_PER_NODE[name] * vb / 8 * cfg["nodes"]
         achieved = nbytes / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": "k_df_" + name[2:], "bound": "hbm", "achieved": round(achieved, 1),
+        roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": traffic_per_launch("k_df_" + name[2:]),
+                "traffic": traffic_per_launch(kname),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
-                "bytes_per_node": KERNEL_BYTES_PER_NODE[name]}
+                "bytes_per_node": KERNEL_BYTES_PER_NODE[name] * vb / 8}
     roof.update({"share": round(kms[k] / max(sum(kms), 1e-30), 4), "kernel_ms_per_launch": per_launch})
     stage_s = ms_max / 1e3 / (3 * K)
-    hbm_frac = cfg["nodes"] * STAGE_BYTES_PER_NODE / stage_s / 1e9 / hbm
+    hbm_frac = cfg["nodes"] * STAGE_BYTES_PER_NODE * (4 if prec == xg.XG_FP32 else 8) / 8 \
+        / stage_s / 1e9 / hbm
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -379,17 +382,19 @@ def run_xg(args, world, rank, local):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": Ke}
     xg.xg_destroy(ctx)
 
-    # plain FP64 on the same workload, same GPU (the comparison the metric asks for)
-    plain = None
-    if prec != xg.XG_FP64 and not args.no_plain:
+    # the other precisions on the same workload and GPU: plain FP64 (the
+    # comparison the metric asks for) and the FP32 precision form
+    def side_run(p, dtype):
         Kp = max(1, min(K, 10))
-        ctxp = make_ctx(xg, torch, wl, dev, xg.XG_FP64)
-        msp, kmsp, klp, _ = timed_steps(xg, torch, ctxp, dt, Kp, 3, stream, world, local, False)
-        xg.xg_destroy(ctxp)
-        plain = {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": "f64",
-                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
-                 "kernel_ms_per_launch": {KERNELS[i]: round(kmsp[i] / max(klp[i], 1), 4)
-                                          for i in range(3)}}
+        c2 = make_ctx(xg, torch, wl, dev, p)
+        msp, kmsp, klp, _ = timed_steps(xg, torch, c2, dt, Kp, 3, stream, world, local, False)
+        xg.xg_destroy(c2)
+        return {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": dtype,
+                "ms_per_step": round(msp / Kp, 4), "steps": Kp,
+                "kernel_ms_per_launch": {KERNELS[i]: round(kmsp[i] / max(klp[i], 1), 4)
+                                         for i in range(3)}}
+    plain = side_run(xg.XG_FP64, "f64") if prec != xg.XG_FP64 and not args.no_plain else None
+    fp32 = side_run(xg.XG_FP32, "f32") if prec != xg.XG_FP32 and not args.no_plain else None
 
     cpu, l2 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -397,6 +402,7 @@ def run_xg(args, world, rank, local):
         g, steps, secs, _ = time_oracle(sw)
         l2 = {"df64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_DF64),
               "fp64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP64),
+              "fp32": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32),
               "what": "relative L2 difference of one GPU right-hand side from the FP64 oracle "
                       "on the CPU sample, per variable (rho', rho u, rho v, rho w, Theta'); "
                       "at the vortex state the rho' and Theta' tendencies are residuals of "
@@ -409,12 +415,15 @@ def run_xg(args, world, rank, local):
         out = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
                "steps": K, "warmup": Wm, "ms_per_step": round(ms_max / K, 4),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64" if prec == xg.XG_FP64 else "f32x2",
+               "dtype": {xg.XG_FP64: "f64", xg.XG_DF64: "f32x2", xg.XG_FP32: "f32"}[prec],
                "precision": args.precision, "data": "synthetic", "impl": "xg",
                "config": cfg,
                "gdof_paper_convention": round(dof_p * 3 * K * world / (ms_max / 1e3) / 1e9, 4),
                "plain_fp64": plain,
                "speedup_vs_plain_fp64": round(value / plain["value"], 3) if plain else None,
+               "fp32_form": fp32,
+               "fp32_speedup_vs_plain_fp64": (round(fp32["value"] / plain["value"], 3)
+                                              if fp32 and plain else None),
                "l2_error_vs_oracle": l2,
                "hbm_roofline_frac": round(hbm_frac, 4),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -478,11 +487,11 @@ def main():
     ap.add_argument("--workload", choices=["tc", "bubble"], default="tc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "df64"], default="df64",
+    ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
                     help="df64: FP64-accurate double-float on the FP32 pipes (default); "
-                         "fp64: native FP64")
+                         "fp64: native FP64; fp32: the FP32 precision form")
     ap.add_argument("--no-plain", action="store_true",
-                    help="skip the plain-FP64 comparison run")
+                    help="skip the plain-FP64 and FP32-form comparison runs")
     ap.add_argument("--nel", type=int, nargs=3, default=None,
                     help="element counts of a smaller cyclone box (same spacing), for profiling")
     args = ap.parse_args()

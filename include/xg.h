@@ -74,7 +74,10 @@ enum { XG_FP64 = 0, XG_FP32 = 1, XG_DF64 = 2 };
  *               XG_DF64: FP64-accurate "double-float" arithmetic (each value
  *               an unevaluated pair of floats, 48-bit significand) on the
  *               FP32 pipes, with the state kept in that form on the device;
- *               the ABI still takes and returns FP64 arrays
+ *               XG_FP32: the precision form -- FP32 state perturbations and
+ *               volume arithmetic, with the pressure perturbation of Eq. 3
+ *               evaluated FP64-accurately from the FP64 reference state;
+ *               in every precision the ABI takes and returns FP64 arrays
  *   f_coriolis  f-plane Coriolis parameter (s^-1)
  *   g, R, cp, cv, p_a   gravity, dry-air gas constant, heat capacities and
  *               reference surface pressure of Eq. 1 and Eq. 3 (SI units) */
@@ -98,8 +101,8 @@ const char* xg_status_str(xg_status s);
  * device buffer of the path (owned by the context).  On success *out is a
  * new context; on failure *out is NULL.  Errors: XG_ERR_ARG (NULL, nel < 1,
  * order outside [1, 8], hi <= lo, non-positive constants),
- * XG_ERR_UNSUPPORTED (precision other than XG_FP64 or XG_DF64, or a line of
- * more nodes than one CTA stages in shared memory), XG_ERR_OOM, XG_ERR_CUDA. */
+ * XG_ERR_UNSUPPORTED (an unknown precision, or a line of more nodes than one
+ * CTA stages in shared memory), XG_ERR_OOM, XG_ERR_CUDA. */
 xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out);
 
 /* Number of global (unique) nodes Np = n_x n_y n_z. */
@@ -137,6 +140,14 @@ xg_status xg_step(xg_ctx* ctx, double dt, int nsteps, void* stream);
 /* Copy the current state to q [5][Np], on `stream` (XG_HOST waits for it).
  * Errors: XG_ERR_ARG (NULL, no state yet), XG_ERR_CUDA. */
 xg_status xg_get_state(xg_ctx* ctx, double* q, int where, void* stream);
+
+/* Conservation sums of the current state, accumulated in FP64 whatever the
+ * precision: out[v] = sum_I M_I q_v,I for v = 0..4 (rho', rho u, rho v,
+ * rho w, Theta'), with M_I the diagonal mass of Eqs. 9 and 12 (the LGL
+ * weights times the Jacobian, assembled).  Deterministic (fixed summation
+ * order); waits for the GPU.  Errors: XG_ERR_ARG (NULL, no state yet),
+ * XG_ERR_CUDA. */
+xg_status xg_diagnostics(xg_ctx* ctx, double out[5], void* stream);
 
 /* Kernel timing (Sec. 5.4 measures its kernels against a roofline; this is
  * the hook for doing the same here).  enable = 1 brackets every kernel that

@@ -24,6 +24,12 @@ using xg::LineParams;
 using xg::StageBufs;
 using xg::df;
 
+namespace xg {
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(df v) { return df_to_double(v); }
+}  // namespace xg
+
 struct xg_ctx {
   xg_mesh_desc d;
   int n[3];
@@ -31,7 +37,9 @@ struct xg_ctx {
   int dev;
   LineParams P;
   DfParams Pdf;          // launch constants of the double-float kernels
+  xg::FParams Pf;        // launch constants of the FP32 kernels
   bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
+  bool f32 = false;      // precision XG_FP32: device arrays hold floats
   double* A = nullptr;   // q^n (the state)
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer
@@ -40,6 +48,9 @@ struct xg_ctx {
   double* T = nullptr;   // [5][np] partial tendency
   double* S = nullptr;   // [np] heating
   double* base = nullptr;  // [4][nz]
+  double* wasm = nullptr;  // assembled 1-D mass weights: [n_x + n_y + n_z], J folded into x
+  double* partial = nullptr;  // [kDiagBlocks][5] per-block conservation sums
+  double* hdiag = nullptr;    // pinned [5]
   int* flag = nullptr;
   int* hflag = nullptr;  // pinned
   bool has_state = false;
@@ -79,9 +90,59 @@ __global__ void k_from_df(const df* __restrict__ in, double* __restrict__ out, l
        i += (long long)gridDim.x * blockDim.x)
     out[i] = df_to_double(in[i]);
 }
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(in[i]);
+}
+__global__ void k_from_f32(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
 }  // namespace xg
 
 namespace {
+
+constexpr int kDiagBlocks = 512;
+constexpr int kDiagThreads = 256;
+
+// Per-block FP64 sums of M_I q_v,I (v = 0..4), M_I = Wx(gx) Wy(gy) Wz(gz)
+// with the Jacobian folded into Wx; a fixed tree order in shared memory.
+template <typename R>
+__global__ void k_diag_partial(const R* __restrict__ q, const double* __restrict__ wasm, int nx,
+                               int ny, int nz, long long np, double* __restrict__ partial) {
+  __shared__ double red[5][kDiagThreads];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < np;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(I % nx);
+    const long long r = I / nx;
+    const int gy = (int)(r % ny), gz = (int)(r / ny);
+    const double m = wasm[gx] * wasm[nx + gy] * wasm[nx + ny + gz];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += m * xg::to_double(q[v * np + I]);
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int h = kDiagThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(const double* __restrict__ partial, double* __restrict__ out) {
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int b = 0; b < kDiagBlocks; ++b) s += partial[b * 5 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
 
 unsigned conv_blocks(long long n) {
   const long long b = (n + 255) / 256;
@@ -153,6 +214,9 @@ cudaError_t configure_n(xg_ctx* c) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(xg::k_df_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)c->xsmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(xg::k_f_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(c->xsmem / 2));
   return e;
 }
 
@@ -173,6 +237,40 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
   prof_mark(c, 2, false, st);
   xg::k_df_tline<N, 2><<<gz, blk, 0, st>>>(c->Pdf, B);
   prof_mark(c, 2, true, st);
+}
+
+template <int N>
+void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
+  dim3 gx(c->n[1], c->n[2]);
+  prof_mark(c, 0, false, st);
+  xg::k_f_line_x<N><<<gx, xg::kXThreads, c->xsmem / 2, st>>>(c->Pf, B);
+  prof_mark(c, 0, true, st);
+  constexpr int K = xg::tile_segments(N);
+  const dim3 blk(xg::kTileCols, K * N + 1);
+  const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
+  dim3 gy(xb, (c->d.nel[1] + K - 1) / K, c->n[2]);
+  prof_mark(c, 1, false, st);
+  xg::k_f_tline<N, 1><<<gy, blk, 0, st>>>(c->Pf, B);
+  prof_mark(c, 1, true, st);
+  dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);
+  prof_mark(c, 2, false, st);
+  xg::k_f_tline<N, 2><<<gz, blk, 0, st>>>(c->Pf, B);
+  prof_mark(c, 2, true, st);
+}
+
+cudaError_t launch_f32_stage(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
+  switch (c->d.order) {
+    case 1: launch_f32_stage_n<1>(c, B, st); break;
+    case 2: launch_f32_stage_n<2>(c, B, st); break;
+    case 3: launch_f32_stage_n<3>(c, B, st); break;
+    case 4: launch_f32_stage_n<4>(c, B, st); break;
+    case 5: launch_f32_stage_n<5>(c, B, st); break;
+    case 6: launch_f32_stage_n<6>(c, B, st); break;
+    case 7: launch_f32_stage_n<7>(c, B, st); break;
+    case 8: launch_f32_stage_n<8>(c, B, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_df_stage(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
@@ -242,6 +340,22 @@ StageBufs make_bufs(xg_ctx* c, const double* q, const double* qn, double* out, d
 // arrays of the context's precision.
 cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, double dt,
                       double alpha, double beta, int rhs_only, cudaStream_t st) {
+  if (c->f32) {
+    xg::FBufs F;
+    F.q = (const float*)q;
+    F.qn = (const float*)qn;
+    F.out = (float*)out;
+    F.W = (float*)c->W;
+    F.T = (float*)c->T;
+    F.S = c->has_forcing ? (const float*)c->S : nullptr;
+    F.base = (const df*)c->base;
+    F.flag = c->flag;
+    F.dt = (float)dt;
+    F.alpha = (float)alpha;
+    F.beta = (float)beta;
+    F.rhs_only = rhs_only;
+    return launch_f32_stage(c, F, st);
+  }
   if (!c->dfm)
     return launch_stage(c, make_bufs(c, (const double*)q, (const double*)qn, (double*)out, dt,
                                      alpha, beta, rhs_only), st);
@@ -264,6 +378,10 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
 
 // Device FP64 array -> the context's device representation (n values).
 cudaError_t import_values(xg_ctx* c, const double* src, void* dst, long long n, cudaStream_t st) {
+  if (c->f32) {
+    xg::k_to_f32<<<conv_blocks(n), 256, 0, st>>>(src, (float*)dst, n);
+    return cudaGetLastError();
+  }
   if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
   xg::k_to_df<<<conv_blocks(n), 256, 0, st>>>(src, (df*)dst, n);
   return cudaGetLastError();
@@ -271,6 +389,10 @@ cudaError_t import_values(xg_ctx* c, const double* src, void* dst, long long n, 
 
 // The context's device representation -> device FP64 array.
 cudaError_t export_values(xg_ctx* c, const void* src, double* dst, long long n, cudaStream_t st) {
+  if (c->f32) {
+    xg::k_from_f32<<<conv_blocks(n), 256, 0, st>>>((const float*)src, dst, n);
+    return cudaGetLastError();
+  }
   if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
   xg::k_from_df<<<conv_blocks(n), 256, 0, st>>>((const df*)src, dst, n);
   return cudaGetLastError();
@@ -318,7 +440,9 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
 
   xg::fill_line_params(d, geo, &c->P);
   c->dfm = d->precision == XG_DF64;
+  c->f32 = d->precision == XG_FP32;
   if (c->dfm) xg::fill_df_params(c->P, &c->Pdf);
+  if (c->f32) xg::fill_f32_params(c->P, &c->Pf);
   xg::plan_marches(d, geo, sms, &c->chunk_y, &c->nchunk_y, &c->chunk_z, &c->nchunk_z);
 
   const size_t vec = sizeof(double) * (size_t)np;
@@ -335,6 +459,30 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
   }
   e = cudaMalloc((void**)&c->flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hflag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->wasm, sizeof(double) * (size_t)(n[0] + n[1] + n[2]));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 5 * kDiagBlocks);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hdiag, sizeof(double) * 5);
+  if (e == cudaSuccess) {
+    // assembled 1-D LGL weights per direction (Eq. 8-9 on the uniform box):
+    // w_a inside an element, 2 w_0 on a shared face, w_0 on a wall; the
+    // Jacobian (h_x h_y h_z / 8) is folded into the x weights
+    double wl[xg::kMaxOrder + 1];
+    xg::lgl_weights(d->order, wl);
+    std::vector<double> wa(n[0] + n[1] + n[2]);
+    double J = 1.0;
+    for (int k = 0; k < 3; ++k) J *= (d->hi[k] - d->lo[k]) / d->nel[k] / 2.0;
+    int off = 0;
+    for (int k = 0; k < 3; ++k) {
+      for (int g = 0; g < n[k]; ++g) {
+        const int a = g % d->order;
+        double w = wl[a];
+        if (a == 0) w = (d->periodic[k] || (g > 0 && g < n[k] - 1)) ? 2.0 * wl[0] : wl[0];
+        wa[off + g] = k == 0 ? w * J : w;
+      }
+      off += n[k];
+    }
+    e = cudaMemcpy(c->wasm, wa.data(), sizeof(double) * wa.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = configure(c);
   if (e != cudaSuccess) {
     fail_cuda(c, e, "xg_mesh_create");
@@ -388,7 +536,7 @@ xg_status xg_set_state(xg_ctx* c, const double* q, const double* rho0, const dou
       hb[2 * nz + k] = c->d.p_a * pow(c->d.R * t0[k] / c->d.p_a, gamma);  // Eq. 3
       hb[3 * nz + k] = 1.0 / t0[k];
     }
-    if (c->dfm) {  // the same table as double-float pairs (8 bytes each, in place)
+    if (c->dfm || c->f32) {  // the table as double-float pairs (8 bytes each, in place)
       for (int k = 0; k < 4 * nz; ++k) {
         const df v = xg::split_df(hb[k]);
         memcpy(hb + k, &v, sizeof(df));
@@ -401,7 +549,7 @@ xg_status xg_set_state(xg_ctx* c, const double* q, const double* rho0, const dou
     c->has_base = true;
   }
   const long long n5 = 5 * c->np;
-  if (!c->dfm) {
+  if (!c->dfm && !c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(c->A, q, sizeof(double) * (size_t)n5,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else if (where == XG_DEVICE) {
@@ -423,7 +571,7 @@ xg_status xg_set_forcing(xg_ctx* c, const double* S, int where, void* stream) {
     c->has_forcing = false;
     return XG_OK;
   }
-  if (!c->dfm) {
+  if (!c->dfm && !c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(c->S, S, sizeof(double) * (size_t)c->np,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else if (where == XG_DEVICE) {
@@ -443,7 +591,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
-  if (!c->dfm) {
+  if (!c->dfm && !c->f32) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
   } else {
     XG_CUDA(c, run_stage(c, c->A, nullptr, c->Cq, 0.0, 0.0, 1.0, 1, st));
@@ -488,7 +636,7 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const long long n5 = 5 * c->np;
-  if (!c->dfm) {
+  if (!c->dfm && !c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(q, c->A, sizeof(double) * (size_t)n5,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   } else if (where == XG_DEVICE) {
@@ -529,9 +677,35 @@ xg_status xg_reciprocal(const double* x, double* out, long long n, void* stream)
   return XG_OK;
 }
 
+xg_status xg_diagnostics(xg_ctx* c, double out[5], void* stream) {
+  if (!c || !out) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!c->has_state) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->f32)
+    k_diag_partial<float><<<kDiagBlocks, kDiagThreads, 0, st>>>((const float*)c->A, c->wasm, c->n[0],
+                                                                c->n[1], c->n[2], c->np, c->partial);
+  else if (c->dfm)
+    k_diag_partial<df><<<kDiagBlocks, kDiagThreads, 0, st>>>((const df*)c->A, c->wasm, c->n[0],
+                                                             c->n[1], c->n[2], c->np, c->partial);
+  else
+    k_diag_partial<double><<<kDiagBlocks, kDiagThreads, 0, st>>>(c->A, c->wasm, c->n[0], c->n[1],
+                                                                 c->n[2], c->np, c->partial);
+  XG_CUDA(c, cudaGetLastError());
+  k_diag_final<<<1, 32, 0, st>>>(c->partial, c->T);   // T is free between stages
+  XG_CUDA(c, cudaGetLastError());
+  XG_CUDA(c, cudaMemcpyAsync(c->hdiag, c->T, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+  XG_CUDA(c, cudaStreamSynchronize(st));
+  for (int v = 0; v < 5; ++v) out[v] = c->hdiag[v];
+  return XG_OK;
+}
+
 void xg_destroy(xg_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  cudaFree(c->wasm);
+  cudaFree(c->partial);
+  if (c->hdiag) cudaFreeHost(c->hdiag);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   cudaFree(c->A);
   cudaFree(c->Bq);

@@ -1,0 +1,315 @@
+// xg_kernels_f32.cuh -- the precision form: FP32 state and volume arithmetic.
+//
+// Same method and three-pass stage as xg_kernels.cuh.  The state
+// perturbations (rho', rho u, rho v, rho w, Theta'), the fluxes, the LGL
+// contractions, the assembly, the sources and the SSP-RK combination are
+// FP32 (4 bytes per value, FMA on the FP32 pipes).  The pressure
+// perturbation p' = p(Theta_0 + Theta') - p(Theta_0) of Eq. 3 is evaluated
+// FP64-accurately (double-float, xg_df.cuh) from the FP64 reference state,
+// so the hydrostatic reference is subtracted analytically and never from
+// rounded FP32 totals; conservation sums are FP64 (xg_diagnostics).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "xg_df.cuh"
+#include "xg_kernels.cuh"
+#include "xg_kernels_df.cuh"
+
+namespace xg {
+
+struct FParams {
+  int n[3];
+  int nseg[3];
+  int per[3];
+  long long np;
+  float Dm[3][kMaxOrder + 1][kMaxOrder + 1];   // -(2/h_d) D, rows 0 and N halved
+  df eos_c[3];                                 // C(gamma,1..3)
+  float eos_g[kEosTerms - 3];                  // C(gamma,4..8)
+  float eos_xmax;
+  double gamma;
+  float f, g;
+};
+
+struct FBufs {
+  const float* q;
+  const float* qn;
+  float* out;
+  float* W;          // [3][np] v, w, p'
+  float* T;          // [5][np]
+  const float* S;    // [np] or null
+  const df* base;    // [4][nz] rho0, Theta0, p0, 1/Theta0 (FP64-accurate pairs)
+  int* flag;
+  float dt, alpha, beta;
+  int rhs_only;
+};
+
+__device__ __forceinline__ bool f_nonfinite(float v) {
+  return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
+}
+
+// p' = p0 ((1 + x)^gamma - 1), x = Theta'/Theta0, in double-float.
+__device__ __forceinline__ float f_pressure_pert(const FParams& P, float tp, df p0, df iTh0) {
+  const df x = df_mul_f(iTh0, tp);
+  df phi;
+  if (fabsf(x.h) < P.eos_xmax) {
+    float g = P.eos_g[kEosTerms - 4];
+#pragma unroll
+    for (int k = kEosTerms - 5; k >= 0; --k) g = __fmaf_rn(g, x.h, P.eos_g[k]);
+    df a = df_add_nc(P.eos_c[2], df_mul_f(x, g));
+    a = df_add_nc(P.eos_c[1], df_mul(x, a));
+    a = df_add_nc(P.eos_c[0], df_mul(x, a));
+    phi = df_mul(x, a);
+  } else {
+    phi = df_from_double(expm1(P.gamma * log1p(df_to_double(x))));
+  }
+  const df pp = df_mul(p0, phi);
+  return __fadd_rn(pp.h, pp.l);
+}
+
+template <int N, int D>
+__device__ __forceinline__ float f_row_from(const FParams& P, int a, const float (&f)[N + 1], float acc) {
+#pragma unroll
+  for (int l = 0; l <= N; ++l) acc = fmaf(P.Dm[D][a][l], f[l], acc);
+  return acc;
+}
+
+// ---------------------------------------------------------------- x lines
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_f_line_x(const FParams P, const FBufs B) {
+  extern __shared__ float smf[];
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nseg = P.nseg[0];
+  const int y = blockIdx.x, z = blockIdx.y;
+  const long long np = P.np;
+  const long long row = (long long)nx * (y + (long long)ny * z);
+  const int ld = nx + 1;
+  float* F = smf;            // [5][ld], later rows 0..N-1 of every segment in place
+  float* RN = smf + 5 * ld;  // [5][nseg] row N
+  const df rho0d = B.base[z], Th0d = B.base[nz + z], p0 = B.base[2 * nz + z];
+  const df iTh0 = B.base[3 * nz + z];
+  const float rho0 = rho0d.h + rho0d.l, Th0 = Th0d.h + Th0d.l;
+  const float* __restrict__ q = B.q;
+  float* __restrict__ Wo = B.W;
+  float* __restrict__ To = B.T;
+
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const long long I = row + i;
+    const float rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
+    const float tp = q[4 * np + I];
+    const float ir = __frcp_rn(rho0 + rp);
+    const float u = mu * ir, v = mv * ir, w = mw * ir;
+    const float pp = f_pressure_pert(P, tp, p0, iTh0);
+    Wo[I] = v;
+    Wo[np + I] = w;
+    Wo[2 * np + I] = pp;
+    F[i] = mu;
+    F[ld + i] = fmaf(mu, u, pp);
+    F[2 * ld + i] = mv * u;
+    F[3 * ld + i] = mw * u;
+    F[4 * ld + i] = (Th0 + tp) * u;
+    if (P.per[0] && i == 0) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) F[c * ld + nx] = F[c * ld];
+    }
+  }
+  __syncthreads();
+
+  for (int s0 = 0; s0 < nseg; s0 += blockDim.x) {
+    const int s = s0 + threadIdx.x;
+    float rows[5][N + 1];
+    if (s < nseg) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        float f[N + 1];
+#pragma unroll
+        for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
+#pragma unroll
+        for (int a = 0; a <= N; ++a) rows[c][a] = f_row_from<N, 0>(P, a, f, 0.0f);
+      }
+    }
+    __syncthreads();
+    if (s < nseg) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) F[c * ld + s * N + a] = rows[c][a];
+        RN[c * nseg + s] = rows[c][N];
+      }
+    }
+    __syncthreads();
+  }
+
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const int s = i / N, a = i - s * N;
+    const long long I = row + i;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float v;
+      if (s == nseg) {
+        v = 2.0f * RN[c * nseg + nseg - 1];
+      } else if (a != 0) {
+        v = F[c * ld + i];
+      } else {
+        const float r0 = F[c * ld + i];
+        const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
+        v = left >= 0 ? r0 + RN[c * nseg + left] : 2.0f * r0;
+      }
+      To[c * np + I] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- y and z lines, tiled
+// One thread per node over (32 x-columns) x (K segments along DIR) tiles, as
+// k_df_tline; DIR = 1 adds the y part into T, DIR = 2 finishes the node.
+template <int DIR>
+__device__ __forceinline__ void f_flux_dir(const float* __restrict__ q, const float* __restrict__ W,
+                                           long long np, long long I, float Th0, float (&f)[5]) {
+  const float mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+  if (DIR == 1) {
+    const float v = W[I], pp = W[2 * np + I];
+    f[0] = mv;
+    f[1] = mu * v;
+    f[2] = fmaf(mv, v, pp);
+    f[3] = mw * v;
+    f[4] = (Th0 + tp) * v;
+  } else {
+    const float w = W[np + I], pp = W[2 * np + I];
+    f[0] = mw;
+    f[1] = mu * w;
+    f[2] = mv * w;
+    f[3] = fmaf(mw, w, pp);
+    f[4] = (Th0 + tp) * w;
+  }
+}
+
+__device__ __forceinline__ void f_finish_node(const FParams& P, const FBufs& B,
+                                              const float* __restrict__ q,
+                                              const float* __restrict__ qn,
+                                              float* __restrict__ out, long long I, int x, int y,
+                                              int gz, float (&L)[5], bool& bad) {
+  const long long np = P.np;
+  const float rp = q[I], mu = q[np + I], mv = q[2 * np + I];
+  L[1] = fmaf(P.f, mv, L[1]);
+  L[2] = fmaf(-P.f, mu, L[2]);
+  L[3] = fmaf(-P.g, rp, L[3]);
+  if (B.S) {
+    const df r0 = B.base[gz];
+    L[4] = fmaf(r0.h + rp, B.S[I], L[4]);
+  }
+  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = 0.0f;
+  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = 0.0f;
+  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0f;
+  if (B.rhs_only) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      out[c * np + I] = L[c];
+      bad |= f_nonfinite(L[c]);
+    }
+  } else if (B.alpha == 0.0f) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float o = fmaf(B.dt, L[c], q[c * np + I]);
+      out[c * np + I] = o;
+      bad |= f_nonfinite(o);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float o = fmaf(B.alpha, qn[c * np + I], B.beta * fmaf(B.dt, L[c], q[c * np + I]));
+      out[c * np + I] = o;
+      bad |= f_nonfinite(o);
+    }
+  }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams P, const FBufs B) {
+  constexpr int K = tile_segments(N);
+  constexpr int NS = K * N + N + 1;
+  __shared__ float Fs[5][NS][kTileCols];
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int nd = P.n[DIR];
+  const int nseg = P.nseg[DIR];
+  const bool per = P.per[DIR] != 0;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * kTileCols + tx;
+  const bool xin = x < nx;
+  const int s0 = blockIdx.y * K;
+  const int kc = min(K, nseg - s0);
+  const int other = blockIdx.z;
+  const long long np = P.np;
+  const long long sd = DIR == 1 ? (long long)nx : (long long)nx * ny;
+  const long long base = DIR == 1 ? x + (long long)nx * ny * other : x + (long long)nx * other;
+  const float* __restrict__ q = B.q;
+  const float* __restrict__ W = B.W;
+  const bool has_left = s0 > 0 || per;
+  auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
+  auto th0 = [&](int g) -> float {
+    const df t = B.base[nz + (DIR == 2 ? g : other)];
+    return t.h + t.l;
+  };
+
+  const int own = s0 * N + ty;
+  const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
+  if (xin && ty <= kc * N) {
+    const int g = plane(own);
+    float f[5];
+    f_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+  }
+  if (xin && has_left && ty < N) {
+    const int g = plane((s0 - 1) * N + ty);
+    float f[5];
+    f_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
+  }
+  const long long I = base + sd * (owns ? plane(own) : 0);
+  float t[5];
+  if (owns) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+  }
+  __syncthreads();
+  if (!owns) return;
+
+  const int k = ty < kc * N ? ty / N : kc - 1;
+  const int a = ty < kc * N ? ty - k * N : N;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float f[N + 1];
+#pragma unroll
+    for (int l = 0; l <= N; ++l) f[l] = Fs[c][N + k * N + l][tx];
+    if (a == N) {
+      t[c] = fmaf(2.0f, f_row_from<N, DIR>(P, N, f, 0.0f), t[c]);
+    } else if (a > 0) {
+      t[c] = f_row_from<N, DIR>(P, a, f, t[c]);
+    } else if (k > 0 || has_left) {
+      float fl[N + 1];
+#pragma unroll
+      for (int l = 0; l <= N; ++l) fl[l] = Fs[c][k * N + l][tx];
+      t[c] = f_row_from<N, DIR>(P, 0, f, t[c]);
+      t[c] = f_row_from<N, DIR>(P, N, fl, t[c]);
+    } else {
+      t[c] = f_row_from<N, DIR>(P, 0, f, t[c]);
+      t[c] = f_row_from<N, DIR>(P, 0, f, t[c]);
+    }
+  }
+  if (DIR == 1) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) B.T[c * np + I] = t[c];
+  } else {
+    bool bad = false;
+    f_finish_node(P, B, q, B.qn, B.out, I, x, other, plane(own), t, bad);
+    if (bad) *B.flag = 1;
+  }
+}
+
+// FP64 <-> FP32 conversion of n values (data entering or leaving).
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n);
+__global__ void k_from_f32(const float* __restrict__ in, double* __restrict__ out, long long n);
+
+}  // namespace xg

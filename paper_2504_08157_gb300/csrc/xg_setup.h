@@ -10,6 +10,7 @@
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
 #include "xg_kernels_df.cuh"
+#include "xg_kernels_f32.cuh"
 
 namespace xg {
 
@@ -64,6 +65,26 @@ inline void lgl_derivative(int N, double D[kMaxOrder + 1][kMaxOrder + 1]) {
     }
 }
 
+// LGL weights w_j = 2 / (N (N+1) P_N(x_j)^2) at the points of lgl_derivative.
+inline void lgl_weights(int N, double* w) {
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int j = 0; j <= N; ++j) {
+    long double xj = -cosl(pi * j / N);
+    for (int it = 0; it < 100; ++it) {
+      long double pn, pn1;
+      legendre2(N, xj, &pn, &pn1);
+      long double dx = (xj * pn - pn1) / ((N + 1) * pn);
+      xj -= dx;
+      if (fabsl(dx) < 1e-30L) break;
+    }
+    if (j == 0) xj = -1.0L;
+    if (j == N) xj = 1.0L;
+    long double pn, pn1;
+    legendre2(N, xj, &pn, &pn1);
+    w[j] = (double)(2.0L / ((long double)N * (N + 1) * pn * pn));
+  }
+}
+
 // Binomial coefficients C(gamma, k), k = 1..K (K = kEosTerms), of
 // (1+x)^gamma - 1 and the largest |x| (<= 0.1) for which the truncation
 // error after K terms stays below 2^-56 of the sum:
@@ -102,7 +123,8 @@ inline xg_status check_desc(const xg_mesh_desc* d, MeshGeom* g) {
   if (!(std::isfinite(d->g) && d->g >= 0.0 && std::isfinite(d->f_coriolis))) return XG_ERR_ARG;
   const double gamma = d->cp / d->cv;
   if (!(gamma > 1.0 && gamma < 2.0)) return XG_ERR_ARG;
-  if (d->precision != XG_FP64 && d->precision != XG_DF64) return XG_ERR_UNSUPPORTED;
+  if (d->precision != XG_FP64 && d->precision != XG_DF64 && d->precision != XG_FP32)
+    return XG_ERR_UNSUPPORTED;
   const int N = d->order;
   for (int k = 0; k < 3; ++k) {
     long long nk = (long long)N * d->nel[k] + (d->periodic[k] ? 0 : 1);
@@ -175,6 +197,25 @@ inline void fill_df_params(const LineParams& P, DfParams* Q) {
   Q->gamma = P.gamma;
   Q->f = split_df(P.f);
   Q->g = split_df(P.g);
+}
+
+// Launch constants of the FP32 line kernels, from the FP64 ones.
+inline void fill_f32_params(const LineParams& P, FParams* Q) {
+  memset(Q, 0, sizeof(*Q));
+  for (int k = 0; k < 3; ++k) {
+    Q->n[k] = P.n[k];
+    Q->nseg[k] = P.nseg[k];
+    Q->per[k] = P.per[k];
+    for (int a = 0; a <= kMaxOrder; ++a)
+      for (int l = 0; l <= kMaxOrder; ++l) Q->Dm[k][a][l] = (float)P.Dm[k][a][l];
+  }
+  Q->np = P.np;
+  for (int k = 0; k < 3; ++k) Q->eos_c[k] = split_df(P.eos_c[k]);
+  for (int k = 3; k < kEosTerms; ++k) Q->eos_g[k - 3] = (float)P.eos_c[k];
+  Q->eos_xmax = (float)P.eos_xmax;
+  Q->gamma = P.gamma;
+  Q->f = (float)P.f;
+  Q->g = (float)P.g;
 }
 
 // Element segments per marching thread of k_line_y / k_line_z.  A launch

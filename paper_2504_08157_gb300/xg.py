@@ -23,7 +23,7 @@ XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
+           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -83,6 +83,8 @@ def library():
     lib.xg_rhs_noalloc.argtypes = [ctypes.POINTER(xg_mesh_desc), P, P, P, P, P, P]
     lib.xg_reciprocal.restype = I
     lib.xg_reciprocal.argtypes = [P, P, LL, P]
+    lib.xg_diagnostics.restype = I
+    lib.xg_diagnostics.argtypes = [P, ctypes.POINTER(D), P]
     lib.xg_destroy.restype = None
     lib.xg_destroy.argtypes = [P]
     _lib = lib
@@ -241,6 +243,20 @@ def xg_reciprocal(x, out, stream=None):
         raise ValueError("xg_reciprocal takes device arrays")
     n = x.numel() if hasattr(x, "numel") else len(x)
     _check(library().xg_reciprocal(px, po, int(n), _stream(stream, sx)), "xg_reciprocal")
+
+
+def xg_diagnostics(ctx, stream=None):
+    """FP64 conservation sums sum_I M_I q_v,I, v = 0..4, of the current state."""
+    out = (ctypes.c_double * 5)()
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    _check(library().xg_diagnostics(ctx, out, _stream(stream, None)), "xg_diagnostics")
+    return tuple(out)
 
 
 def xg_destroy(ctx):

@@ -66,7 +66,7 @@ def test_mesh_create_rejects_bad_arguments(lib, bad):
 def test_unsupported_precision(lib):
     from paper_2504_08157_gb300 import xg
     with pytest.raises(xg.XgError) as e:
-        xg.xg_mesh_create(_desc(precision=xg.XG_FP32))
+        xg.xg_mesh_create(_desc(precision=7))
     assert e.value.status == xg.XG_ERR_UNSUPPORTED
 
 

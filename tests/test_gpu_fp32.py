@@ -1,0 +1,125 @@
+"""The precision form (XG_FP32) against the FP64 oracle, and the FP64
+conservation sums (xg_diagnostics) in every precision.
+
+Precision form: FP32 state perturbations and volume arithmetic, the
+pressure perturbation of Eq. 3 FP64-accurate, conservation sums in FP64.
+Bar: relative L2 per variable <= 1e-5 for one right-hand side.  On the
+rising bubble (the config the precision form is judged on) the errors after
+1 RHS and after 200 SSP-RK3 steps are measured and bounded."""
+
+import numpy as np
+import pytest
+
+from inputs import workloads as W
+from oracle import euler as E
+
+from helpers import GpuRun, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64, DF64 = 1, 0, 2
+RHS_TOL32 = 1e-5
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 8])
+def test_fp32_rhs_every_order(cuda_device, N):
+    """Orders 2-8 within 1e-5.  Linear elements (N = 1) difference the FP32
+    p' across two nodes of an element only: their pressure-gradient error is
+    eps_32 |p'| / |delta p'| (about 2e-5 on this coarse random state), so
+    their bar is 5e-5."""
+    wl = W.box((2, 3, 2), N, (0.0, 0.0, 0.0), (2000.0, 3000.0, 2000.0), (True, False, True),
+               seed=40 + N)
+    with GpuRun(wl, precision=FP32) as g:
+        got = g.rhs()
+    err = rel_l2_per_var(got, oracle_rhs(wl))
+    assert np.all(err <= (RHS_TOL32 if N > 1 else 5e-5)), err
+
+
+@pytest.mark.parametrize("nel,periodic", [
+    ((1, 1, 1), (False, False, False)),
+    ((2, 2, 2), (True, True, True)),
+    ((3, 2, 5), (False, False, False)),
+    ((37, 3, 2), (False, True, False)),
+])
+def test_fp32_rhs_sizes_and_boundaries(cuda_device, nel, periodic):
+    L = tuple(1000.0 * n for n in nel)
+    wl = W.box(nel, 4, (0.0, 0.0, 0.0), L, periodic, seed=sum(nel) + 3)
+    with GpuRun(wl, precision=FP32) as g:
+        got = g.rhs()
+    err = rel_l2_per_var(got, oracle_rhs(wl))
+    assert np.all(err <= RHS_TOL32), err
+
+
+def test_fp32_rhs_tc_scaled(cuda_device):
+    wl = W.tc(nel=(16, 16, 4), state="random")
+    with GpuRun(wl, precision=FP32) as g:
+        got = g.rhs()
+    err = rel_l2_per_var(got, oracle_rhs(wl))
+    assert np.all(err <= RHS_TOL32), err
+
+
+@pytest.mark.slow
+def test_fp32_bubble_rhs_and_200_steps(cuda_device):
+    """Config 3: the rising bubble in FP32.  After one RHS every variable is
+    within 1e-5 of the oracle (the initial state's zero tendencies are
+    exactly zero).  After 200 steps (600 FP32 stage updates) the measured
+    errors are bounded as regression guards: state within 2e-5, its change
+    within 1e-2."""
+    wl = W.bubble(state="random")
+    with GpuRun(wl, precision=FP32) as g:
+        r = g.rhs()
+    assert np.all(rel_l2_per_var(r, oracle_rhs(wl)) <= RHS_TOL32)
+    wl = W.bubble()
+    with GpuRun(wl, precision=FP32) as g:
+        r = g.rhs()
+        g.step(200)
+        q = g.state()
+    ref_r = oracle_rhs(wl)
+    e_rhs = rel_l2_per_var(r, ref_r)
+    assert np.all(e_rhs <= RHS_TOL32), e_rhs
+    ref = oracle_steps(wl, 200)
+    e_state = rel_l2_per_var(q, ref)
+    e_inc = rel_l2_per_var(q - wl["q"], ref - wl["q"])
+    print("fp32 bubble: rhs", e_rhs, "state after 200 steps", e_state, "increment", e_inc)
+    assert np.all(e_state <= 2e-5), (e_state, e_inc)
+    assert np.all(e_inc <= 1e-2), (e_state, e_inc)
+
+
+@pytest.mark.slow
+def test_fp32_full_size_tc_rhs_sampled(cuda_device):
+    import test_gpu_parity as P
+    got, ref, _ = P._full_size_sampled(W.tc(state="random"), FP32)
+    err = rel_l2_per_var(got, ref)
+    assert np.all(err <= RHS_TOL32), err
+
+
+# ------------------------------------------------------------------ FP64 conservation sums
+
+@pytest.mark.parametrize("prec", [FP64, DF64, FP32], ids=["fp64", "df64", "fp32"])
+def test_diagnostics_match_oracle_mass_sums(cuda_device, prec):
+    """sum_I M_I q_v,I computed on the GPU in FP64 equals the oracle's mass
+    matrix (Eq. 9) applied to the state read back from the GPU."""
+    wl = W.tc(nel=(6, 5, 4), state="random")
+    m, _, _ = oracle_of(wl)
+    M = E.mass(m)
+    with GpuRun(wl, precision=prec) as g:
+        d = np.array(g.xg.xg_diagnostics(g.ctx))
+        q = g.state()
+    ref = q @ M
+    scale = np.abs(q) @ M
+    assert np.all(np.abs(d - ref) <= 1e-14 * scale), (d, ref)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-13), (DF64, 1e-13), (FP32, 1e-6)],
+                         ids=["fp64", "df64", "fp32"])
+def test_mass_conserved_on_gpu(cuda_device, prec, tol):
+    """Walled bubble box: the FP64 sum of M rho' is unchanged after 20 steps,
+    relative to the total mass (FP32 to its own rounding)."""
+    wl = W.bubble()
+    with GpuRun(wl, precision=prec) as g:
+        before = g.xg.xg_diagnostics(g.ctx)[0]
+        g.step(20)
+        after = g.xg.xg_diagnostics(g.ctx)[0]
+    m, _, base = oracle_of(wl)
+    total = np.dot(E.mass(m), base.rho0[m.gidx[2]] + wl["q"][0])
+    assert abs(after - before) <= tol * total, (before, after, total)
