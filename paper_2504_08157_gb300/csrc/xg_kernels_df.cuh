@@ -253,59 +253,6 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
 }
 
 // ---------------------------------------------------------------- z lines + sources + stage
-__device__ __forceinline__ void df_finish_node(const DfParams& P, const DfBufs& B,
-                                               const df* __restrict__ q, const df* __restrict__ qn,
-                                               df* __restrict__ out, long long I, int x, int y,
-                                               int gz, df (&L)[5], bool& bad) {
-  const long long np = P.np;
-  const df rp = q[I], mu = q[np + I], mv = q[2 * np + I];
-  {
-    dacc A = dacc_from(L[1]);
-    dacc_fma(A, P.f, mv);                        // +f rho v
-    L[1] = dacc_value(A);
-    A = dacc_from(L[2]);
-    dacc_fma(A, df_neg(P.f), mu);                // -f rho u
-    L[2] = dacc_value(A);
-    A = dacc_from(L[3]);
-    dacc_fma(A, df_neg(P.g), rp);                // -rho' g
-    L[3] = dacc_value(A);
-    if (B.S) {
-      A = dacc_from(L[4]);
-      dacc_fma(A, df_add(B.base[gz], rp), B.S[I]);   // rho S_theta
-      L[4] = dacc_value(A);
-    }
-  }
-  const df zero = {0.0f, 0.0f};
-  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = zero;
-  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = zero;
-  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = zero;
-  if (B.rhs_only) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      out[c * np + I] = L[c];
-      bad |= df_nonfinite(L[c]);
-    }
-  } else if (B.alpha.h == 0.0f) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      dacc A = dacc_from(q[c * np + I]);
-      dacc_fma(A, B.dt, L[c]);
-      const df o = dacc_value(A);
-      out[c * np + I] = o;
-      bad |= df_nonfinite(o);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      dacc A = dacc_prod(B.alpha, qn[c * np + I]);
-      dacc_fma(A, B.beta, q[c * np + I]);
-      dacc_fma(A, B.bdt, L[c]);
-      const df o = dacc_value(A);
-      out[c * np + I] = o;
-      bad |= df_nonfinite(o);
-    }
-  }
-}
 
 // FP64 <-> double-float conversion of n values (data entering or leaving).
 __global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, long long n);
@@ -329,24 +276,59 @@ namespace xg {
 // the sources, walls and the stage store.  Thread row K N handles the
 // chunk's end face: its fluxes close the last segment, and at a wall it
 // also owns the wall node.
+// Fluxes along DIR at one node from loaded values: qv = (rho', rho u,
+// rho v, rho w, Theta'), vel = v (DIR 1) or w (DIR 2), pp = p'.
 template <int DIR>
-__device__ __forceinline__ void df_flux_dir(const df* __restrict__ q, const df* __restrict__ W,
-                                            long long np, long long I, df Th0, df (&f)[5]) {
-  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
-  if (DIR == 1) {
-    const df v = W[I], pp = W[2 * np + I];
-    f[0] = mv;
-    f[1] = df_mul(mu, v);
-    f[2] = df_add(df_mul(mv, v), pp);
-    f[3] = df_mul(mw, v);
-    f[4] = df_mul(df_add(Th0, tp), v);
-  } else {
-    const df w = W[np + I], pp = W[2 * np + I];
-    f[0] = mw;
-    f[1] = df_mul(mu, w);
-    f[2] = df_mul(mv, w);
-    f[3] = df_add(df_mul(mw, w), pp);
-    f[4] = df_mul(df_add(Th0, tp), w);
+__device__ __forceinline__ void df_flux_vals(const df (&qv)[5], df vel, df pp, df Th0, df (&f)[5]) {
+  const df Th = df_add(Th0, qv[4]);
+  f[0] = qv[DIR + 1];
+  f[1] = DIR == 1 ? df_mul(qv[1], vel) : df_mul(qv[1], vel);
+  f[2] = DIR == 1 ? df_add(df_mul(qv[2], vel), pp) : df_mul(qv[2], vel);
+  f[3] = DIR == 1 ? df_mul(qv[3], vel) : df_add(df_mul(qv[3], vel), pp);
+  f[4] = df_mul(Th, vel);
+}
+
+// Sources, walls and the stage store of one node from loaded values.
+__device__ __forceinline__ void df_finish_vals(const DfParams& P, const DfBufs& B,
+                                               const df (&qv)[5], const df (&qnv)[5], df sv,
+                                               df rho0, df* __restrict__ out, long long I, int x,
+                                               int y, int gz, df (&L)[5], bool& bad) {
+  const long long np = P.np;
+  dacc A = dacc_from(L[1]);
+  dacc_fma(A, P.f, qv[2]);                       // +f rho v
+  L[1] = dacc_value(A);
+  A = dacc_from(L[2]);
+  dacc_fma(A, df_neg(P.f), qv[1]);               // -f rho u
+  L[2] = dacc_value(A);
+  A = dacc_from(L[3]);
+  dacc_fma(A, df_neg(P.g), qv[0]);               // -rho' g
+  L[3] = dacc_value(A);
+  if (B.S) {
+    A = dacc_from(L[4]);
+    dacc_fma(A, df_add(rho0, qv[0]), sv);        // rho S_theta
+    L[4] = dacc_value(A);
+  }
+  const df zero = {0.0f, 0.0f};
+  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = zero;
+  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = zero;
+  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = zero;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    df o;
+    if (B.rhs_only) {
+      o = L[c];
+    } else if (B.alpha.h == 0.0f) {
+      dacc R = dacc_from(qv[c]);
+      dacc_fma(R, B.dt, L[c]);
+      o = dacc_value(R);
+    } else {
+      dacc R = dacc_prod(B.alpha, qnv[c]);
+      dacc_fma(R, B.beta, qv[c]);
+      dacc_fma(R, B.bdt, L[c]);
+      o = dacc_value(R);
+    }
+    out[c * np + I] = o;
+    bad |= df_nonfinite(o);
   }
 }
 
@@ -355,7 +337,7 @@ constexpr int kTileCols = 32;
 __host__ __device__ constexpr int tile_segments(int N) { return N >= 16 ? 1 : 16 / N; }
 
 template <int N, int DIR>
-__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_df_tline(const DfParams P, const DfBufs B) {
+__global__ void __launch_bounds__(kTileCols * (16 + 1), 2) k_df_tline(const DfParams P, const DfBufs B) {
   constexpr int K = tile_segments(N);
   constexpr int NS = K * N + N + 1;            // flux slots: N halo planes + K N + 1
   __shared__ df Fs[5][NS][kTileCols];
@@ -372,38 +354,58 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_df_tline(const DfParam
   const long long np = P.np;
   const long long sd = DIR == 1 ? (long long)nx : (long long)nx * ny;
   const long long base = DIR == 1 ? x + (long long)nx * ny * other : x + (long long)nx * other;
-  const df* __restrict__ q = B.q;
-  const df* __restrict__ W = B.W;
   const bool has_left = s0 > 0 || per;
   auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
-  auto th0 = [&](int g) -> df { return B.base[nz + (DIR == 2 ? g : other)]; };
+  const int vslot = DIR == 1 ? 0 : 1;            // v or w in W
 
   // the node this thread owns: planes s0 N + ty for ty < kc N, and the end
   // wall plane for the extra row of the last chunk of a walled line
   const int own = s0 * N + ty;
   const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
-  // fluxes of this thread's plane (the extra row always fills the end face)
-  if (xin && ty <= kc * N) {
-    const int g = plane(own);
-    df f[5];
-    df_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+  const bool main_plane = xin && ty <= kc * N;   // the extra row fills the end face
+  const bool halo = xin && has_left && ty < N;   // the N planes before the chunk
+  const int g = plane(own);
+  const int gh = plane((s0 - 1) * N + ty);
+  const long long I = base + sd * (main_plane ? g : 0);
+  const long long Ih = base + sd * (halo ? gh : 0);
+
+  // every global load of the thread first: one memory round trip
+  df qv[5], vel, pp, hq[5], hvel, hpp, t[5], qnv[5], sv = {0.0f, 0.0f};
+  hq[0] = sv;
+  if (main_plane) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+    for (int c = 0; c < 5; ++c) qv[c] = B.q[c * np + I];
+    vel = B.W[vslot * np + I];
+    pp = B.W[2 * np + I];
   }
-  // halo: the N planes of the segment before the chunk
-  if (xin && has_left && ty < N) {
-    const int g = plane((s0 - 1) * N + ty);
-    df f[5];
-    df_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+  if (halo) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
+    for (int c = 1; c < 5; ++c) hq[c] = B.q[c * np + Ih];
+    hvel = B.W[vslot * np + Ih];
+    hpp = B.W[2 * np + Ih];
   }
-  // inputs of the node's epilogue, loaded before the barrier
-  const long long I = base + sd * (owns ? plane(own) : 0);
-  df t[5];
   if (owns) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+    if (DIR == 2) {
+      if (!B.rhs_only && B.alpha.h != 0.0f) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) qnv[c] = B.qn[c * np + I];
+      }
+      if (B.S) sv = B.S[I];
+    }
+  }
+  if (main_plane) {
+    df f[5];
+    df_flux_vals<DIR>(qv, vel, pp, B.base[nz + (DIR == 2 ? g : other)], f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+  }
+  if (halo) {
+    df f[5];
+    df_flux_vals<DIR>(hq, hvel, hpp, B.base[nz + (DIR == 2 ? gh : other)], f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
   }
   __syncthreads();
   if (!owns) return;
@@ -437,8 +439,7 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_df_tline(const DfParam
     for (int c = 0; c < 5; ++c) B.T[c * np + I] = t[c];
   } else {
     bool bad = false;
-    const int yy = other, gz = plane(own);
-    df_finish_node(P, B, q, B.qn, B.out, I, x, yy, gz, t, bad);
+    df_finish_vals(P, B, qv, qnv, sv, B.base[g], B.out, I, x, other, g, t, bad);
     if (bad) *B.flag = 1;
   }
 }

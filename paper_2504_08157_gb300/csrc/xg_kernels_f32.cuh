@@ -164,66 +164,43 @@ __global__ void __launch_bounds__(kXThreads) k_f_line_x(const FParams P, const F
 // One thread per node over (32 x-columns) x (K segments along DIR) tiles, as
 // k_df_tline; DIR = 1 adds the y part into T, DIR = 2 finishes the node.
 template <int DIR>
-__device__ __forceinline__ void f_flux_dir(const float* __restrict__ q, const float* __restrict__ W,
-                                           long long np, long long I, float Th0, float (&f)[5]) {
-  const float mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
-  if (DIR == 1) {
-    const float v = W[I], pp = W[2 * np + I];
-    f[0] = mv;
-    f[1] = mu * v;
-    f[2] = fmaf(mv, v, pp);
-    f[3] = mw * v;
-    f[4] = (Th0 + tp) * v;
-  } else {
-    const float w = W[np + I], pp = W[2 * np + I];
-    f[0] = mw;
-    f[1] = mu * w;
-    f[2] = mv * w;
-    f[3] = fmaf(mw, w, pp);
-    f[4] = (Th0 + tp) * w;
-  }
+__device__ __forceinline__ void f_flux_vals(const float (&qv)[5], float vel, float pp, float Th0,
+                                            float (&f)[5]) {
+  f[0] = qv[DIR + 1];
+  f[1] = qv[1] * vel;
+  f[2] = DIR == 1 ? fmaf(qv[2], vel, pp) : qv[2] * vel;
+  f[3] = DIR == 1 ? qv[3] * vel : fmaf(qv[3], vel, pp);
+  f[4] = (Th0 + qv[4]) * vel;
 }
 
-__device__ __forceinline__ void f_finish_node(const FParams& P, const FBufs& B,
-                                              const float* __restrict__ q,
-                                              const float* __restrict__ qn,
-                                              float* __restrict__ out, long long I, int x, int y,
-                                              int gz, float (&L)[5], bool& bad) {
+__device__ __forceinline__ void f_finish_vals(const FParams& P, const FBufs& B,
+                                              const float (&qv)[5], const float (&qnv)[5],
+                                              float sv, float rho0, float* __restrict__ out,
+                                              long long I, int x, int y, int gz, float (&L)[5],
+                                              bool& bad) {
   const long long np = P.np;
-  const float rp = q[I], mu = q[np + I], mv = q[2 * np + I];
-  L[1] = fmaf(P.f, mv, L[1]);
-  L[2] = fmaf(-P.f, mu, L[2]);
-  L[3] = fmaf(-P.g, rp, L[3]);
-  if (B.S) {
-    const df r0 = B.base[gz];
-    L[4] = fmaf(r0.h + rp, B.S[I], L[4]);
-  }
+  L[1] = fmaf(P.f, qv[2], L[1]);
+  L[2] = fmaf(-P.f, qv[1], L[2]);
+  L[3] = fmaf(-P.g, qv[0], L[3]);
+  if (B.S) L[4] = fmaf(rho0 + qv[0], sv, L[4]);
   if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = 0.0f;
   if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = 0.0f;
   if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0f;
-  if (B.rhs_only) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      out[c * np + I] = L[c];
-      bad |= f_nonfinite(L[c]);
-    }
-  } else if (B.alpha == 0.0f) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const float o = fmaf(B.dt, L[c], q[c * np + I]);
-      out[c * np + I] = o;
-      bad |= f_nonfinite(o);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const float o = fmaf(B.alpha, qn[c * np + I], B.beta * fmaf(B.dt, L[c], q[c * np + I]));
-      out[c * np + I] = o;
-      bad |= f_nonfinite(o);
-    }
+  for (int c = 0; c < 5; ++c) {
+    float o;
+    if (B.rhs_only) o = L[c];
+    else if (B.alpha == 0.0f) o = fmaf(B.dt, L[c], qv[c]);
+    else o = fmaf(B.alpha, qnv[c], B.beta * fmaf(B.dt, L[c], qv[c]));
+    out[c * np + I] = o;
+    bad |= f_nonfinite(o);
   }
 }
 
+// One thread per node over (32 x-columns) x (K segments along DIR) tiles, as
+// k_df_tline: every global load first, fluxes to shared memory, then each
+// thread assembles its node (DIR = 1 adds the y part into T, DIR = 2
+// finishes the node).
 template <int N, int DIR>
 __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams P, const FBufs B) {
   constexpr int K = tile_segments(N);
@@ -242,36 +219,59 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams 
   const long long np = P.np;
   const long long sd = DIR == 1 ? (long long)nx : (long long)nx * ny;
   const long long base = DIR == 1 ? x + (long long)nx * ny * other : x + (long long)nx * other;
-  const float* __restrict__ q = B.q;
-  const float* __restrict__ W = B.W;
   const bool has_left = s0 > 0 || per;
   auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
   auto th0 = [&](int g) -> float {
     const df t = B.base[nz + (DIR == 2 ? g : other)];
     return t.h + t.l;
   };
+  const int vslot = DIR == 1 ? 0 : 1;
 
   const int own = s0 * N + ty;
   const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
-  if (xin && ty <= kc * N) {
-    const int g = plane(own);
-    float f[5];
-    f_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+  const bool main_plane = xin && ty <= kc * N;
+  const bool halo = xin && has_left && ty < N;
+  const int g = plane(own);
+  const int gh = plane((s0 - 1) * N + ty);
+  const long long I = base + sd * (main_plane ? g : 0);
+  const long long Ih = base + sd * (halo ? gh : 0);
+
+  float qv[5], vel = 0.0f, pp = 0.0f, hq[5] = {0, 0, 0, 0, 0}, hvel = 0.0f, hpp = 0.0f;
+  float t[5], qnv[5] = {0, 0, 0, 0, 0}, sv = 0.0f;
+  if (main_plane) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+    for (int c = 0; c < 5; ++c) qv[c] = B.q[c * np + I];
+    vel = B.W[vslot * np + I];
+    pp = B.W[2 * np + I];
   }
-  if (xin && has_left && ty < N) {
-    const int g = plane((s0 - 1) * N + ty);
-    float f[5];
-    f_flux_dir<DIR>(q, W, np, base + sd * g, th0(g), f);
+  if (halo) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
+    for (int c = 1; c < 5; ++c) hq[c] = B.q[c * np + Ih];
+    hvel = B.W[vslot * np + Ih];
+    hpp = B.W[2 * np + Ih];
   }
-  const long long I = base + sd * (owns ? plane(own) : 0);
-  float t[5];
   if (owns) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+    if (DIR == 2) {
+      if (!B.rhs_only && B.alpha != 0.0f) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) qnv[c] = B.qn[c * np + I];
+      }
+      if (B.S) sv = B.S[I];
+    }
+  }
+  if (main_plane) {
+    float f[5];
+    f_flux_vals<DIR>(qv, vel, pp, th0(g), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+  }
+  if (halo) {
+    float f[5];
+    f_flux_vals<DIR>(hq, hvel, hpp, th0(gh), f);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
   }
   __syncthreads();
   if (!owns) return;
@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams 
     for (int c = 0; c < 5; ++c) B.T[c * np + I] = t[c];
   } else {
     bool bad = false;
-    f_finish_node(P, B, q, B.qn, B.out, I, x, other, plane(own), t, bad);
+    const df r0 = B.base[g];
+    f_finish_vals(P, B, qv, qnv, sv, r0.h, B.out, I, x, other, g, t, bad);
     if (bad) *B.flag = 1;
   }
 }
