@@ -16,7 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libxg.so")
 SOURCES = [os.path.join(HERE, "csrc", "xg_api.cu"), os.path.join(HERE, "csrc", "xg_noalloc.cu")]
-DEPENDS = SOURCES + [os.path.join(HERE, "csrc", "xg_kernels.cuh"), os.path.join(HERE, "csrc", "xg_setup.h"),
+DEPENDS = SOURCES + [os.path.join(HERE, "csrc", f) for f in
+                     ("xg_kernels.cuh", "xg_setup.h", "xg_df.cuh", "xg_kernels_df.cuh",
+                      "xg_kernels_f32.cuh", "xg_plane_f32.cuh")] + [
                      os.path.join(ROOT, "include", "xg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

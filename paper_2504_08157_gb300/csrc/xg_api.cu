@@ -217,6 +217,9 @@ cudaError_t configure_n(xg_ctx* c) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(xg::k_f_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(c->xsmem / 2));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(xg::k_f_plane_xy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)xg::PlaneLayoutF<N>::bytes);
   return e;
 }
 
@@ -241,17 +244,15 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
 
 template <int N>
 void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
-  dim3 gx(c->n[1], c->n[2]);
+  // x and y passes fused over element tiles of each level, then the z pass
+  constexpr int E = xg::plane_elems_f32(N);
+  dim3 gp((c->d.nel[0] + E - 1) / E, (c->d.nel[1] + E - 1) / E, c->n[2]);
   prof_mark(c, 0, false, st);
-  xg::k_f_line_x<N><<<gx, xg::kXThreads, c->xsmem / 2, st>>>(c->Pf, B);
+  xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
   prof_mark(c, 0, true, st);
   constexpr int K = xg::tile_segments(N);
   const dim3 blk(xg::kTileCols, K * N + 1);
   const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
-  dim3 gy(xb, (c->d.nel[1] + K - 1) / K, c->n[2]);
-  prof_mark(c, 1, false, st);
-  xg::k_f_tline<N, 1><<<gy, blk, 0, st>>>(c->Pf, B);
-  prof_mark(c, 1, true, st);
   dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);
   prof_mark(c, 2, false, st);
   xg::k_f_tline<N, 2><<<gz, blk, 0, st>>>(c->Pf, B);

@@ -1,0 +1,188 @@
+// xg_plane_f32.cuh -- FP32 precision form: the x and y passes fused into one
+// kernel over element-aligned tiles of one z-level.
+//
+// A CTA owns up to TS x TS nodes of a level (TS = N E: E elements per side;
+// the last tile of a walled direction also owns the wall node).  It loads the
+// state of a cross-shaped region -- its own rows extended by the N columns
+// before them and the one after (the x segments), and its own columns
+// extended likewise (the y segments) -- computes the primitives (u, v, w,
+// p') once per loaded node and keeps the x-fluxes and y-fluxes in shared
+// memory.  Each thread then evaluates its own nodes' x and y parts straight
+// from those tiles: an element-interior node one row of its segment, a face
+// node row 0 of its segment plus row N of the segment before (FP32 FMAs are
+// cheap next to the HBM traffic this kernel moves), and writes T = x part +
+// y part and W = (v, w, p') for the z pass.  Compared with separate x and y
+// passes this saves the y pass's re-reads of q and W and its
+// read-modify-write of T.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "xg_kernels_f32.cuh"
+
+namespace xg {
+
+__host__ __device__ constexpr int plane_elems_f32(int N) { return N >= 32 ? 1 : 32 / N; }
+constexpr int kPlaneThreads = 256;
+constexpr int kPlaneBatch = 2;
+
+// Shared-memory layout of one tile (floats), see k_f_plane_xy.
+template <int N>
+struct PlaneLayoutF {
+  static constexpr int E = plane_elems_f32(N);
+  static constexpr int TS = E * N;
+  static constexpr int LO = TS + 1;          // owned extent across the line (wall node included)
+  static constexpr int LX = TS + N + 1;      // loaded extent along the line
+  static constexpr int FX = 5 * LO * LX;     // x-fluxes [5][LO][LX]
+  static constexpr int FY = 5 * LX * LO;     // y-fluxes [5][LX][LO]
+  static constexpr int total = FX + FY;
+  static constexpr size_t bytes = sizeof(float) * (size_t)total;
+};
+
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, const FBufs B) {
+  using L = PlaneLayoutF<N>;
+  constexpr int E = L::E, LO = L::LO, LX = L::LX;
+  extern __shared__ float sm_plane[];
+  float* FX = sm_plane;                   // [c][j][i + N]
+  float* FY = FX + L::FX;                 // [c][j + N][i]
+  auto fx = [&](int c, int j, int ii) -> float& { return FX[(c * LO + j) * LX + ii]; };
+  auto fy = [&](int c, int jj, int i) -> float& { return FY[(c * LX + jj) * LO + i]; };
+
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int z = blockIdx.z;
+  const int ex0 = blockIdx.x * E, ey0 = blockIdx.y * E;
+  const int ekx = min(E, P.nseg[0] - ex0), eky = min(E, P.nseg[1] - ey0);
+  const int x0 = ex0 * N, y0 = ey0 * N;
+  const bool wallx = !P.per[0] && ex0 + ekx == P.nseg[0];
+  const bool wally = !P.per[1] && ey0 + eky == P.nseg[1];
+  const int ox = ekx * N + (wallx ? 1 : 0), oy = eky * N + (wally ? 1 : 0);
+  const bool hxl = ex0 > 0 || P.per[0];
+  const bool hyl = ey0 > 0 || P.per[1];
+  const long long np = P.np;
+  const long long zoff = (long long)nx * ny * z;
+  const df rho0d = B.base[z], Th0d = B.base[nz + z], p0 = B.base[2 * nz + z];
+  const df iTh0 = B.base[3 * nz + z];
+  const float rho0 = rho0d.h + rho0d.l, Th0 = Th0d.h + Th0d.l;
+  const float* __restrict__ q = B.q;
+  float* __restrict__ Wo = B.W;
+  float* __restrict__ To = B.T;
+
+  // ---- pointwise over the cross: local (i, j) with i in [-N, ekx N] and
+  // j in [-N, eky N]; x-fluxes on owned rows (i extended by the segment
+  // before and the end face), y-fluxes on owned columns (j likewise).  The
+  // cross is enumerated as the owned rows at full width, then the owned
+  // columns of the rows above and below them.
+  // Each thread takes kPlaneBatch items per pass and issues all their loads
+  // before any arithmetic, to keep enough bytes in flight.
+  const int wx = ekx * N + N + 1, wy = eky * N + N + 1;
+  const int nrow = oy * wx;                       // owned rows, full width
+  const int nitem = nrow + ox * (wy - oy);        // + owned columns, remaining rows
+  for (int base = threadIdx.x; base < nitem; base += kPlaneBatch * blockDim.x) {
+    int ib[kPlaneBatch], jb[kPlaneBatch];
+    long long Ib[kPlaneBatch];
+    float qb[kPlaneBatch][5];
+#pragma unroll
+    for (int u = 0; u < kPlaneBatch; ++u) {
+      const int idx = base + u * blockDim.x;
+      int i = -N - 1, j = 0;                      // i = -N - 1 marks "nothing to do"
+      if (idx < nrow) {
+        i = idx % wx - N;
+        j = idx / wx;
+      } else if (idx < nitem) {
+        const int r = (idx - nrow) / ox;
+        i = (idx - nrow) % ox;
+        j = r < N ? r - N : oy + (r - N);          // N rows before, then the rows after
+      }
+      const bool needx = j >= 0 && j < oy && (i >= 0 || hxl) && i >= -N;
+      const bool needy = i >= 0 && i < ox && (j >= 0 || hyl);
+      if (!needx && !needy) i = -N - 1;
+      ib[u] = i;
+      jb[u] = j;
+      int gx = x0 + i, gy = y0 + j;
+      if (gx < 0) gx += nx;                       // only reached when periodic (hxl)
+      if (gy < 0) gy += ny;
+      if (gx >= nx) gx -= nx;                     // the periodic end face
+      if (gy >= ny) gy -= ny;
+      Ib[u] = zoff + gx + (long long)nx * gy;
+      if (i >= -N) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) qb[u][c] = q[c * np + Ib[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPlaneBatch; ++u) {
+      const int i = ib[u], j = jb[u];
+      if (i < -N) continue;
+      const long long I = Ib[u];
+      const float mu = qb[u][1], mv = qb[u][2], mw = qb[u][3], tp = qb[u][4];
+      const float ir = __frcp_rn(rho0 + qb[u][0]);
+      const float u_ = mu * ir, v = mv * ir, w = mw * ir;
+      const float pp = f_pressure_pert(P, tp, p0, iTh0);
+      const float Th = Th0 + tp;
+      const bool inx = i >= 0 && i < ox;
+      const bool iny = j >= 0 && j < oy;
+      if (inx && iny) {
+        Wo[I] = v;
+        Wo[np + I] = w;
+        Wo[2 * np + I] = pp;
+      }
+      if (iny) {                                  // x-fluxes on owned rows
+        const int ii = i + N;
+        fx(0, j, ii) = mu;
+        fx(1, j, ii) = fmaf(mu, u_, pp);
+        fx(2, j, ii) = mv * u_;
+        fx(3, j, ii) = mw * u_;
+        fx(4, j, ii) = Th * u_;
+      }
+      if (inx) {                                  // y-fluxes on owned columns
+        const int jj = j + N;
+        fy(0, jj, i) = mv;
+        fy(1, jj, i) = mu * v;
+        fy(2, jj, i) = fmaf(mv, v, pp);
+        fy(3, jj, i) = mw * v;
+        fy(4, jj, i) = Th * v;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- each owned node: x part + y part from the flux tiles
+  for (int idx = threadIdx.x; idx < ox * oy; idx += blockDim.x) {
+    const int i = idx % ox, j = idx / ox;
+    const long long I = zoff + (x0 + i) + (long long)nx * (y0 + j);
+    const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
+    const int sy = min(j / N, eky - 1), ay = j - sy * N;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float f[N + 1], v = 0.0f;
+#pragma unroll
+      for (int l = 0; l <= N; ++l) f[l] = fx(c, j, N + sx * N + l);
+      v = f_row_from<N, 0>(P, ax, f, v);
+      if (ax == 0 || ax == N) {
+        if (ax == 0 && (sx > 0 || hxl)) {
+#pragma unroll
+          for (int l = 0; l <= N; ++l) f[l] = fx(c, j, sx * N + l);
+          v = f_row_from<N, 0>(P, N, f, v);
+        } else {
+          v = v + v;                                  // wall: the one-sided row counts twice
+        }
+      }
+#pragma unroll
+      for (int l = 0; l <= N; ++l) f[l] = fy(c, N + sy * N + l, i);
+      float w = f_row_from<N, 1>(P, ay, f, 0.0f);
+      if (ay == 0 || ay == N) {
+        if (ay == 0 && (sy > 0 || hyl)) {
+#pragma unroll
+          for (int l = 0; l <= N; ++l) f[l] = fy(c, sy * N + l, i);
+          w = f_row_from<N, 1>(P, N, f, w);
+        } else {
+          w = w + w;
+        }
+      }
+      To[c * np + I] = v + w;
+    }
+  }
+}
+
+}  // namespace xg

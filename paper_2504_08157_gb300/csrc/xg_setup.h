@@ -11,6 +11,7 @@
 #include "xg_kernels.cuh"
 #include "xg_kernels_df.cuh"
 #include "xg_kernels_f32.cuh"
+#include "xg_plane_f32.cuh"
 
 namespace xg {
 
