@@ -46,8 +46,14 @@ METRIC = "RK-stage GDOF/s vs plain FP64 at stated L2 error; % of HBM roofline"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", f)
-               for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh")]
+               for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh", "xg_kernels_f32.cuh",
+                         "xg_plane_f32.cuh", "xg_batch.cu")]
 KERNELS = ("k_line_x", "k_line_y", "k_line_z")
+# the kernels behind the three timing slots in each precision (the FP32 form
+# fuses the x and y passes into one plane kernel; slot 1 stays empty)
+KERNEL_NAMES = {0: ("k_line_x", "k_line_y", "k_line_z"),
+                2: ("k_df_line_x", "k_df_line_y", "k_df_tline"),
+                1: ("k_f_plane_xy", "-", "k_f_tline")}
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -212,6 +218,10 @@ def cpu_sample_workload(name):
     from inputs import workloads as W
     if name == "tc":
         return W.tc(nel=(16, 16, 16))
+    if name == "batch":
+        specs = W.batch_specs()
+        sizes = [s["N"] ** 3 * s["nel"][0] * s["nel"][1] * s["nel"][2] for s in specs]
+        return W.batch_instance(specs[int(np.argsort(sizes)[len(sizes) // 2])])
     return W.bubble()
 
 
@@ -334,20 +344,21 @@ def run_xg(args, world, rank, local):
     # roofline of the dominant kernel (largest share of device time)
     k = int(np.argmax(kms))
     name = KERNELS[k]
+    kname = KERNEL_NAMES[prec][k]
     avg_ms = kms[k] / max(klaunch[k], 1)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    per_launch = {KERNELS[i]: round(kms[i] / max(klaunch[i], 1), 4) for i in range(3)}
+    per_launch = {KERNEL_NAMES[prec][i]: round(kms[i] / max(klaunch[i], 1), 4)
+                  for i in range(3) if klaunch[i]}
     if prec == xg.XG_FP64:
         flops = flops_per_node(name, wl["N"]) * cfg["nodes"]
         achieved = flops / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
+        roof = {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic_per_launch(name),
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic_per_launch(kname),
                 "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
         vb = 8 if prec == xg.XG_DF64 else 4          # bytes per stored value
-        kname = ("k_df_" if prec == xg.XG_DF64 else "k_f_") + name[2:]
         nbytes = KERNEL_BYTES_PER_NODE[name] * vb / 8 * cfg["nodes"]
         achieved = nbytes / (avg_ms / 1e3) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1),
@@ -391,10 +402,15 @@ def run_xg(args, world, rank, local):
         xg.xg_destroy(c2)
         return {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": dtype,
                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
-                "kernel_ms_per_launch": {KERNELS[i]: round(kmsp[i] / max(klp[i], 1), 4)
-                                         for i in range(3)}}
+                "kernel_ms_per_launch": {KERNEL_NAMES[p][i]: round(kmsp[i] / max(klp[i], 1), 4)
+                                         for i in range(3) if klp[i]}}
     plain = side_run(xg.XG_FP64, "f64") if prec != xg.XG_FP64 and not args.no_plain else None
     fp32 = side_run(xg.XG_FP32, "f32") if prec != xg.XG_FP32 and not args.no_plain else None
+    batched = None
+    if not args.no_plain and not args.no_batch:
+        batched = batch_measure(xg, torch, dev, stream, world, local, max(1, min(K, 10)), 3,
+                                False, compare=True, oracle_check=rank == 0)
+        batched.pop("clocks", None)
 
     cpu, l2 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -424,10 +440,225 @@ def run_xg(args, world, rank, local):
                "fp32_form": fp32,
                "fp32_speedup_vs_plain_fp64": (round(fp32["value"] / plain["value"], 3)
                                               if fp32 and plain else None),
+               "batched_form": batched,
                "l2_error_vs_oracle": l2,
                "hbm_roofline_frac": round(hbm_frac, 4),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(sum(klaunch))}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batched persistent form
+
+BATCH_BYTES_PER_NODE = 4 * (5 + 3 + 5) + 4 * (5 + 2 + 5 + 1 + 5 * 2 / 3 + 5)   # plane + z passes, FP32
+
+
+def batch_workloads(count=96):
+    from inputs import workloads as W
+    return [W.batch_instance(s) for s in W.batch_specs()[:count]]
+
+
+def make_batch(xg, torch, wls, dev):
+    descs = []
+    for wl in wls:
+        ph = wl["phys"]
+        descs.append(xg.mesh_desc(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"],
+                                  f=ph["f"], g=ph["g"], R=ph["R"], cp=ph["cp"], cv=ph["cv"],
+                                  p_a=ph["p_a"], precision=xg.XG_FP32))
+    b = xg.xg_batch_create(descs)
+    for i, wl in enumerate(wls):
+        c = xg.xg_batch_instance(b, i)
+        xg.xg_set_state(c, torch.from_numpy(wl["q"]).to(dev), torch.from_numpy(wl["rho0"]).to(dev),
+                        torch.from_numpy(wl["Theta0"]).to(dev))
+        if wl["S_theta"] is not None:
+            xg.xg_set_forcing(c, torch.from_numpy(wl["S_theta"]).to(dev))
+    torch.cuda.synchronize()
+    return b
+
+
+def batch_describe(wls):
+    from inputs import workloads as W
+    dof_u = sum(W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[0] for wl in wls)
+    dof_p = sum(W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[1] for wl in wls)
+    orders = {str(n): sum(1 for wl in wls if wl["N"] == n) for n in (3, 4, 5, 6)}
+    sizes = [W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[0] // 5 for wl in wls]
+    return dict(workload="batch of %d limited-area instances, 512x512x20 km, nel 4..24 x 4..24 x "
+                         "4..12, N 3..6, FP32 (ppw)" % len(wls),
+                instances=len(wls), nodes=dof_u // 5, dof_unique=dof_u, dof_paper=dof_p,
+                orders=orders, nodes_min=min(sizes), nodes_max=max(sizes),
+                l2="inputs larger than L2 (the batch's FP32 states total %.0f MB > 129 MB L2)"
+                   % (dof_u * 4 / 1e6),
+                parallelism="replicas")
+
+
+def batch_measure(xg, torch, dev, stream, world, local, K, Wm, sample_clocks, compare,
+                  oracle_check, count=96):
+    """The batched form on the 96-instance workload: autotune, then K steps
+    in one persistent launch timed with CUDA events; with ``compare`` also
+    the same instances stepped through single contexts (FP32, one launch
+    sequence per instance) and in plain FP64."""
+    wls = batch_workloads(count)
+    cfg = batch_describe(wls)
+    dts = [wl["dt"] for wl in wls]
+    dof_u = cfg["dof_unique"]
+    b = make_batch(xg, torch, wls, dev)
+    out = {}
+    try:
+        tune = xg.xg_batch_autotune(b, dts, trial_steps=2, stream=stream.cuda_stream)
+        xg.xg_batch_step(b, dts, Wm, stream=stream.cuda_stream)
+        clocks = ClockSampler(local) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xg.xg_batch_step(b, dts, K, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = reduce_max(e0.elapsed_time(e1), world)
+        out["clocks"] = clocks.stop() if clocks else None
+        out["value"] = round(dof_u * 3 * K * world / (ms / 1e3) / 1e9, 4)
+        out["unit"] = "GDOF/s"
+        out["dtype"] = "f32"
+        out["ms_per_step"] = round(ms / K, 4)
+        out["steps"] = K
+        out["launches_per_call"] = 1
+        out["tuning"] = tune.as_dict()
+        out["config"] = cfg
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = BATCH_BYTES_PER_NODE * cfg["nodes"] * 3 * K / (ms / 1e3) / 1e9
+        out["roofline"] = {"kernel": "k_batch", "bound": "hbm", "achieved": round(achieved, 1),
+                           "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                           "traffic": traffic_per_launch("k_batch"),
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+                           "bytes_per_node_stage": round(BATCH_BYTES_PER_NODE, 2),
+                           "launch": "one persistent launch of %d steps (%d stages)" % (K, 3 * K)}
+        if oracle_check:
+            # one right-hand side of the whole batch, with the smallest
+            # instance set to a seeded smooth random state (at the vortex
+            # state several tendencies are cancellation residuals or exactly
+            # zero), against the FP64 oracle
+            from inputs import workloads as W
+            from oracle import euler as E, mesh as M
+            outs = [torch.empty((5, xg.xg_mesh_np(xg.xg_batch_instance(b, i))), dtype=torch.float64,
+                                device=dev) for i in range(len(wls))]
+            i = int(np.argmin([o.shape[1] for o in outs]))
+            wl = W.batch_instance(W.batch_specs()[i], state="random", seed=i + 1)
+            xg.xg_set_state(xg.xg_batch_instance(b, i), torch.from_numpy(wl["q"]).to(dev),
+                            stream=stream.cuda_stream)
+            xg.xg_batch_rhs(b, outs, stream=stream.cuda_stream)
+            m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"])
+            ref = E.rhs(m, wl["q"], E.Base(wl["rho0"], wl["Theta0"]), wl["S_theta"],
+                        E.Physics(**wl["phys"]))
+            got = outs[i].cpu().numpy()
+            del outs
+            out["l2_error_vs_oracle"] = {
+                "instance": i, "nel": list(wl["nel"]), "N": wl["N"],
+                "rel_l2": [float("%.3e" % (np.linalg.norm(got[v] - ref[v]) /
+                                           max(np.linalg.norm(ref[v]), 1e-300))) for v in range(5)],
+                "what": "one batched right-hand side (all 96 instances in one launch) of the "
+                        "smallest instance, at a seeded smooth random state plus its vortex, vs "
+                        "the FP64 oracle, relative L2 per variable"}
+    finally:
+        xg.xg_batch_destroy(b)
+    if compare:
+        def sequential(p, Kp):
+            ctxs = [make_ctx(xg, torch, wl, dev, p) for wl in wls]
+            try:
+                for c, wl in zip(ctxs, wls):
+                    xg.xg_step(c, wl["dt"], 1, stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for c, wl in zip(ctxs, wls):
+                    xg.xg_step(c, wl["dt"], Kp, stream=stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                msq = e0.elapsed_time(e1)
+            finally:
+                for c in ctxs:
+                    xg.xg_destroy(c)
+            return {"value": round(dof_u * 3 * Kp / (msq / 1e3) / 1e9, 4), "unit": "GDOF/s",
+                    "ms_per_step": round(msq / Kp, 4), "steps": Kp}
+        out["per_instance_fp32"] = sequential(xg.XG_FP32, K)
+        out["per_instance_fp32"]["what"] = ("the same instances through single XG_FP32 contexts, "
+                                            "one xg_step call per instance")
+        out["plain_fp64"] = sequential(xg.XG_FP64, max(1, K // 2))
+        out["plain_fp64"]["what"] = "the same instances in native FP64, one context per instance"
+        out["speedup_vs_plain_fp64"] = round(out["value"] / out["plain_fp64"]["value"], 3)
+        out["speedup_vs_per_instance_fp32"] = round(out["value"] / out["per_instance_fp32"]["value"], 3)
+    return out
+
+
+def run_batch(args, world, rank, local):
+    import torch
+    from paper_2504_08157_gb300 import build, xg
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+    K, Wm = args.steps, args.warmup
+    res = batch_measure(xg, torch, dev, stream, world, local, K, Wm, True,
+                        compare=not args.no_plain, oracle_check=rank == 0 and world == 1,
+                        count=args.instances)
+    cfg = res.pop("config")
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: every instance's state from pinned
+        # host memory, one batched step, every state back to pinned memory
+        wls = batch_workloads(args.instances)
+        dts = [wl["dt"] for wl in wls]
+        b = make_batch(xg, torch, wls, dev)
+        try:
+            hin = [torch.from_numpy(wl["q"]).pin_memory() for wl in wls]
+            hout = [torch.empty_like(h).pin_memory() for h in hin]
+            Ke = max(1, min(K, 5))
+            xg.xg_batch_step(b, dts, 1, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(Ke):
+                for i, h in enumerate(hin):
+                    xg.xg_set_state(xg.xg_batch_instance(b, i), h, stream=stream.cuda_stream)
+                xg.xg_batch_step(b, dts, 1, stream=stream.cuda_stream)
+                for i, h in enumerate(hout):
+                    xg.xg_get_state(xg.xg_batch_instance(b, i), h, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            te = reduce_max(time.perf_counter() - t0, world)
+            nbytes = sum(h.numel() * 8 for h in hin)
+            e2e = {"value": round(cfg["dof_unique"] * 3 * Ke * world / te / 1e9, 4), "unit": "GDOF/s",
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": Ke}
+        finally:
+            xg.xg_batch_destroy(b)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sw = cpu_sample_workload("batch")
+        g, steps, secs, _ = time_oracle(sw)
+        cpu = {"value": round(g, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": "batch instance %dx%dx%d N=%d, %d SSP-RK3 steps in %.1f s (numpy, 1 thread)"
+                         % (*sw["nel"], sw["N"], steps, secs)}
+    if rank == 0:
+        roof = res.pop("roofline")
+        clk = res.pop("clocks")
+        out = {"metric": METRIC, "value": res.pop("value"), "unit": "GDOF/s", "n_gpus": world,
+               "steps": K, "warmup": Wm, "ms_per_step": res.pop("ms_per_step"),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "precision": "fp32", "data": "synthetic", "impl": "xg", "config": cfg,
+               "gdof_paper_convention": None, **res, "roofline": roof, "cpu_baseline": cpu,
+               "e2e": e2e, "clocks": clk, "gpu_launches": 1}
+        out["gdof_paper_convention"] = round(out["value"] * cfg["dof_paper"] / cfg["dof_unique"], 4)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
@@ -465,6 +696,14 @@ def run_reference(args, world, rank, local):
 
 def workload_desc_only(name):
     from inputs import workloads as W
+    if name == "batch":
+        specs = W.batch_specs()
+        dof = [W.dof_counts(sp["nel"], sp["N"], (True, True, False)) for sp in specs]
+        return dict(workload="batch of %d limited-area instances, 512x512x20 km, nel 4..24 x "
+                             "4..24 x 4..12, N 3..6, FP32 (ppw)" % len(specs),
+                    instances=len(specs), nodes=sum(d[0] for d in dof) // 5,
+                    dof_unique=sum(d[0] for d in dof), dof_paper=sum(d[1] for d in dof),
+                    parallelism="replicas")
     if name == "tc":
         nel, N, per, dt = (128, 128, 16), 4, (True, True, False), 0.1
         label = "tc"
@@ -484,7 +723,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["xg", "reference"], default="xg")
-    ap.add_argument("--workload", choices=["tc", "bubble"], default="tc")
+    ap.add_argument("--workload", choices=["tc", "bubble", "batch"], default="tc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
@@ -492,6 +731,10 @@ def main():
                          "fp64: native FP64; fp32: the FP32 precision form")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain-FP64 and FP32-form comparison runs")
+    ap.add_argument("--instances", type=int, default=96,
+                    help="instances of the batched workload (the first ones of the seeded list)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-form comparison in the cyclone line")
     ap.add_argument("--nel", type=int, nargs=3, default=None,
                     help="element counts of a smaller cyclone box (same spacing), for profiling")
     args = ap.parse_args()
@@ -500,6 +743,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank, local)
+    elif args.workload == "batch":
+        run_batch(args, world, rank, local)
     else:
         run_xg(args, world, rank, local)
 

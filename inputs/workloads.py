@@ -4,6 +4,14 @@
                (33^3 nodes), isentropic theta_0 = 300 K, +2 K cosine bubble of
                radius 2 km centred at (5, 5, 2) km, no-flux walls on all six
                faces, no Coriolis, no heating, dt = 0.02 s.
+``batch``   -- the batched form: ``count`` independent limited-area boxes of
+               512 x 512 x 20 km (doubly periodic laterally, no-flux bottom
+               and top, stable sounding, f = 5e-5 1/s), each with seeded
+               element counts (uniform in 4..24 horizontally, 4..12
+               vertically), order N uniform in {3, 4, 5, 6}, its own
+               modified-Rankine vortex (Vmax U(10, 30) m/s at radius
+               U(30, 80) km) and heating ring, and a step dt at the acoustic
+               Courant number of ``tc`` (0.1 s for 216 m vertical spacing).
 ``tc``      -- tropical-cyclone-shaped box: 1024 x 1024 x 20 km, 128 x 128 x 16
                elements, N = 4, doubly periodic laterally with no-flux bottom
                and top (512 x 512 x 65 nodes), stable sounding N_BV = 0.01 1/s,
@@ -22,6 +30,7 @@ import numpy as np
 
 from . import atmosphere as atm
 from . import grid
+from . import rng
 
 PHYS = dict(g=9.81, R=287.0, cp=1004.5, cv=717.5, p_a=1.0e5)
 
@@ -89,3 +98,46 @@ def dof_counts(nel, N, periodic):
     global nodes, and the paper's convention N_e (N+1)^3 x 5 (Sec. 5.2)."""
     n = [N * nel[d] + (0 if periodic[d] else 1) for d in range(3)]
     return 5 * n[0] * n[1] * n[2], 5 * nel[0] * nel[1] * nel[2] * (N + 1) ** 3
+
+
+BATCH_BOX = (512.0e3, 512.0e3, 20.0e3)
+
+
+def batch_specs(count=96, seed=4096):
+    """Seeded per-instance parameters of the batched form: a list of dicts
+    with nel, N, vmax, rmax, ring radius and peak, centre offset."""
+    u = rng.uniform(seed, 8 * count).reshape(count, 8)
+    specs = []
+    for i in range(count):
+        nel = (4 + int(21 * u[i, 0]), 4 + int(21 * u[i, 1]), 4 + int(9 * u[i, 2]))
+        specs.append(dict(nel=nel, N=3 + int(4 * u[i, 3]), vmax=10.0 + 20.0 * u[i, 4],
+                          rmax=30.0e3 + 50.0e3 * u[i, 5], ring_peak=5.0 + 10.0 * u[i, 6],
+                          centre=(40.0e3 * (u[i, 7] - 0.5), -40.0e3 * (u[i, 7] - 0.5))))
+    return specs
+
+
+def _min_vertical_spacing(nel_z, N):
+    xi = grid.lgl_points(N)
+    return (BATCH_BOX[2] / nel_z) * (xi[1] - xi[0]) / 2.0
+
+
+def batch_instance(spec, state="initial", seed=1):
+    """Workload dict of one instance of the batched form (as ``tc``)."""
+    nel, N = spec["nel"], spec["N"]
+    lo = (-BATCH_BOX[0] / 2, -BATCH_BOX[1] / 2, 0.0)
+    hi = (BATCH_BOX[0] / 2, BATCH_BOX[1] / 2, BATCH_BOX[2])
+    periodic = (True, True, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.stable_sounding(ax[2], nbv=0.01)
+    n_xy = ax[0].size * ax[1].size
+    c = spec["centre"]
+    q = atm.vortex_state(X, Y, Z, rho0, n_xy, c, vmax=spec["vmax"], rmax=spec["rmax"])
+    if state == "random":
+        q += atm.smooth_random_state(X, Y, Z, lo, hi, periodic, seed)
+    elif state != "initial":
+        raise ValueError(state)
+    S = atm.heating(X, Y, Z, c, seed=seed, ncells=0, ring_peak=spec["ring_peak"],
+                    ring_r=0.8 * spec["rmax"])
+    dt = 0.1 * _min_vertical_spacing(nel[2], N) / _min_vertical_spacing(16, 4)
+    return dict(name="batch", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=5.0e-5), dt=dt, q=q, rho0=rho0, Theta0=Th0, S_theta=S)

@@ -17,6 +17,7 @@
 #include "xg_kernels.cuh"
 #include "xg_kernels_df.cuh"
 #include "xg_setup.h"
+#include "xg_ctx.h"
 
 using xg::DfBufs;
 using xg::DfParams;
@@ -30,43 +31,6 @@ __device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(df v) { return df_to_double(v); }
 }  // namespace xg
 
-struct xg_ctx {
-  xg_mesh_desc d;
-  int n[3];
-  long long np;
-  int dev;
-  LineParams P;
-  DfParams Pdf;          // launch constants of the double-float kernels
-  xg::FParams Pf;        // launch constants of the FP32 kernels
-  bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
-  bool f32 = false;      // precision XG_FP32: device arrays hold floats
-  double* A = nullptr;   // q^n (the state)
-  double* Bq = nullptr;  // stage buffer
-  double* Cq = nullptr;  // stage buffer
-  double* Dq = nullptr;  // q^{n+1}; swapped with A after every step
-  double* W = nullptr;   // [3][np] primitives v, w, p'
-  double* T = nullptr;   // [5][np] partial tendency
-  double* S = nullptr;   // [np] heating
-  double* base = nullptr;  // [4][nz]
-  double* wasm = nullptr;  // assembled 1-D mass weights: [n_x + n_y + n_z], J folded into x
-  double* partial = nullptr;  // [kDiagBlocks][5] per-block conservation sums
-  double* hdiag = nullptr;    // pinned [5]
-  int* flag = nullptr;
-  int* hflag = nullptr;  // pinned
-  bool has_state = false;
-  bool has_base = false;
-  bool has_forcing = false;
-  bool failed = false;
-  int chunk_y = 1, nchunk_y = 1, chunk_z = 1, nchunk_z = 1;
-  size_t xsmem = 0;
-  // profiling: event pairs recorded around launches since the last fold
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  std::vector<int> ev_kernel;   // kernel id of each recorded pair
-  size_t ev_used = 0;           // pairs recorded
-  double k_ms[3] = {0, 0, 0};
-  long long k_launches[3] = {0, 0, 0};
-};
 
 namespace {
 
@@ -209,17 +173,10 @@ void launch_stage_n(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
 
 template <int N>
 cudaError_t configure_n(xg_ctx* c) {
-  cudaError_t e = cudaFuncSetAttribute(xg::k_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)c->xsmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xg::k_df_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)c->xsmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xg::k_f_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(c->xsmem / 2));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xg::k_f_plane_xy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)xg::PlaneLayoutF<N>::bytes);
+  cudaError_t e = xg::raise_dynamic_smem(xg::k_line_x<N>, c->xsmem);
+  if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_df_line_x<N>, c->xsmem);
+  if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_line_x<N>, c->xsmem / 2);
+  if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_plane_xy<N>, xg::PlaneLayoutF<N>::bytes);
   return e;
 }
 

@@ -1,0 +1,52 @@
+// xg_ctx.h -- the context behind the opaque xg_ctx handle of include/xg.h:
+// one mesh, its launch constants and its device buffers.  Shared by the
+// single-instance entry points (xg_api.cu) and the batched persistent form
+// (xg_batch.cu), which advances many contexts in one launch.
+#pragma once
+
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/xg.h"
+#include "xg_kernels.cuh"
+#include "xg_kernels_df.cuh"
+#include "xg_kernels_f32.cuh"
+
+struct xg_ctx {
+  xg_mesh_desc d;
+  int n[3];
+  long long np;
+  int dev;
+  xg::LineParams P;
+  xg::DfParams Pdf;      // launch constants of the double-float kernels
+  xg::FParams Pf;        // launch constants of the FP32 kernels
+  bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
+  bool f32 = false;      // precision XG_FP32: device arrays hold floats
+  double* A = nullptr;   // q^n (the state)
+  double* Bq = nullptr;  // stage buffer
+  double* Cq = nullptr;  // stage buffer
+  double* Dq = nullptr;  // q^{n+1}; swapped with A after every step
+  double* W = nullptr;   // [3][np] primitives v, w, p'
+  double* T = nullptr;   // [5][np] partial tendency
+  double* S = nullptr;   // [np] heating
+  double* base = nullptr;  // [4][nz]
+  double* wasm = nullptr;  // assembled 1-D mass weights: [n_x + n_y + n_z], J folded into x
+  double* partial = nullptr;  // [kDiagBlocks][5] per-block conservation sums
+  double* hdiag = nullptr;    // pinned [5]
+  int* flag = nullptr;
+  int* hflag = nullptr;  // pinned
+  bool has_state = false;
+  bool has_base = false;
+  bool has_forcing = false;
+  bool failed = false;
+  int chunk_y = 1, nchunk_y = 1, chunk_z = 1, nchunk_z = 1;
+  size_t xsmem = 0;
+  // profiling: event pairs recorded around launches since the last fold
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> ev_kernel;   // kernel id of each recorded pair
+  size_t ev_used = 0;           // pairs recorded
+  double k_ms[3] = {0, 0, 0};
+  long long k_launches[3] = {0, 0, 0};
+};

@@ -201,21 +201,33 @@ __device__ __forceinline__ void f_finish_vals(const FParams& P, const FBufs& B,
 // k_df_tline: every global load first, fluxes to shared memory, then each
 // thread assembles its node (DIR = 1 adds the y part into T, DIR = 2
 // finishes the node).
-template <int N, int DIR>
-__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams P, const FBufs B) {
-  constexpr int K = tile_segments(N);
+//
+// f_tline_tile is the body of one tile (bx: 32-column block, by: K-segment
+// block, other: the y index for DIR = 2, the z index for DIR = 1) for the
+// thread (tx, ty), ty < K N + 1 (larger ty own nothing); Fs is the tile's
+// shared flux array [5][K N + N + 1][32].
+// CG selects L2-only loads (ld.global.cg) for every array a launch may
+// itself have written, which a persistent launch that runs several passes
+// needs; the per-pass kernels use ordinary loads.
+template <bool CG>
+__device__ __forceinline__ float ldf(const float* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <int N, int DIR, bool CG, int K = tile_segments(N)>
+__device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, int bx, int by,
+                                             int other, int tx, int ty, float* Fsm) {
   constexpr int NS = K * N + N + 1;
-  __shared__ float Fs[5][NS][kTileCols];
+  auto Fs = reinterpret_cast<float(*)[NS][kTileCols]>(Fsm);
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
   const int nd = P.n[DIR];
   const int nseg = P.nseg[DIR];
   const bool per = P.per[DIR] != 0;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * kTileCols + tx;
+  const int x = bx * kTileCols + tx;
   const bool xin = x < nx;
-  const int s0 = blockIdx.y * K;
+  const int s0 = by * K;
   const int kc = min(K, nseg - s0);
-  const int other = blockIdx.z;
   const long long np = P.np;
   const long long sd = DIR == 1 ? (long long)nx : (long long)nx * ny;
   const long long base = DIR == 1 ? x + (long long)nx * ny * other : x + (long long)nx * other;
@@ -240,23 +252,23 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams 
   float t[5], qnv[5] = {0, 0, 0, 0, 0}, sv = 0.0f;
   if (main_plane) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) qv[c] = B.q[c * np + I];
-    vel = B.W[vslot * np + I];
-    pp = B.W[2 * np + I];
+    for (int c = 0; c < 5; ++c) qv[c] = ldf<CG>(B.q + c * np + I);
+    vel = ldf<CG>(B.W + vslot * np + I);
+    pp = ldf<CG>(B.W + 2 * np + I);
   }
   if (halo) {
 #pragma unroll
-    for (int c = 1; c < 5; ++c) hq[c] = B.q[c * np + Ih];
-    hvel = B.W[vslot * np + Ih];
-    hpp = B.W[2 * np + Ih];
+    for (int c = 1; c < 5; ++c) hq[c] = ldf<CG>(B.q + c * np + Ih);
+    hvel = ldf<CG>(B.W + vslot * np + Ih);
+    hpp = ldf<CG>(B.W + 2 * np + Ih);
   }
   if (owns) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+    for (int c = 0; c < 5; ++c) t[c] = ldf<CG>(B.T + c * np + I);
     if (DIR == 2) {
       if (!B.rhs_only && B.alpha != 0.0f) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) qnv[c] = B.qn[c * np + I];
+        for (int c = 0; c < 5; ++c) qnv[c] = ldf<CG>(B.qn + c * np + I);
       }
       if (B.S) sv = B.S[I];
     }
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams 
     for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
   }
   __syncthreads();
-  if (!owns) return;
+  if (!owns) return;   // no barrier follows: the caller synchronises before reusing Fs
 
   const int k = ty < kc * N ? ty / N : kc - 1;
   const int a = ty < kc * N ? ty - k * N : N;
@@ -307,6 +319,12 @@ __global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams 
     f_finish_vals(P, B, qv, qnv, sv, r0.h, B.out, I, x, other, g, t, bad);
     if (bad) *B.flag = 1;
   }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams P, const FBufs B) {
+  __shared__ float Fs[5 * (tile_segments(N) * N + N + 1) * kTileCols];
+  f_tline_tile<N, DIR, false>(P, B, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, Fs);
 }
 
 // FP64 <-> FP32 conversion of n values (data entering or leaving).

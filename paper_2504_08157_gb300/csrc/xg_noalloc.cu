@@ -70,8 +70,7 @@ __global__ void k_base_table(const double* __restrict__ rho0, const double* __re
 template <int N>
 cudaError_t launch_rhs(const xg::LineParams& P, const xg::StageBufs& B, size_t xsmem,
                        int chunk_y, int nchunk_y, int chunk_z, int nchunk_z, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(xg::k_line_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)xsmem);
+  cudaError_t e = xg::raise_dynamic_smem(xg::k_line_x<N>, xsmem);
   if (e != cudaSuccess) return e;
   dim3 gx(P.n[1], P.n[2]);
   xg::k_line_x<N><<<gx, xg::kXThreads, xsmem, st>>>(P, B);

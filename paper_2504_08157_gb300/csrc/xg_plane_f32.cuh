@@ -26,10 +26,10 @@ __host__ __device__ constexpr int plane_elems_f32(int N) { return N >= 32 ? 1 : 
 constexpr int kPlaneThreads = 256;
 constexpr int kPlaneBatch = 2;
 
-// Shared-memory layout of one tile (floats), see k_f_plane_xy.
-template <int N>
+// Shared-memory layout of a tile of E x E elements (floats), see f_plane_tile.
+template <int N, int E_ = plane_elems_f32(N)>
 struct PlaneLayoutF {
-  static constexpr int E = plane_elems_f32(N);
+  static constexpr int E = E_;
   static constexpr int TS = E * N;
   static constexpr int LO = TS + 1;          // owned extent across the line (wall node included)
   static constexpr int LX = TS + N + 1;      // loaded extent along the line
@@ -39,19 +39,22 @@ struct PlaneLayoutF {
   static constexpr size_t bytes = sizeof(float) * (size_t)total;
 };
 
-template <int N>
-__global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, const FBufs B) {
-  using L = PlaneLayoutF<N>;
-  constexpr int E = L::E, LO = L::LO, LX = L::LX;
-  extern __shared__ float sm_plane[];
+// One tile (bx, by) of level z, run by threads tid = 0 .. nthr-1 of the
+// block; sm holds PlaneLayoutF<N, E>::bytes.  CG: L2-only loads of q (see
+// ldf).  The block synchronises once, between the pointwise and the
+// contraction phases; the caller synchronises before reusing sm.
+template <int N, int E, int BATCH, bool CG>
+__device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, int bx, int by, int z,
+                                             float* sm_plane, int tid, int nthr) {
+  using L = PlaneLayoutF<N, E>;
+  constexpr int LO = L::LO, LX = L::LX;
   float* FX = sm_plane;                   // [c][j][i + N]
   float* FY = FX + L::FX;                 // [c][j + N][i]
   auto fx = [&](int c, int j, int ii) -> float& { return FX[(c * LO + j) * LX + ii]; };
   auto fy = [&](int c, int jj, int i) -> float& { return FY[(c * LX + jj) * LO + i]; };
 
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const int z = blockIdx.z;
-  const int ex0 = blockIdx.x * E, ey0 = blockIdx.y * E;
+  const int ex0 = bx * E, ey0 = by * E;
   const int ekx = min(E, P.nseg[0] - ex0), eky = min(E, P.nseg[1] - ey0);
   const int x0 = ex0 * N, y0 = ey0 * N;
   const bool wallx = !P.per[0] && ex0 + ekx == P.nseg[0];
@@ -73,18 +76,18 @@ __global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, c
   // before and the end face), y-fluxes on owned columns (j likewise).  The
   // cross is enumerated as the owned rows at full width, then the owned
   // columns of the rows above and below them.
-  // Each thread takes kPlaneBatch items per pass and issues all their loads
+  // Each thread takes BATCH items per pass and issues all their loads
   // before any arithmetic, to keep enough bytes in flight.
   const int wx = ekx * N + N + 1, wy = eky * N + N + 1;
   const int nrow = oy * wx;                       // owned rows, full width
   const int nitem = nrow + ox * (wy - oy);        // + owned columns, remaining rows
-  for (int base = threadIdx.x; base < nitem; base += kPlaneBatch * blockDim.x) {
-    int ib[kPlaneBatch], jb[kPlaneBatch];
-    long long Ib[kPlaneBatch];
-    float qb[kPlaneBatch][5];
+  for (int base = tid; base < nitem; base += BATCH * nthr) {
+    int ib[BATCH], jb[BATCH];
+    long long Ib[BATCH];
+    float qb[BATCH][5];
 #pragma unroll
-    for (int u = 0; u < kPlaneBatch; ++u) {
-      const int idx = base + u * blockDim.x;
+    for (int u = 0; u < BATCH; ++u) {
+      const int idx = base + u * nthr;
       int i = -N - 1, j = 0;                      // i = -N - 1 marks "nothing to do"
       if (idx < nrow) {
         i = idx % wx - N;
@@ -107,11 +110,11 @@ __global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, c
       Ib[u] = zoff + gx + (long long)nx * gy;
       if (i >= -N) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) qb[u][c] = q[c * np + Ib[u]];
+        for (int c = 0; c < 5; ++c) qb[u][c] = ldf<CG>(q + c * np + Ib[u]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < kPlaneBatch; ++u) {
+    for (int u = 0; u < BATCH; ++u) {
       const int i = ib[u], j = jb[u];
       if (i < -N) continue;
       const long long I = Ib[u];
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, c
   __syncthreads();
 
   // ---- each owned node: x part + y part from the flux tiles
-  for (int idx = threadIdx.x; idx < ox * oy; idx += blockDim.x) {
+  for (int idx = tid; idx < ox * oy; idx += nthr) {
     const int i = idx % ox, j = idx / ox;
     const long long I = zoff + (x0 + i) + (long long)nx * (y0 + j);
     const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
@@ -183,6 +186,13 @@ __global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, c
       To[c * np + I] = v + w;
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads) k_f_plane_xy(const FParams P, const FBufs B) {
+  extern __shared__ float sm_plane[];
+  f_plane_tile<N, plane_elems_f32(N), kPlaneBatch, false>(P, B, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                           sm_plane, threadIdx.x, blockDim.x);
 }
 
 }  // namespace xg

@@ -6,6 +6,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
 
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
@@ -252,6 +255,22 @@ inline void plan_marches(const xg_mesh_desc* d, const MeshGeom& g, int sms, int*
   const long long xblocks = (g.n[0] + 127) / 128;
   choose_chunks(d->nel[1], xblocks * g.n[2], sms, d->periodic[1] != 0, chunk_y, nchunk_y);
   choose_chunks(d->nel[2], xblocks * g.n[1], sms, d->periodic[2] != 0, chunk_z, nchunk_z);
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit is an attribute of the kernel function on the device, shared by
+// every context (and every translation unit that launches the kernel), so
+// it is only ever raised: lowering it for one mesh would break the launches
+// of a larger mesh that is still alive.
+template <typename F>
+inline cudaError_t raise_dynamic_smem(F* func, size_t bytes) {
+  static std::mutex m;
+  std::lock_guard<std::mutex> lock(m);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, (const void*)func);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace xg

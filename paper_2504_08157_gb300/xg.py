@@ -1,4 +1,5 @@
-"""ctypes binding of the C ABI in ``include/xg.h`` (same function names).
+"""ctypes binding of the C ABI in ``include/xg.h`` and ``include/xg_batch.h``
+(same function names).
 
 Argument marshalling only: every step of the path runs in ``libxg.so``.
 Arrays may be torch tensors (CUDA tensors are passed as device pointers,
@@ -20,10 +21,15 @@ XG_OK, XG_ERR_ARG, XG_ERR_CUDA, XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, \
     XG_ERR_UNSUPPORTED = range(7)
 XG_HOST, XG_DEVICE = 0, 1
 XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
+XG_SCHED_ROUND_ROBIN, XG_SCHED_LPT, XG_SCHED_DYNAMIC = 0, 1, 2
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library", "XG_HOST", "XG_DEVICE",
+           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library",
+           "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
+           "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
+           "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
+           "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -35,6 +41,16 @@ class xg_mesh_desc(ctypes.Structure):
                 ("f_coriolis", ctypes.c_double), ("g", ctypes.c_double),
                 ("R", ctypes.c_double), ("cp", ctypes.c_double), ("cv", ctypes.c_double),
                 ("p_a", ctypes.c_double)]
+
+
+class xg_batch_tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("plane_tile", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(schedule=("round_robin", "lpt", "dynamic")[self.schedule],
+                    plane_tile=self.plane_tile, ctas_per_sm=self.ctas_per_sm,
+                    ms_per_step=self.ms_per_step)
 
 
 class XgError(RuntimeError):
@@ -87,6 +103,27 @@ def library():
     lib.xg_diagnostics.argtypes = [P, ctypes.POINTER(D), P]
     lib.xg_destroy.restype = None
     lib.xg_destroy.argtypes = [P]
+    TP = ctypes.POINTER(xg_batch_tuning)
+    lib.xg_batch_create.restype = I
+    lib.xg_batch_create.argtypes = [ctypes.POINTER(xg_mesh_desc), I, ctypes.POINTER(P)]
+    lib.xg_batch_count.restype = I
+    lib.xg_batch_count.argtypes = [P, ctypes.POINTER(I)]
+    lib.xg_batch_instance.restype = P
+    lib.xg_batch_instance.argtypes = [P, I]
+    lib.xg_batch_step.restype = I
+    lib.xg_batch_step.argtypes = [P, ctypes.POINTER(D), I, P]
+    lib.xg_batch_rhs.restype = I
+    lib.xg_batch_rhs.argtypes = [P, ctypes.POINTER(P), I, P]
+    lib.xg_batch_autotune.restype = I
+    lib.xg_batch_autotune.argtypes = [P, ctypes.POINTER(D), I, TP, P]
+    lib.xg_batch_set_tuning.restype = I
+    lib.xg_batch_set_tuning.argtypes = [P, TP]
+    lib.xg_batch_get_tuning.restype = I
+    lib.xg_batch_get_tuning.argtypes = [P, TP]
+    lib.xg_batch_barrier_selftest.restype = I
+    lib.xg_batch_barrier_selftest.argtypes = [P, LL, P]
+    lib.xg_batch_destroy.restype = None
+    lib.xg_batch_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -262,3 +299,96 @@ def xg_diagnostics(ctx, stream=None):
 def xg_destroy(ctx):
     if ctx:
         library().xg_destroy(ctx)
+
+
+# ------------------------------------------------------------------ batched persistent form
+
+def _default_stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    return _stream(stream, None)
+
+
+def xg_batch_create(descs):
+    """Batch of XG_FP32 instances from a sequence of xg_mesh_desc; returns the
+    handle (an integer address)."""
+    arr = (xg_mesh_desc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _check(library().xg_batch_create(arr, len(descs), ctypes.byref(out)), "xg_batch_create")
+    return out.value
+
+
+def xg_batch_count(batch):
+    n = ctypes.c_int()
+    _check(library().xg_batch_count(batch, ctypes.byref(n)), "xg_batch_count")
+    return n.value
+
+
+def xg_batch_instance(batch, i):
+    """The xg_ctx handle of instance i (owned by the batch)."""
+    c = library().xg_batch_instance(batch, int(i))
+    if not c:
+        raise XgError(XG_ERR_ARG, "xg_batch_instance")
+    return c
+
+
+def _dt_array(dt):
+    a = np.ascontiguousarray(np.asarray(dt, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def xg_batch_step(batch, dt, nsteps, stream=None):
+    """nsteps SSP-RK3 steps of every instance (dt: one value per instance)."""
+    a, p = _dt_array(dt)
+    if a.size != xg_batch_count(batch):
+        raise ValueError("dt needs one value per instance")
+    _check(library().xg_batch_step(batch, p, int(nsteps), _default_stream(stream)),
+           "xg_batch_step")
+
+
+def xg_batch_rhs(batch, dqdt, stream=None):
+    """Right-hand sides of every instance into dqdt[i] (all host or all
+    device float64 arrays)."""
+    ptrs = [_ptr(a, writable=True) for a in dqdt]
+    where = {p[1] for p in ptrs}
+    if len(where) != 1:
+        raise ValueError("dqdt arrays must be all host or all device")
+    implied = next((p[2] for p in ptrs if p[2] is not None), None)
+    arr = (ctypes.c_void_p * len(ptrs))(*[p[0] for p in ptrs])
+    _check(library().xg_batch_rhs(batch, arr, where.pop(), _stream(stream, implied) if implied
+                                  else _default_stream(stream)), "xg_batch_rhs")
+
+
+def xg_batch_autotune(batch, dt, trial_steps=2, stream=None):
+    a, p = _dt_array(dt)
+    t = xg_batch_tuning()
+    _check(library().xg_batch_autotune(batch, p, int(trial_steps), ctypes.byref(t),
+                                       _default_stream(stream)), "xg_batch_autotune")
+    return t
+
+
+def xg_batch_set_tuning(batch, schedule, plane_tile=0, ctas_per_sm=2):
+    t = xg_batch_tuning(int(schedule), int(plane_tile), int(ctas_per_sm), 0.0)
+    _check(library().xg_batch_set_tuning(batch, ctypes.byref(t)), "xg_batch_set_tuning")
+
+
+def xg_batch_get_tuning(batch):
+    t = xg_batch_tuning()
+    _check(library().xg_batch_get_tuning(batch, ctypes.byref(t)), "xg_batch_get_tuning")
+    return t
+
+
+def xg_batch_barrier_selftest(batch, spin_limit=20000, stream=None):
+    """Returns the status of the deliberately starved barrier (XG_ERR_TIMEOUT
+    when the bounded wait works)."""
+    return library().xg_batch_barrier_selftest(batch, int(spin_limit), _default_stream(stream))
+
+
+def xg_batch_destroy(batch):
+    if batch:
+        library().xg_batch_destroy(batch)

@@ -87,3 +87,60 @@ class GpuRun:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchRun:
+    """A batch of XG_FP32 instances (the batched persistent form), one per
+    workload, inputs resident on cuda:0."""
+
+    def __init__(self, wls, device="cuda:0"):
+        import torch
+        from paper_2504_08157_gb300 import xg
+        self.xg, self.torch, self.wls = xg, torch, list(wls)
+        self.dev = torch.device(device)
+        descs = []
+        for wl in self.wls:
+            ph = wl["phys"]
+            descs.append(xg.mesh_desc(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"],
+                                      f=ph["f"], g=ph["g"], R=ph["R"], cp=ph["cp"], cv=ph["cv"],
+                                      p_a=ph["p_a"], precision=xg.XG_FP32))
+        self.b = xg.xg_batch_create(descs)
+        self.ctx = [xg.xg_batch_instance(self.b, i) for i in range(len(self.wls))]
+        self.np = [xg.xg_mesh_np(c) for c in self.ctx]
+        for c, wl in zip(self.ctx, self.wls):
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(self.dev)
+            xg.xg_set_state(c, t(wl["q"]), t(wl["rho0"]), t(wl["Theta0"]))
+            if wl["S_theta"] is not None:
+                xg.xg_set_forcing(c, t(wl["S_theta"]))
+        torch.cuda.synchronize()
+
+    @property
+    def dts(self):
+        return [wl["dt"] for wl in self.wls]
+
+    def rhs(self):
+        outs = [self.torch.empty((5, n), dtype=self.torch.float64, device=self.dev) for n in self.np]
+        self.xg.xg_batch_rhs(self.b, outs)
+        return [o.cpu().numpy() for o in outs]
+
+    def step(self, nsteps):
+        self.xg.xg_batch_step(self.b, self.dts, nsteps)
+
+    def states(self):
+        outs = []
+        for c, n in zip(self.ctx, self.np):
+            o = self.torch.empty((5, n), dtype=self.torch.float64, device=self.dev)
+            self.xg.xg_get_state(c, o)
+            outs.append(o)
+        return [o.cpu().numpy() for o in outs]
+
+    def close(self):
+        if self.b:
+            self.xg.xg_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,6 +1,6 @@
 """CPU tests of the C-ABI library: it builds, loads, exports every function
-that include/xg.h declares, and rejects invalid arguments on the host before
-any GPU work (no compute calls here)."""
+that include/xg.h and include/xg_batch.h declare, and rejects invalid
+arguments on the host before any GPU work (no compute calls here)."""
 
 import ctypes
 import os
@@ -9,7 +9,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "xg.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("xg.h", "xg_batch.h")]
 
 
 @pytest.fixture(scope="module")
@@ -20,15 +20,18 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(xg_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(xg_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("xg_mesh_create", "xg_set_state", "xg_set_forcing", "xg_rhs", "xg_step",
-                     "xg_destroy"):
+                     "xg_destroy", "xg_batch_create", "xg_batch_step", "xg_batch_autotune",
+                     "xg_batch_destroy"):
         assert required in names
 
 
@@ -92,3 +95,41 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(xg, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError):
         xg.library()
+
+
+# ------------------------------------------------------------------ batched form (host checks)
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(precision=0), "XG_ERR_UNSUPPORTED"),     # FP64 instances are not batched
+    (dict(precision=2), "XG_ERR_UNSUPPORTED"),
+    (dict(precision=1, order=2), "XG_ERR_UNSUPPORTED"),
+    (dict(precision=1, order=7), "XG_ERR_UNSUPPORTED"),
+    (dict(precision=1, order=9), "XG_ERR_ARG"),
+])
+def test_batch_create_rejects_on_the_host(lib, kw, status):
+    from paper_2504_08157_gb300 import xg
+    descs = [_desc(precision=1), _desc(**kw)]
+    with pytest.raises(xg.XgError) as e:
+        xg.xg_batch_create(descs)
+    assert e.value.status == getattr(xg, status)
+
+
+def test_batch_null_arguments(lib):
+    from paper_2504_08157_gb300 import xg
+    P = ctypes.c_void_p
+    out = P()
+    assert lib.xg_batch_create(None, 1, ctypes.byref(out)) == xg.XG_ERR_ARG and not out.value
+    d = (xg.xg_mesh_desc * 1)(_desc(precision=1))
+    assert lib.xg_batch_create(d, 0, ctypes.byref(out)) == xg.XG_ERR_ARG
+    assert lib.xg_batch_create(d, 5000, ctypes.byref(out)) == xg.XG_ERR_ARG
+    assert lib.xg_batch_create(d, 1, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_instance(None, 0) is None
+    assert lib.xg_batch_step(None, None, 1, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_rhs(None, None, 0, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_autotune(None, None, 1, None, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_set_tuning(None, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_get_tuning(None, None) == xg.XG_ERR_ARG
+    assert lib.xg_batch_barrier_selftest(None, 10, None) == xg.XG_ERR_ARG
+    n = ctypes.c_int()
+    assert lib.xg_batch_count(None, ctypes.byref(n)) == xg.XG_ERR_ARG
+    lib.xg_batch_destroy(None)

@@ -322,3 +322,20 @@ def test_zero_steps_is_identity(cuda_device):
     with GpuRun(wl) as g:
         g.step(0)
         assert np.array_equal(g.state(), wl["q"])
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp64", "fp32", "df64"])
+def test_contexts_of_one_order_coexist(cuda_device, prec):
+    """Kernel attributes are per function, not per context: a context with
+    long x lines keeps working after a context of the same order with short
+    lines was created (and gives the same result as before)."""
+    big = W.box((12, 2, 2), 4, (0.0, 0.0, 0.0), (12000.0, 2000.0, 2000.0), (False, True, False),
+                seed=91)
+    small = W.box((1, 2, 2), 4, (0.0, 0.0, 0.0), (1000.0, 2000.0, 2000.0), (False, True, False),
+                  seed=92)
+    with GpuRun(big, precision=prec) as g:
+        r0 = g.rhs()
+        with GpuRun(small, precision=prec) as s:
+            s.rhs()
+            r1 = g.rhs()
+    assert np.array_equal(r0, r1)
