@@ -22,6 +22,12 @@ numpy float64:
                 the inverse diagonal mass matrix (Eq. 12).
 * ``ssprk3`` -- the three-stage strong-stability-preserving Runge-Kutta
                 update (Shu-Osher form) that advances Eq. 12.
+* ``closure`` -- the learned subgrid closure's pieces (not in the paper):
+                per-node features (state, assembled gradients, heating),
+                fine-to-coarse restriction by the elements' Lagrange
+                interpolants, the 21-64-64-5 SiLU network with its
+                back-propagated gradient, Adam, and the bfloat16 inference
+                precision.
 
 Every function cites the passage it follows.  The pins that tie each function
 to something other than itself live in ``tests/test_oracle_*.py``.
@@ -29,8 +35,11 @@ to something other than itself live in ``tests/test_oracle_*.py``.
 Parity status: every function here is pinned (closed forms, polynomial
 exactness, brute-force assembly, a manufactured solution derived symbolically
 from Eq. 1, conservation and rest-state invariants, the SSP-RK3 amplification
-polynomial, inertial rotation).  The synthetic config inputs themselves
+polynomial, inertial rotation; for the closure: finite-difference
+gradients with planted mistakes, closed forms of the network and of Adam's
+first step, bfloat16 ties, polynomial exactness of features and
+restriction).  The synthetic config inputs themselves
 (vortex, heating cells) are inputs, not oracle functions.
 """
 
-from . import lgl, mesh, euler, ssprk3  # noqa: F401
+from . import lgl, mesh, euler, ssprk3, closure  # noqa: F401
