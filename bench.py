@@ -411,6 +411,9 @@ def run_xg(args, world, rank, local):
         batched = batch_measure(xg, torch, dev, stream, world, local, max(1, min(K, 10)), 3,
                                 False, compare=True, oracle_check=rank == 0)
         batched.pop("clocks", None)
+    closure_rate = None
+    if not args.no_plain and not args.no_batch:
+        closure_rate = closure_throughput(xg, torch, dev, stream, max(1, min(K, 10)), 3)
 
     cpu, l2 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -441,6 +444,7 @@ def run_xg(args, world, rank, local):
                "fp32_speedup_vs_plain_fp64": (round(fp32["value"] / plain["value"], 3)
                                               if fp32 and plain else None),
                "batched_form": batched,
+               "closure_form": closure_rate,
                "l2_error_vs_oracle": l2,
                "hbm_roofline_frac": round(hbm_frac, 4),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -665,6 +669,91 @@ def run_batch(args, world, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ learned-closure form
+
+def closure_throughput(xg, torch, dev, stream, K, Wm, nel=(64, 64, 16)):
+    """The closure form's step rate on the config-5 coarse mesh (FP32 with
+    the bfloat16 tensor-core closure in every stage; a seeded untrained
+    network: the rate does not depend on the weights) against plain FP64 on
+    the same mesh."""
+    from inputs import workloads as W
+    from paper_2504_08157_gb300 import closure as CL
+    wl = W.closure_case(1, nel=nel)
+    dof_u, _ = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])
+    out = {}
+    for name, prec, with_closure in (("closure_fp32", xg.XG_FP32, True), ("plain_fp32", xg.XG_FP32, False),
+                                     ("plain_fp64", xg.XG_FP64, False)):
+        ctx = make_ctx(xg, torch, wl, dev, prec)
+        if with_closure:
+            p = CL.init_params(3, dev)
+            one = torch.ones(21, dtype=torch.float32, device=dev)
+            xg.xg_closure_set(ctx, p, torch.zeros_like(one), one, one[:5] * 1e-6)
+        xg.xg_step(ctx, wl["dt"], Wm, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xg.xg_step(ctx, wl["dt"], K, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        xg.xg_destroy(ctx)
+        out[name] = {"value": round(dof_u * 3 * K / (ms / 1e3) / 1e9, 4), "unit": "GDOF/s",
+                     "ms_per_step": round(ms / K, 4), "steps": K}
+    out["config"] = "closure coarse mesh %dx%dx%d N=4 (10 km cube, walls), %d nodes" % (*nel, dof_u // 5)
+    out["speedup_vs_plain_fp64"] = round(out["closure_fp32"]["value"] / out["plain_fp64"]["value"], 3)
+    return out
+
+
+def run_closure(args, world, rank, local):
+    """Config 5: train the closure on refined-minus-coarse tendency
+    differences of paired runs (coarse 64 x 64 x 16, refined 128 x 128 x 32
+    elements, 8 seeded runs, 2e6 samples) with the library's kernels, then
+    judge it against the refined run; and the closure form's step rate."""
+    import torch
+    from inputs import workloads as W
+    from paper_2504_08157_gb300 import build, closure as CL, xg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+    K, Wm = args.steps, args.warmup
+    nel = tuple(args.nel) if args.nel else (64, 64, 16)
+    t0 = time.perf_counter()
+    nseeds, snaps = 8, 4
+    per_snap = args.samples // (nseeds * snaps)
+    X, T = CL.sample_pairs(W.closure_case, seeds=list(range(1, nseeds + 1)), coarse_nel=nel,
+                           snapshots=snaps, steps_between=20, samples=per_snap, dev=dev)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = CL.train(X, T, dev, epochs=args.epochs, batch=16384, lr=2e-3, holdout=1.0 / nseeds)
+    t_train = time.perf_counter() - t0
+    ev = CL.evaluate(W.closure_case, 100, nel, model, args.eval_steps, dev)
+    rate = closure_throughput(xg, torch, dev, stream, K, Wm, nel)
+    if rank == 0:
+        dof_u, dof_p = W.dof_counts(nel, 4, (False, False, False))
+        cfg = {"workload": "closure form: coarse %dx%dx%d N=4 FP32 + 21-64-64-5 bf16 closure, 10 km "
+                           "cube (walls), refined %dx%dx%d" % (*nel, *(2 * n for n in nel)),
+               "nodes": dof_u // 5, "dof_unique": dof_u, "dof_paper": dof_p,
+               "training_samples": int(X.shape[1]), "runs": nseeds, "snapshots_per_run": snaps,
+               "parallelism": "replicas"}
+        out = {"metric": METRIC, "value": rate["closure_fp32"]["value"], "unit": "GDOF/s",
+               "n_gpus": world, "steps": K, "warmup": Wm,
+               "ms_per_step": rate["closure_fp32"]["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+               "impl": "xg", "config": cfg, "closure_form": rate,
+               "training": {"seconds_data": round(t_data, 2), "seconds_train": round(t_train, 2),
+                            "epochs": args.epochs,
+                            "holdout_loss_zero_correction": round(model["holdout_zero"], 5),
+                            "holdout_loss_trained": round(model["holdout"], 5),
+                            "history": [[h[0], round(h[1], 5), round(h[2], 5)] for h in model["history"]],
+                            "what": "normalised mean-squared tendency error on the held-out run's "
+                                    "samples, without and with the closure"},
+               "vs_refined_run": ev, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+               "e2e": None}
+        print(json.dumps(out))
+
+
 def run_reference(args, world, rank, local):
     """The FP64 oracle on the host cores, one bounded sample per step."""
     if rank != 0:
@@ -723,7 +812,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["xg", "reference"], default="xg")
-    ap.add_argument("--workload", choices=["tc", "bubble", "batch"], default="tc")
+    ap.add_argument("--workload", choices=["tc", "bubble", "batch", "closure"], default="tc")
+    ap.add_argument("--samples", type=int, default=2000000,
+                    help="closure workload: training samples")
+    ap.add_argument("--epochs", type=int, default=20, help="closure workload: training epochs")
+    ap.add_argument("--eval-steps", type=int, default=500,
+                    help="closure workload: coarse steps of the judged run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
@@ -745,6 +839,8 @@ def main():
         run_reference(args, world, rank, local)
     elif args.workload == "batch":
         run_batch(args, world, rank, local)
+    elif args.workload == "closure":
+        run_closure(args, world, rank, local)
     else:
         run_xg(args, world, rank, local)
 

@@ -86,7 +86,9 @@ xg_ctx* xg_batch_instance(xg_batch* b, int i);
  * array of `count` values), all in one persistent launch on `stream`.
  * Every instance must have a state.  Waits for the GPU at the end.
  * Errors: XG_ERR_ARG (NULL, nsteps < 0, a dt not finite, an instance
- * without state), XG_ERR_NONFINITE (some instance produced a NaN or Inf),
+ * without state), XG_ERR_UNSUPPORTED (an instance has a learned closure
+ * set, see xg_closure.h: the batched kernel evaluates the plain right-hand
+ * side only), XG_ERR_NONFINITE (some instance produced a NaN or Inf),
  * XG_ERR_TIMEOUT, XG_ERR_CUDA. */
 xg_status xg_batch_step(xg_batch* b, const double* dt, int nsteps, void* stream);
 

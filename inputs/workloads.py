@@ -12,6 +12,14 @@
                modified-Rankine vortex (Vmax U(10, 30) m/s at radius
                U(30, 80) km) and heating ring, and a step dt at the acoustic
                Courant number of ``tc`` (0.1 s for 216 m vertical spacing).
+``closure_case`` -- a run of the learned-closure form: config 1's 10 km cube
+               (no-flux walls, isentropic theta_0 = 300 K), a seeded warm
+               bubble (+1..3 K, radius 1.5..2.5 km) and a seeded vortex scaled
+               to the box (Vmax 5..15 m/s at 1..2 km, cut off beyond 3.5 km
+               so the wall-normal momentum vanishes), and a heating ring
+               scaled down from ``tc``'s (peak 5..15 K/h at 2 km, width
+               0.5 km, below 8 km); dt at the acoustic Courant number of
+               ``tc``.
 ``tc``      -- tropical-cyclone-shaped box: 1024 x 1024 x 20 km, 128 x 128 x 16
                elements, N = 4, doubly periodic laterally with no-flux bottom
                and top (512 x 512 x 65 nodes), stable sounding N_BV = 0.01 1/s,
@@ -141,3 +149,33 @@ def batch_instance(spec, state="initial", seed=1):
     dt = 0.1 * _min_vertical_spacing(nel[2], N) / _min_vertical_spacing(16, 4)
     return dict(name="batch", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
                 phys=dict(PHYS, f=5.0e-5), dt=dt, q=q, rho0=rho0, Theta0=Th0, S_theta=S)
+
+
+CLOSURE_BOX = 10.0e3
+
+
+def closure_case(seed, nel=(64, 64, 16), N=4):
+    """One seeded run of the learned-closure form on the 10 km cube (see the
+    module docstring).  The same seed gives the same analytic fields on any
+    mesh (the fine and coarse runs of a pair share it)."""
+    u = rng.uniform(seed, 8)
+    lo, hi = (0.0, 0.0, 0.0), (CLOSURE_BOX,) * 3
+    periodic = (False, False, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.isentropic_sounding(ax[2])
+    n_xy = ax[0].size * ax[1].size
+    c = (5.0e3 + 1.0e3 * (u[0] - 0.5), 5.0e3 + 1.0e3 * (u[1] - 0.5))
+    q = atm.bubble_state(X, Y, Z, ax[2], rho0, Th0, n_xy, dtheta=1.0 + 2.0 * u[2],
+                         radius=1.5e3 + 1.0e3 * u[3], centre=(c[0], c[1], 2.0e3 + 1.0e3 * u[4]))
+    q += atm.vortex_state(X, Y, Z, rho0, n_xy, c, vmax=5.0 + 10.0 * u[5], rmax=1.0e3 + 1.0e3 * u[6],
+                          D1=4.0e3, D2=3.5e3)
+    s = [(X - lo[0]) / CLOSURE_BOX, (Y - lo[1]) / CLOSURE_BOX]
+    for d in range(2):   # no flux through the lateral walls
+        q[1 + d][(s[d] < 1e-9) | (s[d] > 1.0 - 1e-9)] = 0.0
+    S = atm.heating(X, Y, Z, c, seed=seed, ncells=0, ring_peak=5.0 + 10.0 * u[7], ring_r=2.0e3,
+                    ring_w=0.5e3, ztop=8.0e3)
+    xi = grid.lgl_points(N)
+    dmin = min(CLOSURE_BOX / nel[d] * (xi[1] - xi[0]) / 2.0 for d in range(3))
+    dt = 0.1 * dmin / _min_vertical_spacing(16, 4)
+    return dict(name="closure", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=0.0), dt=dt, q=q, rho0=rho0, Theta0=Th0, S_theta=S)

@@ -181,15 +181,23 @@ def bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+CLAMP_IN = 8.0
+
+
 def normalise(X, mean, scale):
-    """(x - mean) * scale per feature, in float32 (the kernels' order)."""
+    """(x - mean) * scale per feature in float32 (the kernels' order),
+    clamped to [-8, 8] (a state outside the training distribution cannot
+    drive the network without bound)."""
     X32 = np.asarray(X, dtype=np.float32)
-    return ((X32 - np.asarray(mean, np.float32)) * np.asarray(scale, np.float32)).astype(np.float64)
+    Xn = (X32 - np.asarray(mean, np.float32)) * np.asarray(scale, np.float32)
+    return np.clip(Xn, -CLAMP_IN, CLAMP_IN).astype(np.float64)
 
 
 def forward_bf16(p, Xn, sizes=SIZES):
     """Inference precision: bfloat16 weights, inputs and hidden activations,
-    float64 biases and sums (the kernels accumulate in float32)."""
+    float64 biases and sums (the kernels accumulate in float32 and evaluate
+    SiLU through a hardware tanh approximation, both below the bfloat16
+    rounding that follows)."""
     layers = unpack(np.asarray(p, dtype=np.float64), sizes)
     h = bf16(Xn)
     for k, (W, b) in enumerate(layers):

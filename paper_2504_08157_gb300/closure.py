@@ -1,0 +1,216 @@
+"""Training and evaluation of the learned closure through the C ABI
+(include/xg_closure.h).
+
+Orchestration only: the right-hand sides, time steps, restriction, features,
+statistics, loss gradients and Adam updates all run in ``libxg.so``; torch
+holds the device arrays and gathers the sampled training columns.
+
+A training pair is a refined run and the coarse mesh of the same box (the
+refined mesh has twice the elements per direction, same order).  At each
+snapshot of the refined run:
+
+    target  = R L_fine(q_fine) - L_coarse(R q_fine)
+    features = xg_features of the coarse context holding R q_fine
+
+where R is the restriction (xg_restrict: the fine elements' interpolants at
+the coarse nodes).  The closure learns the target from the features; a
+coarse run with the closure then adds its prediction to L_coarse.
+"""
+
+import numpy as np
+
+from . import xg
+
+P = xg.XG_CLOSURE_PARAMS
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_ctx(wl, dev, precision=xg.XG_FP32):
+    torch = _torch()
+    ph = wl["phys"]
+    ctx = xg.xg_mesh_create(xg.mesh_desc(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"],
+                                         f=ph["f"], g=ph["g"], R=ph["R"], cp=ph["cp"], cv=ph["cv"],
+                                         p_a=ph["p_a"], precision=precision))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    xg.xg_set_state(ctx, t(wl["q"]), t(wl["rho0"]), t(wl["Theta0"]))
+    if wl["S_theta"] is not None:
+        xg.xg_set_forcing(ctx, t(wl["S_theta"]))
+    return ctx
+
+
+def _state(ctx, dev):
+    torch = _torch()
+    q = torch.empty((5, xg.xg_mesh_np(ctx)), dtype=torch.float64, device=dev)
+    xg.xg_get_state(ctx, q)
+    return q
+
+
+def _rhs(ctx, dev):
+    torch = _torch()
+    r = torch.empty((5, xg.xg_mesh_np(ctx)), dtype=torch.float64, device=dev)
+    xg.xg_rhs(ctx, r)
+    return r
+
+
+def sample_pairs(case, seeds, coarse_nel, snapshots, steps_between, samples, dev, sample_seed=7,
+                 target="rhs"):
+    """Training set from refined runs: for each seed, a refined run of
+    2 x coarse_nel elements advanced ``steps_between`` refined steps between
+    ``snapshots`` snapshots (the first at t = 0); at each snapshot
+    ``samples`` coarse nodes drawn by the seeded generator.  The target is
+    the refined-minus-coarse tendency difference at the snapshot,
+    ``target="rhs"``: R L_f(q_f) - L_c(R q_f); or averaged over one coarse
+    step, ``target="step"``: (R q_f(t + dt) - S_c(R q_f(t))) / dt with S_c
+    one coarse SSP-RK3 step (what a correction added in every stage of that
+    step must supply).  Returns float32 CUDA tensors X [21][n], T [5][n]."""
+    torch = _torch()
+    from inputs import rng
+    fine_nel = tuple(2 * n for n in coarse_nel)
+    Xs, Ts = [], []
+    draw = 0
+    for seed in seeds:
+        fwl = case(seed, nel=fine_nel)
+        cwl = case(seed, nel=coarse_nel)
+        fctx = make_ctx(fwl, dev)
+        cctx = make_ctx(cwl, dev)
+        try:
+            npc = xg.xg_mesh_np(cctx)
+            X = torch.empty((21, npc), dtype=torch.float32, device=dev)
+            qc = torch.empty((5, npc), dtype=torch.float64, device=dev)
+            rc_f = torch.empty((5, npc), dtype=torch.float64, device=dev)
+            for k in range(snapshots):
+                if k:
+                    xg.xg_step(fctx, fwl["dt"], steps_between)
+                xg.xg_restrict(fctx, cctx, _state(fctx, dev), qc)
+                xg.xg_set_state(cctx, qc)
+                xg.xg_features(cctx, X)
+                if target == "rhs":
+                    xg.xg_restrict(fctx, cctx, _rhs(fctx, dev), rc_f)
+                    T = rc_f - _rhs(cctx, dev)
+                else:
+                    q_save = _state(fctx, dev)
+                    xg.xg_step(fctx, fwl["dt"], 2)          # two refined steps = one coarse step
+                    xg.xg_restrict(fctx, cctx, _state(fctx, dev), rc_f)
+                    xg.xg_set_state(fctx, q_save)          # the refined run continues unchanged
+                    xg.xg_step(cctx, cwl["dt"], 1)
+                    T = (rc_f - _state(cctx, dev)) / cwl["dt"]
+                u = rng.uniform(sample_seed, samples, offset=draw)
+                draw += samples
+                idx = torch.from_numpy(np.minimum((u * npc).astype(np.int64), npc - 1)).to(dev)
+                Xs.append(X[:, idx])
+                Ts.append(T[:, idx].to(torch.float32))
+        finally:
+            xg.xg_destroy(fctx)
+            xg.xg_destroy(cctx)
+    return torch.cat(Xs, dim=1).contiguous(), torch.cat(Ts, dim=1).contiguous()
+
+
+def init_params(seed, dev):
+    """Seeded uniform initialisation, +-1/sqrt(fan_in) per layer."""
+    torch = _torch()
+    from inputs import rng
+    u = rng.uniform(seed, P, -1.0, 1.0)
+    p = np.empty(P)
+    k = 0
+    for fin, fout in ((21, 64), (64, 64), (64, 5)):
+        nw = fin * fout
+        p[k:k + nw] = u[k:k + nw] / np.sqrt(fin)
+        k += nw
+        p[k:k + fout] = 0.0
+        k += fout
+    return torch.from_numpy(p.astype(np.float32)).to(dev)
+
+
+def normalisation(X, T, dev):
+    """(in_mean, in_scale, out_scale) float32 CUDA tensors from the column
+    statistics of the training set (xg_column_stats)."""
+    torch = _torch()
+    mx, sx = xg.xg_column_stats(X)
+    _, st = xg.xg_column_stats(T)
+    in_scale = np.where(sx > 0, 1.0 / np.maximum(sx, 1e-30), 1.0)
+    out_scale = np.where(st > 0, st, 1.0)
+    f = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float32)).to(dev)
+    return f(mx), f(in_scale), f(out_scale)
+
+
+def train(X, T, dev, epochs=20, batch=4096, lr=2e-3, seed=11, holdout=0.1):
+    """Adam (cosine-decayed step) on minibatches of the samples in a seeded
+    random order; the last ``holdout`` fraction of the set (the last run's
+    snapshots) is held out.  Returns a dict with the parameters,
+    the normalisation and the loss history (the loss is the normalised MSE;
+    the network predicting zero scores the normalised target variance)."""
+    torch = _torch()
+    from inputs import rng
+    n = X.shape[1]
+    ntr = int(n * (1.0 - holdout))
+    perm = torch.from_numpy(np.argsort(rng.uniform(seed + 1, ntr))).to(dev)
+    Xtr, Ttr = X[:, :ntr][:, perm].contiguous(), T[:, :ntr][:, perm].contiguous()
+    Xho, Tho = X[:, ntr:].contiguous(), T[:, ntr:].contiguous()
+    mean, scale, oscale = normalisation(Xtr, Ttr, dev)
+    p = init_params(seed, dev)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    g = torch.empty_like(p)
+    zero = torch.zeros_like(p)
+    hist = []
+    t = 0
+    base_ho = xg.xg_mlp_loss_grad(zero, Xho, Tho, mean, scale, oscale, g)
+    for ep in range(epochs):
+        tot = 0.0
+        for b0 in range(0, ntr - batch + 1, batch):
+            Xb = Xtr[:, b0:b0 + batch]
+            Tb = Ttr[:, b0:b0 + batch]
+            # minibatch columns as their own contiguous arrays
+            Xb = Xb.contiguous()
+            Tb = Tb.contiguous()
+            tot += xg.xg_mlp_loss_grad(p, Xb, Tb, mean, scale, oscale, g)
+            t += 1
+            lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * ep / max(epochs, 1)))
+            xg.xg_mlp_adam(p, m, v, g, t, lr=lr_t)
+        ho = xg.xg_mlp_loss_grad(p, Xho, Tho, mean, scale, oscale, g)
+        hist.append((ep, tot / max(1, (ntr // batch)), ho))
+    return dict(params=p, in_mean=mean, in_scale=scale, out_scale=oscale, history=hist,
+                holdout_zero=base_ho, holdout=hist[-1][2] if hist else base_ho)
+
+
+def evaluate(case, seed, coarse_nel, model, coarse_steps, dev):
+    """Refined run vs the plain coarse run vs the coarse run with the
+    closure, from the same initial field (the coarse runs start from its
+    restriction), over ``coarse_steps`` coarse steps (twice as many refined
+    steps).  Returns per-variable relative L2 errors of both coarse runs
+    against the restricted refined state."""
+    torch = _torch()
+    fine_nel = tuple(2 * n for n in coarse_nel)
+    fwl = case(seed, nel=fine_nel)
+    cwl = case(seed, nel=coarse_nel)
+    fctx = make_ctx(fwl, dev)
+    plain = make_ctx(cwl, dev)
+    clos = make_ctx(cwl, dev)
+    try:
+        npc = xg.xg_mesh_np(plain)
+        q0 = torch.empty((5, npc), dtype=torch.float64, device=dev)
+        xg.xg_restrict(fctx, plain, _state(fctx, dev), q0)
+        xg.xg_set_state(plain, q0)
+        xg.xg_set_state(clos, q0)
+        xg.xg_closure_set(clos, model["params"], model["in_mean"], model["in_scale"], model["out_scale"])
+        dt = cwl["dt"]
+        xg.xg_step(fctx, fwl["dt"], 2 * coarse_steps)   # the refined step is half the coarse one
+        xg.xg_step(plain, dt, coarse_steps)
+        xg.xg_step(clos, dt, coarse_steps)
+        ref = torch.empty((5, npc), dtype=torch.float64, device=dev)
+        xg.xg_restrict(fctx, plain, _state(fctx, dev), ref)
+        a, b = _state(plain, dev), _state(clos, dev)
+        ref0 = ref - q0
+        err = lambda s: [float(torch.linalg.norm(s[v] - ref[v]) / torch.linalg.norm(ref0[v]).clamp_min(1e-300))
+                         for v in range(5)]
+        return dict(plain=err(a), closure=err(b),
+                    what="relative L2 distance of each coarse run's state from the restricted "
+                         "refined state after %d coarse steps, per variable, relative to the "
+                         "refined run's change over that time" % coarse_steps)
+    finally:
+        for c in (fctx, plain, clos):
+            xg.xg_destroy(c)

@@ -300,6 +300,12 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
                       double alpha, double beta, int rhs_only, cudaStream_t st) {
   if (c->f32) {
     xg::FBufs F;
+    F.C = nullptr;
+    if (c->closure) {
+      const cudaError_t e = closure_launch(c, (const float*)q, st);
+      if (e != cudaSuccess) return e;
+      F.C = c->cl_C;
+    }
     F.q = (const float*)q;
     F.qn = (const float*)qn;
     F.out = (float*)out;
@@ -675,6 +681,7 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->base);
   cudaFree(c->flag);
   if (c->hflag) cudaFreeHost(c->hflag);
+  closure_free(c);
   delete c;
 }
 

@@ -125,6 +125,7 @@ __device__ __forceinline__ FBufs stage_bufs(const BRun& R, const BInst& I, int s
   B.T = I.T;
   B.S = I.S;
   B.base = I.base;
+  B.C = nullptr;
   B.flag = R.flag;
   B.dt = I.dt;
   B.alpha = R.alpha[st];
@@ -551,6 +552,7 @@ bool valid_tuning(const xg_batch_tuning* t) {
 
 xg_status check_ready(xg_batch* b, const double* dt) {
   for (int i = 0; i < b->count; ++i) {
+    if (b->inst[i]->closure) return XG_ERR_UNSUPPORTED;   // the batched kernel has no closure
     if (!b->inst[i]->has_state || b->inst[i]->failed) return XG_ERR_ARG;
     if (dt && !std::isfinite(dt[i])) return XG_ERR_ARG;
   }

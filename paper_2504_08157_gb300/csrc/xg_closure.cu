@@ -1,0 +1,881 @@
+// xg_closure.cu -- learned subgrid closure (include/xg_closure.h).
+//
+// Kernels:
+//   * features of a state: q, assembled gradients, heating (k_features);
+//   * restriction of fine fields to coarse nodes, one axis at a time
+//     (k_interp_axis);
+//   * training in FP32 on the CUDA cores: forward and back-propagation over
+//     chunks of samples with the weights, activations and per-block gradient
+//     sums in shared memory (k_mlp_grad, each gradient entry owned by one
+//     thread so the sums are deterministic), the fixed-order reduction of
+//     the block partials (k_mlp_reduce), Adam (k_adam), column statistics
+//     (k_col_stats);
+//   * inference on the tensor cores (mma m16n8k16, bfloat16 inputs, FP32
+//     accumulation): 16-node row tiles per warp; the first layer's
+//     accumulators, after bias and SiLU, are repacked in registers as the
+//     second layer's A fragments (and likewise into the third), so hidden
+//     activations never leave the registers.  k_closure computes the
+//     features of 128 nodes per CTA straight from the state and runs the
+//     network on them; k_mlp_bf16 runs it on given features.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/xg_closure.h"
+#include "xg_ctx.h"
+#include "xg_setup.h"
+
+namespace xg {
+
+constexpr int kIn = XG_CLOSURE_IN, kHid = XG_CLOSURE_HIDDEN, kOut = XG_CLOSURE_OUT;
+constexpr int kParams = XG_CLOSURE_PARAMS;
+// Normalised inputs are clamped to [-kClampIn, kClampIn]: a state outside
+// the training distribution cannot drive the network's output without bound.
+constexpr float kClampIn = 8.0f;
+__device__ __forceinline__ float norm_in(float x, float mean, float scale) {
+  return fminf(fmaxf((x - mean) * scale, -kClampIn), kClampIn);
+}
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+              kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kOut * kHid;
+static_assert(kOffB3 + kOut == kParams, "parameter layout");
+
+// ------------------------------------------------------------------ features
+
+// Assembled derivative along direction d of the field f at global index g
+// of a line whose first node is f[base] (stride sd): the rows of the scaled
+// matrix Dm = -(2/h) D (rows 0 and N halved) over the node's segment, plus
+// row N of the segment before at a shared face, or twice the one-sided row
+// at a wall; the sign undoes Dm's minus.
+template <int N>
+__device__ __forceinline__ float line_derivative(const FParams& P, int d, const float* __restrict__ f,
+                                                 long long base, long long sd, int g) {
+  const int nd = P.n[d], nseg = P.nseg[d];
+  int s = g / N;
+  if (s >= nseg) s = nseg - 1;
+  const int a = g - s * N;
+  float acc = 0.0f;
+#pragma unroll
+  for (int l = 0; l <= N; ++l) {
+    int k = s * N + l;
+    if (k >= nd) k -= nd;
+    acc = fmaf(P.Dm[d][a][l], f[base + sd * k], acc);
+  }
+  if (a == 0) {
+    if (s > 0 || P.per[d]) {
+      const int s2 = s > 0 ? s - 1 : nseg - 1;
+#pragma unroll
+      for (int l = 0; l <= N; ++l) {
+        int k = s2 * N + l;
+        if (k >= nd) k -= nd;
+        acc = fmaf(P.Dm[d][N][l], f[base + sd * k], acc);
+      }
+    } else {
+      acc = acc + acc;
+    }
+  } else if (a == N) {
+    acc = acc + acc;
+  }
+  return -acc;
+}
+
+// The 21 features of node I, handed to emit(f, value) one variable at a
+// time (the loop over variables is not unrolled, so only one variable's
+// loads and results are live at once).
+template <int N, typename Emit>
+__device__ __forceinline__ void node_features(const FParams& P, const float* __restrict__ q,
+                                              const float* __restrict__ S, long long I, Emit emit) {
+  const long long np = P.np;
+  const int nx = P.n[0], ny = P.n[1];
+  const int gx = (int)(I % nx);
+  const long long r = I / nx;
+  const int gy = (int)(r % ny), gz = (int)(r / ny);
+  const long long bx = I - gx, by = I - (long long)gy * nx, bz = I - (long long)gz * nx * ny;
+#pragma unroll 1
+  for (int v = 0; v < 5; ++v) {
+    const float* f = q + v * np;
+    emit(v, f[I]);
+    emit(5 + 3 * v, line_derivative<N>(P, 0, f, bx, 1, gx));
+    emit(6 + 3 * v, line_derivative<N>(P, 1, f, by, nx, gy));
+    emit(7 + 3 * v, line_derivative<N>(P, 2, f, bz, (long long)nx * ny, gz));
+  }
+  emit(20, S ? S[I] : 0.0f);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_features(const FParams P, const float* __restrict__ q,
+                                                  const float* __restrict__ S, float* __restrict__ X) {
+  const long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (I >= P.np) return;
+  const long long np = P.np;
+  node_features<N>(P, q, S, I, [&](int f, float v) { X[f * np + I] = v; });
+}
+
+// ------------------------------------------------------------------ restriction
+
+// out[o][c][i] = sum_a w[c][a] in[o][(start[c] + a) mod n_in][i]
+__global__ void k_interp_axis(const double* __restrict__ in, double* __restrict__ out, long long outer,
+                              int n_in, int n_out, long long inner, const int* __restrict__ start,
+                              const double* __restrict__ w, int npts) {
+  const long long total = outer * n_out * inner;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t % inner;
+    const long long rest = t / inner;
+    const int c = (int)(rest % n_out);
+    const long long o = rest / n_out;
+    double acc = 0.0;
+    for (int a = 0; a < npts; ++a) {
+      int k = start[c] + a;
+      if (k >= n_in) k -= n_in;
+      acc = fma(w[c * npts + a], in[(o * n_in + k) * inner + i], acc);
+    }
+    out[t] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ training (FP32)
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_prime_f(float z) {
+  const float s = 1.0f / (1.0f + expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+constexpr int kTrainThreads = 256;
+constexpr int kChunk = 32;   // samples per pass through the network
+
+struct TrainSmem {
+  float W[kParams];
+  float G[kParams];
+  float x[kIn][kChunk];
+  float t[kOut][kChunk];
+  float z1[kHid][kChunk];
+  float h1[kHid][kChunk];    // silu(z1)
+  float z2[kHid][kChunk];    // later the first layer's delta
+  float h2[kHid][kChunk];    // silu(z2)
+  float d2[kHid][kChunk];
+  float d3[kOut][kChunk];
+  float stat[2 * kIn + kOut];
+  double red[kTrainThreads];
+};
+
+// Samples [begin, end) of this block; writes the block's gradient sums and
+// loss partial.  scale = 2 / (5 n) (the derivative of the mean square).
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(const float* __restrict__ params,
+                                                           const float* __restrict__ X,
+                                                           const float* __restrict__ T, long long ld,
+                                                           long long n, const float* __restrict__ in_mean,
+                                                           const float* __restrict__ in_scale,
+                                                           const float* __restrict__ out_scale,
+                                                           float* __restrict__ partial,
+                                                           double* __restrict__ lossp, float scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smraw);
+  const int tid = threadIdx.x;
+  for (int k = tid; k < kParams; k += blockDim.x) {
+    S.W[k] = params[k];
+    S.G[k] = 0.0f;
+  }
+  if (tid < kIn) {
+    S.stat[tid] = in_mean[tid];
+    S.stat[kIn + tid] = in_scale[tid];
+  }
+  if (tid < kOut) S.stat[2 * kIn + tid] = 1.0f / out_scale[tid];
+  const long long begin = n * blockIdx.x / gridDim.x, end = n * (blockIdx.x + 1) / gridDim.x;
+  double lacc = 0.0;
+  const float* W1 = S.W + kOffW1;
+  const float* b1 = S.W + kOffB1;
+  const float* W2 = S.W + kOffW2;
+  const float* b2 = S.W + kOffB2;
+  const float* W3 = S.W + kOffW3;
+  const float* b3 = S.W + kOffB3;
+  __syncthreads();
+  for (long long c0 = begin; c0 < end; c0 += kChunk) {
+    const int cn = (int)min((long long)kChunk, end - c0);
+    for (int k = tid; k < kIn * kChunk; k += blockDim.x) {
+      const int f = k / kChunk, s = k % kChunk;
+      S.x[f][s] = s < cn ? norm_in(X[f * ld + c0 + s], S.stat[f], S.stat[kIn + f]) : 0.0f;
+    }
+    for (int k = tid; k < kOut * kChunk; k += blockDim.x) {
+      const int o = k / kChunk, s = k % kChunk;
+      S.t[o][s] = s < cn ? T[o * ld + c0 + s] * S.stat[2 * kIn + o] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = tid; k < kHid * kChunk; k += blockDim.x) {   // z1 = W1 x + b1
+      const int o = k / kChunk, s = k % kChunk;
+      float a = b1[o];
+      for (int i = 0; i < kIn; ++i) a = fmaf(W1[o * kIn + i], S.x[i][s], a);
+      S.z1[o][s] = a;
+      S.h1[o][s] = silu_f(a);
+    }
+    __syncthreads();
+    for (int k = tid; k < kHid * kChunk; k += blockDim.x) {   // z2 = W2 silu(z1) + b2
+      const int o = k / kChunk, s = k % kChunk;
+      float a = b2[o];
+      for (int i = 0; i < kHid; ++i) a = fmaf(W2[o * kHid + i], S.h1[i][s], a);
+      S.z2[o][s] = a;
+      S.h2[o][s] = silu_f(a);
+    }
+    __syncthreads();
+    for (int k = tid; k < kOut * kChunk; k += blockDim.x) {   // y, residual, output delta
+      const int o = k / kChunk, s = k % kChunk;
+      float a = b3[o];
+      for (int i = 0; i < kHid; ++i) a = fmaf(W3[o * kHid + i], S.h2[i][s], a);
+      const float r = s < cn ? a - S.t[o][s] : 0.0f;
+      lacc += (double)r * r;
+      S.d3[o][s] = scale * r;
+    }
+    __syncthreads();
+    for (int k = tid; k < kOut * kHid + kOut; k += blockDim.x) {   // W3, b3 gradients
+      float a = 0.0f;
+      if (k < kOut * kHid) {
+        const int o = k / kHid, i = k % kHid;
+        for (int s = 0; s < cn; ++s) a = fmaf(S.d3[o][s], S.h2[i][s], a);
+      } else {
+        for (int s = 0; s < cn; ++s) a += S.d3[k - kOut * kHid][s];
+      }
+      S.G[kOffW3 + k] += a;
+    }
+    for (int k = tid; k < kHid * kChunk; k += blockDim.x) {   // second hidden layer's delta
+      const int i = k / kChunk, s = k % kChunk;
+      float a = 0.0f;
+      for (int o = 0; o < kOut; ++o) a = fmaf(W3[o * kHid + i], S.d3[o][s], a);
+      S.d2[i][s] = a * silu_prime_f(S.z2[i][s]);
+    }
+    __syncthreads();
+    for (int k = tid; k < kHid * kHid + kHid; k += blockDim.x) {   // W2, b2 gradients
+      float a = 0.0f;
+      if (k < kHid * kHid) {
+        const int o = k / kHid, i = k % kHid;
+        for (int s = 0; s < cn; ++s) a = fmaf(S.d2[o][s], S.h1[i][s], a);
+      } else {
+        for (int s = 0; s < cn; ++s) a += S.d2[k - kHid * kHid][s];
+      }
+      S.G[kOffW2 + k] += a;
+    }
+    __syncthreads();
+    for (int k = tid; k < kHid * kChunk; k += blockDim.x) {   // first hidden layer's delta (into z2)
+      const int i = k / kChunk, s = k % kChunk;
+      float a = 0.0f;
+      for (int o = 0; o < kHid; ++o) a = fmaf(W2[o * kHid + i], S.d2[o][s], a);
+      S.z2[i][s] = a * silu_prime_f(S.z1[i][s]);
+    }
+    __syncthreads();
+    for (int k = tid; k < kHid * kIn + kHid; k += blockDim.x) {   // W1, b1 gradients
+      float a = 0.0f;
+      if (k < kHid * kIn) {
+        const int o = k / kIn, i = k % kIn;
+        for (int s = 0; s < cn; ++s) a = fmaf(S.z2[o][s], S.x[i][s], a);
+      } else {
+        for (int s = 0; s < cn; ++s) a += S.z2[k - kHid * kIn][s];
+      }
+      S.G[kOffW1 + k] += a;
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < kParams; k += blockDim.x) partial[(long long)blockIdx.x * kParams + k] = S.G[k];
+  S.red[tid] = lacc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (tid < h) S.red[tid] += S.red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) lossp[blockIdx.x] = S.red[0];
+}
+
+__global__ void k_mlp_reduce(const float* __restrict__ partial, int nblocks, float* __restrict__ grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kParams) return;
+  float a = 0.0f;
+  for (int b = 0; b < nblocks; ++b) a += partial[(long long)b * kParams + k];
+  grad[k] = a;
+}
+
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float gk = g[k];
+  const float mk = b1 * m[k] + (1.0f - b1) * gk;
+  const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+  m[k] = mk;
+  v[k] = vk;
+  p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+__global__ void k_col_stats(const float* __restrict__ X, long long ld, long long n, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const float* x = X + c * ld;
+  double s = 0.0;
+  for (long long i = tid; i < n; i += blockDim.x) s += x[i];
+  red[tid] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (tid < h) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)n;
+  __syncthreads();
+  double q = 0.0;
+  for (long long i = tid; i < n; i += blockDim.x) {
+    const double d = x[i] - mean;
+    q += d * d;
+  }
+  red[tid] = q;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (tid < h) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[2 * c] = mean;
+    out[2 * c + 1] = sqrt(red[0] / (double)n);
+  }
+}
+
+__global__ void k_mlp_fp32(const float* __restrict__ params, const float* __restrict__ X, long long ld,
+                           long long n, const float* __restrict__ in_mean, const float* __restrict__ in_scale,
+                           const float* __restrict__ out_scale, float* __restrict__ Y, long long ldy) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float x[kIn], h1[kHid], h2[kHid];
+  for (int f = 0; f < kIn; ++f) x[f] = norm_in(X[f * ld + s], in_mean[f], in_scale[f]);
+  for (int o = 0; o < kHid; ++o) {
+    float a = params[kOffB1 + o];
+    for (int i = 0; i < kIn; ++i) a = fmaf(params[kOffW1 + o * kIn + i], x[i], a);
+    h1[o] = silu_f(a);
+  }
+  for (int o = 0; o < kHid; ++o) {
+    float a = params[kOffB2 + o];
+    for (int i = 0; i < kHid; ++i) a = fmaf(params[kOffW2 + o * kHid + i], h1[i], a);
+    h2[o] = silu_f(a);
+  }
+  for (int o = 0; o < kOut; ++o) {
+    float a = params[kOffB3 + o];
+    for (int i = 0; i < kHid; ++i) a = fmaf(params[kOffW3 + o * kHid + i], h2[i], a);
+    Y[o * ldy + s] = a * out_scale[o];
+  }
+}
+
+// ------------------------------------------------------------------ inference (tensor cores)
+
+// Packed inference constants (one device blob, copied to shared memory):
+// bfloat16 W1 [64][40] (inputs 21..39 zero), W2 [64][72], W3 [8][72]
+// (outputs 5..7 and columns 64..71 zero), then FP32 b1 [64], b2 [64],
+// b3 [8], in_mean [24], in_scale [24], out_scale [8].
+constexpr int kLd1 = 40, kLd2 = 72;
+struct InferPack {
+  __nv_bfloat16 W1[kHid * kLd1];
+  __nv_bfloat16 W2[kHid * kLd2];
+  __nv_bfloat16 W3[8 * kLd2];
+  float b1[kHid], b2[kHid], b3[8];
+  float mean[24], scale[24], oscale[8];
+};
+static_assert(sizeof(InferPack) % 16 == 0, "InferPack is copied as int4");
+
+__global__ void k_pack(const float* __restrict__ p, const float* __restrict__ mean,
+                       const float* __restrict__ scale, const float* __restrict__ oscale,
+                       InferPack* __restrict__ out) {
+  for (int k = threadIdx.x; k < kHid * kLd1; k += blockDim.x) {
+    const int o = k / kLd1, i = k % kLd1;
+    out->W1[k] = __float2bfloat16_rn(i < kIn ? p[kOffW1 + o * kIn + i] : 0.0f);
+  }
+  for (int k = threadIdx.x; k < kHid * kLd2; k += blockDim.x) {
+    const int o = k / kLd2, i = k % kLd2;
+    out->W2[k] = __float2bfloat16_rn(i < kHid ? p[kOffW2 + o * kHid + i] : 0.0f);
+  }
+  for (int k = threadIdx.x; k < 8 * kLd2; k += blockDim.x) {
+    const int o = k / kLd2, i = k % kLd2;
+    out->W3[k] = __float2bfloat16_rn(o < kOut && i < kHid ? p[kOffW3 + o * kHid + i] : 0.0f);
+  }
+  for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
+    out->b1[k] = p[kOffB1 + k];
+    out->b2[k] = p[kOffB2 + k];
+  }
+  for (int k = threadIdx.x; k < 24; k += blockDim.x) {
+    out->mean[k] = k < kIn ? mean[k] : 0.0f;
+    out->scale[k] = k < kIn ? scale[k] : 0.0f;
+  }
+  for (int k = threadIdx.x; k < 8; k += blockDim.x) {
+    out->b3[k] = k < kOut ? p[kOffB3 + k] : 0.0f;
+    out->oscale[k] = k < kOut ? oscale[k] : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// SiLU for inference: z sigma(z) = (z/2)(1 + tanh(z/2)) with the hardware
+// tanh approximation (relative error ~2^-11), below the bfloat16 rounding
+// that follows it.
+__device__ __forceinline__ float silu_fast(float z) {
+  const float h = 0.5f * z;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
+
+// One 16-row tile: A rows in shared memory (bfloat16, row stride kLd1),
+// outputs y[2][2] for rows g and g + 8, columns 2c and 2c + 1 (lane = 4 g + c).
+__device__ __forceinline__ void mlp_tile(const InferPack& K, const __nv_bfloat16* A, float (&y)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
+  uint32_t a[2][4];
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt) {
+    a[kt][0] = A32[(g * kLd1 + 16 * kt + 2 * c) / 2];
+    a[kt][1] = A32[((g + 8) * kLd1 + 16 * kt + 2 * c) / 2];
+    a[kt][2] = A32[(g * kLd1 + 16 * kt + 2 * c + 8) / 2];
+    a[kt][3] = A32[((g + 8) * kLd1 + 16 * kt + 2 * c + 8) / 2];
+  }
+  const uint32_t* W1 = reinterpret_cast<const uint32_t*>(K.W1);
+  const uint32_t* W2 = reinterpret_cast<const uint32_t*>(K.W2);
+  const uint32_t* W3 = reinterpret_cast<const uint32_t*>(K.W3);
+  uint32_t h[4][4];   // A fragments of the next layer (k-tiles of 16)
+  {
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float bl = K.b1[8 * j + 2 * c], bh = K.b1[8 * j + 2 * c + 1];
+      acc[j][0] = bl; acc[j][1] = bh; acc[j][2] = bl; acc[j][3] = bh;
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        const int row = 8 * j + g;
+        mma_bf16(acc[j], a[kt][0], a[kt][1], a[kt][2], a[kt][3], W1[(row * kLd1 + 16 * kt + 2 * c) / 2],
+                 W1[(row * kLd1 + 16 * kt + 2 * c + 8) / 2]);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      h[kk][0] = pack_bf16(silu_fast(acc[2 * kk][0]), silu_fast(acc[2 * kk][1]));
+      h[kk][1] = pack_bf16(silu_fast(acc[2 * kk][2]), silu_fast(acc[2 * kk][3]));
+      h[kk][2] = pack_bf16(silu_fast(acc[2 * kk + 1][0]), silu_fast(acc[2 * kk + 1][1]));
+      h[kk][3] = pack_bf16(silu_fast(acc[2 * kk + 1][2]), silu_fast(acc[2 * kk + 1][3]));
+    }
+  }
+  {
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float bl = K.b2[8 * j + 2 * c], bh = K.b2[8 * j + 2 * c + 1];
+      acc[j][0] = bl; acc[j][1] = bh; acc[j][2] = bl; acc[j][3] = bh;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const int row = 8 * j + g;
+        mma_bf16(acc[j], h[kk][0], h[kk][1], h[kk][2], h[kk][3], W2[(row * kLd2 + 16 * kk + 2 * c) / 2],
+                 W2[(row * kLd2 + 16 * kk + 2 * c + 8) / 2]);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      h[kk][0] = pack_bf16(silu_fast(acc[2 * kk][0]), silu_fast(acc[2 * kk][1]));
+      h[kk][1] = pack_bf16(silu_fast(acc[2 * kk][2]), silu_fast(acc[2 * kk][3]));
+      h[kk][2] = pack_bf16(silu_fast(acc[2 * kk + 1][0]), silu_fast(acc[2 * kk + 1][1]));
+      h[kk][3] = pack_bf16(silu_fast(acc[2 * kk + 1][2]), silu_fast(acc[2 * kk + 1][3]));
+    }
+  }
+  const float bl = K.b3[2 * c], bh = K.b3[2 * c + 1];
+  y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    mma_bf16(y, h[kk][0], h[kk][1], h[kk][2], h[kk][3], W3[(g * kLd2 + 16 * kk + 2 * c) / 2],
+             W3[(g * kLd2 + 16 * kk + 2 * c + 8) / 2]);
+}
+
+constexpr int kInferThreads = 128;   // 4 warps x 2 row tiles of 16 = 128 samples per CTA
+
+struct InferSmem {
+  InferPack K;
+  __nv_bfloat16 A[kInferThreads * kLd1];
+};
+
+__device__ __forceinline__ void load_pack(InferPack& dst, const InferPack* src) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(InferPack) / 16); k += blockDim.x) d[k] = s[k];
+}
+
+// the normalised features of this thread's sample as bfloat16 row of A
+__device__ __forceinline__ void store_row(InferSmem& S, const float (&x)[kIn]) {
+  __nv_bfloat16* row = S.A + threadIdx.x * kLd1;
+#pragma unroll
+  for (int f = 0; f < 32; f += 2) {
+    const float lo = f < kIn ? norm_in(x[f], S.K.mean[f], S.K.scale[f]) : 0.0f;
+    const float hi = f + 1 < kIn ? norm_in(x[f + 1], S.K.mean[f + 1], S.K.scale[f + 1]) : 0.0f;
+    *reinterpret_cast<__nv_bfloat162*>(row + f) = __floats2bfloat162_rn(lo, hi);
+  }
+}
+
+// the network on the CTA's 128 rows; writes out_scale * y to Y[o * ldy + s0 + row]
+__device__ __forceinline__ void run_rows(const InferSmem& S, float* __restrict__ Y, long long ldy,
+                                         long long s0, long long n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    const int r0 = 32 * warp + 16 * t;
+    float y[4];
+    mlp_tile(S.K, S.A + r0 * kLd1, y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long s = s0 + r0 + g + 8 * h;
+      if (s >= n) continue;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int o = 2 * c + e;
+        if (o < kOut) Y[o * ldy + s] = y[2 * h + e] * S.K.oscale[o];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kInferThreads) k_mlp_bf16(const InferPack* __restrict__ pack,
+                                                           const float* __restrict__ X, long long ld,
+                                                           long long n, float* __restrict__ Y, long long ldy) {
+  __shared__ __align__(16) InferSmem S;
+  load_pack(S.K, pack);
+  __syncthreads();
+  const long long s0 = blockIdx.x * (long long)kInferThreads;
+  const long long s = s0 + threadIdx.x;
+  float x[kIn];
+#pragma unroll
+  for (int f = 0; f < kIn; ++f) x[f] = s < n ? X[f * ld + s] : S.K.mean[f];
+  store_row(S, x);
+  __syncthreads();
+  run_rows(S, Y, ldy, s0, n);
+}
+
+// Features of 128 consecutive nodes, straight from the state, normalised
+// into the bfloat16 rows of A as they are computed; then the network: the
+// closure correction C [5][np].
+template <int N>
+__global__ void __launch_bounds__(kInferThreads, 4) k_closure(const FParams P, const InferPack* __restrict__ pack,
+                                                             const float* __restrict__ q,
+                                                             const float* __restrict__ Sth,
+                                                             float* __restrict__ C) {
+  __shared__ __align__(16) InferSmem S;
+  load_pack(S.K, pack);
+  __syncthreads();
+  const long long s0 = blockIdx.x * (long long)kInferThreads;
+  const long long I = s0 + threadIdx.x;
+  __nv_bfloat16* row = S.A + threadIdx.x * kLd1;
+#pragma unroll
+  for (int f = kIn; f < 32; ++f) row[f] = __float2bfloat16_rn(0.0f);
+  if (I < P.np) {
+    node_features<N>(P, q, Sth, I, [&](int f, float v) {
+      row[f] = __float2bfloat16_rn(norm_in(v, S.K.mean[f], S.K.scale[f]));
+    });
+  } else {
+#pragma unroll
+    for (int f = 0; f < kIn; ++f) row[f] = __float2bfloat16_rn(0.0f);
+  }
+  __syncthreads();
+  run_rows(S, C, P.np, s0, P.np);
+}
+
+}  // namespace xg
+
+using xg::InferPack;
+
+// ------------------------------------------------------------------ stage hook
+
+// Called by the FP32 stage before its passes when the closure is on:
+// C = correction of the stage's input state.
+cudaError_t closure_launch(xg_ctx* c, const float* q, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((c->np + xg::kInferThreads - 1) / xg::kInferThreads);
+  const float* S = c->has_forcing ? (const float*)c->S : nullptr;
+  const InferPack* K = (const InferPack*)c->cl_pack;
+  switch (c->d.order) {
+    case 1: xg::k_closure<1><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 2: xg::k_closure<2><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 3: xg::k_closure<3><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 4: xg::k_closure<4><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 5: xg::k_closure<5><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 6: xg::k_closure<6><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 7: xg::k_closure<7><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    case 8: xg::k_closure<8><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+void closure_free(xg_ctx* c) {
+  cudaFree(c->cl_pack);
+  cudaFree(c->cl_C);
+  c->cl_pack = nullptr;
+  c->cl_C = nullptr;
+  c->closure = false;
+}
+
+namespace {
+
+xg_status cuda_status(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return XG_OK;
+  fprintf(stderr, "xg_closure: %s: %s\n", where, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? XG_ERR_OOM : XG_ERR_CUDA;
+}
+
+// 1-D restriction table: for each coarse node its fine element's first
+// global node and the N_f + 1 Lagrange weights of the fine element's LGL
+// points at the coarse node's position.
+void axis_table(const xg_ctx* f, const xg_ctx* c, int d, std::vector<int>& start, std::vector<double>& w) {
+  const int Nf = f->d.order, Nc = c->d.order;
+  long double xf[xg::kMaxOrder + 1], xc[xg::kMaxOrder + 1];
+  xg::lgl_nodes(Nf, xf);
+  xg::lgl_nodes(Nc, xc);
+  const double lo = f->d.lo[d], hi = f->d.hi[d];
+  const int nelf = f->d.nel[d], nelc = c->d.nel[d];
+  const int nf = f->n[d], ncn = c->n[d];
+  start.assign(ncn, 0);
+  w.assign((size_t)ncn * (Nf + 1), 0.0);
+  for (int g = 0; g < ncn; ++g) {
+    int e = std::min(g / Nc, nelc - 1);
+    const int a = g - Nc * e;
+    // position as a fraction of the box, then in fine element units
+    const long double frac = ((long double)e + (xc[a] + 1.0L) / 2.0L) / nelc;
+    const long double sf = frac * nelf;
+    int ef = (int)floorl(sf);
+    ef = std::max(0, std::min(ef, nelf - 1));
+    const long double loc = 2.0L * (sf - ef) - 1.0L;
+    start[g] = (Nf * ef) % nf;
+    for (int l = 0; l <= Nf; ++l) {
+      long double L = 1.0L;
+      for (int k = 0; k <= Nf; ++k)
+        if (k != l) L *= (loc - xf[k]) / (xf[l] - xf[k]);
+      w[(size_t)g * (Nf + 1) + l] = (double)L;
+    }
+  }
+  (void)lo;
+  (void)hi;
+}
+
+}  // namespace
+
+extern "C" {
+
+xg_status xg_features(xg_ctx* c, float* X, void* stream) {
+  if (!c || !X) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!c->f32) return XG_ERR_UNSUPPORTED;
+  if (!c->has_state) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned blocks = (unsigned)((c->np + 127) / 128);
+  const float* q = (const float*)c->A;
+  const float* S = c->has_forcing ? (const float*)c->S : nullptr;
+  switch (c->d.order) {
+    case 1: xg::k_features<1><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 2: xg::k_features<2><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 3: xg::k_features<3><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 4: xg::k_features<4><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 5: xg::k_features<5><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 6: xg::k_features<6><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 7: xg::k_features<7><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    case 8: xg::k_features<8><<<blocks, 128, 0, st>>>(c->Pf, q, S, X); break;
+    default: return XG_ERR_ARG;
+  }
+  return cuda_status(cudaGetLastError(), "xg_features");
+}
+
+xg_status xg_restrict(const xg_ctx* f, const xg_ctx* c, const double* src, int nvar, double* dst,
+                      void* stream) {
+  if (!f || !c || !src || !dst || nvar < 1) return XG_ERR_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (f->d.lo[d] != c->d.lo[d] || f->d.hi[d] != c->d.hi[d]) return XG_ERR_ARG;
+    if ((f->d.periodic[d] != 0) != (c->d.periodic[d] != 0)) return XG_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int Nf = f->d.order;
+  std::vector<int> start[3];
+  std::vector<double> w[3];
+  for (int d = 0; d < 3; ++d) axis_table(f, c, d, start[d], w[d]);
+  const int* nf = f->n;
+  const int* nc = c->n;
+  const long long s1 = (long long)nvar * nf[2] * nf[1] * nc[0];
+  const long long s2 = (long long)nvar * nf[2] * nc[1] * nc[0];
+  double *t1 = nullptr, *t2 = nullptr, *dw = nullptr;
+  int* ds = nullptr;
+  size_t nw = 0, ns = 0;
+  for (int d = 0; d < 3; ++d) {
+    nw += w[d].size();
+    ns += start[d].size();
+  }
+  cudaError_t e = cudaMalloc((void**)&t1, sizeof(double) * s1);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t2, sizeof(double) * s2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw, sizeof(double) * nw);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ds, sizeof(int) * ns);
+  size_t ow[3], os[3];
+  if (e == cudaSuccess) {
+    size_t a = 0, b = 0;
+    for (int d = 0; d < 3; ++d) {
+      ow[d] = a;
+      os[d] = b;
+      e = cudaMemcpy(dw + a, w[d].data(), sizeof(double) * w[d].size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(ds + b, start[d].data(), sizeof(int) * start[d].size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) break;
+      a += w[d].size();
+      b += start[d].size();
+    }
+  }
+  if (e == cudaSuccess) {
+    auto grid = [](long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 65535); };
+    // x: [v][z_f][y_f] x (x_f -> x_c)
+    xg::k_interp_axis<<<grid(s1), 256, 0, st>>>(src, t1, (long long)nvar * nf[2] * nf[1], nf[0], nc[0], 1,
+                                                ds + os[0], dw + ow[0], Nf + 1);
+    // y: [v][z_f] x (y_f -> y_c) x [x_c]
+    xg::k_interp_axis<<<grid(s2), 256, 0, st>>>(t1, t2, (long long)nvar * nf[2], nf[1], nc[1], nc[0],
+                                                ds + os[1], dw + ow[1], Nf + 1);
+    // z: [v] x (z_f -> z_c) x [y_c x_c]
+    const long long s3 = (long long)nvar * nc[2] * nc[1] * nc[0];
+    xg::k_interp_axis<<<grid(s3), 256, 0, st>>>(t2, dst, nvar, nf[2], nc[2], (long long)nc[1] * nc[0],
+                                                ds + os[2], dw + ow[2], Nf + 1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(t1);
+  cudaFree(t2);
+  cudaFree(dw);
+  cudaFree(ds);
+  return cuda_status(e, "xg_restrict");
+}
+
+xg_status xg_column_stats(const float* X, int ncol, long long ld, long long n, double* mean,
+                          double* stdev, void* stream) {
+  if (!X || ncol < 1 || n < 1 || ld < n || !mean || !stdev) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d, sizeof(double) * 2 * ncol);
+  if (e == cudaSuccess) {
+    xg::k_col_stats<<<ncol, 256, 0, st>>>(X, ld, n, d);
+    e = cudaGetLastError();
+  }
+  std::vector<double> h(2 * (size_t)ncol);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(e, "xg_column_stats");
+  for (int k = 0; k < ncol; ++k) {
+    mean[k] = h[2 * k];
+    stdev[k] = h[2 * k + 1];
+  }
+  return XG_OK;
+}
+
+xg_status xg_mlp_loss_grad(const float* params, const float* X, const float* T, long long ld,
+                           long long n, const float* in_mean, const float* in_scale,
+                           const float* out_scale, float* grad, double* loss, void* stream) {
+  if (!params || !X || !T || !in_mean || !in_scale || !out_scale || !grad || !loss) return XG_ERR_ARG;
+  if (n < 1 || ld < n) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (int)std::min<long long>((n + xg::kChunk - 1) / xg::kChunk, 2LL * sms);
+  const size_t smem = sizeof(xg::TrainSmem);
+  float* partial = nullptr;
+  double* lossp = nullptr;
+  cudaError_t e = xg::raise_dynamic_smem(xg::k_mlp_grad, smem);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&partial, sizeof(float) * (size_t)blocks * xg::kParams);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&lossp, sizeof(double) * blocks);
+  if (e == cudaSuccess) {
+    xg::k_mlp_grad<<<blocks, xg::kTrainThreads, smem, st>>>(params, X, T, ld, n, in_mean, in_scale, out_scale,
+                                                           partial, lossp, (float)(2.0 / (5.0 * (double)n)));
+    xg::k_mlp_reduce<<<(xg::kParams + 255) / 256, 256, 0, st>>>(partial, blocks, grad);
+    e = cudaGetLastError();
+  }
+  std::vector<double> h(blocks);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), lossp, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(partial);
+  cudaFree(lossp);
+  if (e != cudaSuccess) return cuda_status(e, "xg_mlp_loss_grad");
+  double s = 0.0;
+  for (double v : h) s += v;
+  *loss = s / (5.0 * (double)n);
+  return XG_OK;
+}
+
+xg_status xg_mlp_adam(float* params, float* m, float* v, const float* grad, int nparams, int t,
+                      double lr, double beta1, double beta2, double eps, void* stream) {
+  if (!params || !m || !v || !grad || nparams < 1 || t < 1) return XG_ERR_ARG;
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps >= 0.0))
+    return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+  xg::k_adam<<<(nparams + 255) / 256, 256, 0, st>>>(params, m, v, grad, nparams, (float)lr, (float)beta1,
+                                                    (float)beta2, (float)eps, (float)c1, (float)c2);
+  return cuda_status(cudaGetLastError(), "xg_mlp_adam");
+}
+
+xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long long n,
+                         const float* in_mean, const float* in_scale, const float* out_scale, float* Y,
+                         long long ldy, int precision, void* stream) {
+  if (!params || !X || !in_mean || !in_scale || !out_scale || !Y) return XG_ERR_ARG;
+  if (n < 1 || ld < n || ldy < n) return XG_ERR_ARG;
+  if (precision != XG_MLP_FP32 && precision != XG_MLP_BF16) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == XG_MLP_FP32) {
+    xg::k_mlp_fp32<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(params, X, ld, n, in_mean, in_scale,
+                                                                 out_scale, Y, ldy);
+    return cuda_status(cudaGetLastError(), "xg_mlp_forward");
+  }
+  InferPack* K = nullptr;
+  cudaError_t e = cudaMalloc((void**)&K, sizeof(InferPack));
+  if (e == cudaSuccess) {
+    xg::k_pack<<<1, 256, 0, st>>>(params, in_mean, in_scale, out_scale, K);
+    xg::k_mlp_bf16<<<(unsigned)((n + xg::kInferThreads - 1) / xg::kInferThreads), xg::kInferThreads, 0, st>>>(
+        K, X, ld, n, Y, ldy);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(K);
+  return cuda_status(e, "xg_mlp_forward");
+}
+
+xg_status xg_closure_set(xg_ctx* c, const float* params, const float* in_mean, const float* in_scale,
+                         const float* out_scale, void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!params) {
+    c->closure = false;
+    return XG_OK;
+  }
+  if (!in_mean || !in_scale || !out_scale) return XG_ERR_ARG;
+  if (!c->f32) return XG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->cl_pack) e = cudaMalloc(&c->cl_pack, sizeof(InferPack));
+  if (e == cudaSuccess && !c->cl_C) e = cudaMalloc((void**)&c->cl_C, sizeof(float) * 5 * (size_t)c->np);
+  if (e == cudaSuccess) {
+    xg::k_pack<<<1, 256, 0, st>>>(params, in_mean, in_scale, out_scale, (InferPack*)c->cl_pack);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    closure_free(c);
+    return cuda_status(e, "xg_closure_set");
+  }
+  c->closure = true;
+  return XG_OK;
+}
+
+}  // extern "C"

@@ -49,4 +49,14 @@ struct xg_ctx {
   size_t ev_used = 0;           // pairs recorded
   double k_ms[3] = {0, 0, 0};
   long long k_launches[3] = {0, 0, 0};
+  // learned closure (XG_FP32 only): packed bfloat16 network and the
+  // correction of the current stage's input state
+  bool closure = false;
+  void* cl_pack = nullptr;
+  float* cl_C = nullptr;
 };
+
+// The closure's correction C = MLP(features(q)) of the stage input q into
+// c->cl_C (xg_closure.cu); and freeing its buffers.
+cudaError_t closure_launch(xg_ctx* c, const float* q, cudaStream_t st);
+void closure_free(xg_ctx* c);

@@ -39,6 +39,7 @@ struct FBufs {
   float* T;          // [5][np]
   const float* S;    // [np] or null
   const df* base;    // [4][nz] rho0, Theta0, p0, 1/Theta0 (FP64-accurate pairs)
+  const float* C;    // [5][np] closure correction added to the tendency, or null
   int* flag;
   float dt, alpha, beta;
   int rhs_only;
@@ -177,8 +178,12 @@ __device__ __forceinline__ void f_finish_vals(const FParams& P, const FBufs& B,
                                               const float (&qv)[5], const float (&qnv)[5],
                                               float sv, float rho0, float* __restrict__ out,
                                               long long I, int x, int y, int gz, float (&L)[5],
-                                              bool& bad) {
+                                              bool& bad, const float (&cv)[5]) {
   const long long np = P.np;
+  if (B.C) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[c] += cv[c];
+  }
   L[1] = fmaf(P.f, qv[2], L[1]);
   L[2] = fmaf(-P.f, qv[1], L[2]);
   L[3] = fmaf(-P.g, qv[0], L[3]);
@@ -249,7 +254,7 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   const long long Ih = base + sd * (halo ? gh : 0);
 
   float qv[5], vel = 0.0f, pp = 0.0f, hq[5] = {0, 0, 0, 0, 0}, hvel = 0.0f, hpp = 0.0f;
-  float t[5], qnv[5] = {0, 0, 0, 0, 0}, sv = 0.0f;
+  float t[5], qnv[5] = {0, 0, 0, 0, 0}, sv = 0.0f, cv[5] = {0, 0, 0, 0, 0};
   if (main_plane) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) qv[c] = ldf<CG>(B.q + c * np + I);
@@ -271,6 +276,10 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
         for (int c = 0; c < 5; ++c) qnv[c] = ldf<CG>(B.qn + c * np + I);
       }
       if (B.S) sv = B.S[I];
+      if (B.C) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) cv[c] = ldf<CG>(B.C + c * np + I);
+      }
     }
   }
   if (main_plane) {
@@ -316,7 +325,7 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   } else {
     bool bad = false;
     const df r0 = B.base[g];
-    f_finish_vals(P, B, qv, qnv, sv, r0.h, B.out, I, x, other, g, t, bad);
+    f_finish_vals(P, B, qv, qnv, sv, r0.h, B.out, I, x, other, g, t, bad, cv);
     if (bad) *B.flag = 1;
   }
 }

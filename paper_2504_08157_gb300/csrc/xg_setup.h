@@ -38,8 +38,7 @@ inline void legendre2(int N, long double x, long double* pN, long double* pN1) {
 // points; then the derivative matrix of the Lagrange basis,
 // D[i][j] = P_N(x_i) / (P_N(x_j) (x_i - x_j)) for i != j,
 // D[0][0] = -N(N+1)/4, D[N][N] = N(N+1)/4, else 0 on the diagonal.
-inline void lgl_derivative(int N, double D[kMaxOrder + 1][kMaxOrder + 1]) {
-  long double x[kMaxOrder + 1], PN[kMaxOrder + 1];
+inline void lgl_nodes(int N, long double* x) {
   const long double pi = 3.14159265358979323846264338327950288L;
   for (int j = 0; j <= N; ++j) {
     long double xj = -cosl(pi * j / N);
@@ -54,6 +53,11 @@ inline void lgl_derivative(int N, double D[kMaxOrder + 1][kMaxOrder + 1]) {
   }
   x[0] = -1.0L;
   x[N] = 1.0L;
+}
+
+inline void lgl_derivative(int N, double D[kMaxOrder + 1][kMaxOrder + 1]) {
+  long double x[kMaxOrder + 1], PN[kMaxOrder + 1];
+  lgl_nodes(N, x);
   for (int j = 0; j <= N; ++j) {
     long double pn1;
     legendre2(N, x[j], &PN[j], &pn1);

@@ -1,5 +1,5 @@
-"""ctypes binding of the C ABI in ``include/xg.h`` and ``include/xg_batch.h``
-(same function names).
+"""ctypes binding of the C ABI in ``include/xg.h``, ``include/xg_batch.h`` and
+``include/xg_closure.h`` (same function names).
 
 Argument marshalling only: every step of the path runs in ``libxg.so``.
 Arrays may be torch tensors (CUDA tensors are passed as device pointers,
@@ -22,6 +22,8 @@ XG_OK, XG_ERR_ARG, XG_ERR_CUDA, XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, \
 XG_HOST, XG_DEVICE = 0, 1
 XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
 XG_SCHED_ROUND_ROBIN, XG_SCHED_LPT, XG_SCHED_DYNAMIC = 0, 1, 2
+XG_MLP_FP32, XG_MLP_BF16 = 0, 1
+XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5, 5893
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
@@ -29,7 +31,10 @@ __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_cre
            "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
            "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
            "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
-           "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC", "XG_HOST", "XG_DEVICE",
+           "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC",
+           "xg_features", "xg_restrict", "xg_column_stats", "xg_mlp_loss_grad", "xg_mlp_adam",
+           "xg_mlp_forward", "xg_closure_set", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
+           "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -124,6 +129,20 @@ def library():
     lib.xg_batch_barrier_selftest.argtypes = [P, LL, P]
     lib.xg_batch_destroy.restype = None
     lib.xg_batch_destroy.argtypes = [P]
+    lib.xg_features.restype = I
+    lib.xg_features.argtypes = [P, P, P]
+    lib.xg_restrict.restype = I
+    lib.xg_restrict.argtypes = [P, P, P, I, P, P]
+    lib.xg_column_stats.restype = I
+    lib.xg_column_stats.argtypes = [P, I, LL, LL, ctypes.POINTER(D), ctypes.POINTER(D), P]
+    lib.xg_mlp_loss_grad.restype = I
+    lib.xg_mlp_loss_grad.argtypes = [P, P, P, LL, LL, P, P, P, P, ctypes.POINTER(D), P]
+    lib.xg_mlp_adam.restype = I
+    lib.xg_mlp_adam.argtypes = [P, P, P, P, I, I, D, D, D, D, P]
+    lib.xg_mlp_forward.restype = I
+    lib.xg_mlp_forward.argtypes = [P, P, LL, LL, P, P, P, P, LL, I, P]
+    lib.xg_closure_set.restype = I
+    lib.xg_closure_set.argtypes = [P, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -392,3 +411,84 @@ def xg_batch_barrier_selftest(batch, spin_limit=20000, stream=None):
 def xg_batch_destroy(batch):
     if batch:
         library().xg_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------ learned closure
+# Arrays are float32 CUDA tensors (device memory); feature and target sets
+# are [rows][ld] with the sample index fastest.
+
+def _f32(a, rows=None):
+    import torch
+    if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if rows is not None and (a.dim() != 2 or a.shape[0] != rows):
+        raise ValueError("expected %d rows" % rows)
+    return a.data_ptr()
+
+
+def xg_features(ctx, X, stream=None):
+    """Features of an XG_FP32 context's state into X [21][Np] (float32)."""
+    _check(library().xg_features(ctx, _f32(X, XG_CLOSURE_IN), _default_stream(stream)), "xg_features")
+
+
+def xg_restrict(fine, coarse, src, dst, stream=None):
+    """Fields src [nv][Np_fine] (float64 CUDA) at the nodes of ``coarse`` into dst [nv][Np_coarse]."""
+    ps, ws, _ = _ptr(src)
+    pd, wd, _ = _ptr(dst, writable=True)
+    if ws != XG_DEVICE or wd != XG_DEVICE:
+        raise ValueError("xg_restrict takes device arrays")
+    nv = src.shape[0] if src.dim() == 2 else 1
+    _check(library().xg_restrict(fine, coarse, ps, int(nv), pd, _default_stream(stream)), "xg_restrict")
+
+
+def xg_column_stats(X, n=None, stream=None):
+    """(mean, std) float64 numpy arrays of the rows of X [ncol][ld] over the
+    first n samples."""
+    ncol, ld = X.shape
+    n = ld if n is None else n
+    mean = (ctypes.c_double * ncol)()
+    std = (ctypes.c_double * ncol)()
+    _check(library().xg_column_stats(_f32(X), int(ncol), int(ld), int(n), mean, std,
+                                     _default_stream(stream)), "xg_column_stats")
+    return np.array(mean), np.array(std)
+
+
+def xg_mlp_loss_grad(params, X, T, in_mean, in_scale, out_scale, grad, n=None, stream=None):
+    """MSE of the network on the first n samples of X [21][ld] against T
+    [5][ld]; writes grad (float32 [5893]) and returns the loss."""
+    ld = X.shape[1]
+    n = ld if n is None else n
+    if T.shape[1] != ld:
+        raise ValueError("X and T need the same leading dimension")
+    loss = ctypes.c_double()
+    _check(library().xg_mlp_loss_grad(_f32(params), _f32(X, XG_CLOSURE_IN), _f32(T, XG_CLOSURE_OUT),
+                                      int(ld), int(n), _f32(in_mean), _f32(in_scale), _f32(out_scale),
+                                      _f32(grad), ctypes.byref(loss), _default_stream(stream)),
+           "xg_mlp_loss_grad")
+    return loss.value
+
+
+def xg_mlp_adam(params, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(library().xg_mlp_adam(_f32(params), _f32(m), _f32(v), _f32(grad), int(params.numel()),
+                                 int(t), float(lr), float(beta1), float(beta2), float(eps),
+                                 _default_stream(stream)), "xg_mlp_adam")
+
+
+def xg_mlp_forward(params, X, in_mean, in_scale, out_scale, Y, precision=XG_MLP_BF16, n=None,
+                   stream=None):
+    ld, ldy = X.shape[1], Y.shape[1]
+    n = ld if n is None else n
+    _check(library().xg_mlp_forward(_f32(params), _f32(X, XG_CLOSURE_IN), int(ld), int(n),
+                                    _f32(in_mean), _f32(in_scale), _f32(out_scale),
+                                    _f32(Y, XG_CLOSURE_OUT), int(ldy), int(precision),
+                                    _default_stream(stream)), "xg_mlp_forward")
+
+
+def xg_closure_set(ctx, params=None, in_mean=None, in_scale=None, out_scale=None, stream=None):
+    """Enable the closure on an XG_FP32 context (params None disables it)."""
+    if params is None:
+        _check(library().xg_closure_set(ctx, None, None, None, None, _default_stream(stream)),
+               "xg_closure_set")
+        return
+    _check(library().xg_closure_set(ctx, _f32(params), _f32(in_mean), _f32(in_scale),
+                                    _f32(out_scale), _default_stream(stream)), "xg_closure_set")
