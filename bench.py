@@ -47,7 +47,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", f)
                for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh", "xg_kernels_f32.cuh",
-                         "xg_plane_f32.cuh", "xg_batch.cu")]
+                         "xg_plane_f32.cuh", "xg_batch.cu", "xg_closure.cu")]
 KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 # the kernels behind the three timing slots in each precision (the FP32 form
 # fuses the x and y passes into one plane kernel; slot 1 stays empty)
@@ -541,7 +541,8 @@ def batch_measure(xg, torch, dev, stream, world, local, K, Wm, sample_clocks, co
         achieved = BATCH_BYTES_PER_NODE * cfg["nodes"] * 3 * K / (ms / 1e3) / 1e9
         out["roofline"] = {"kernel": "k_batch", "bound": "hbm", "achieved": round(achieved, 1),
                            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                           "traffic": traffic_per_launch("k_batch"),
+                           "traffic": (lambda b: None if b is None else round(b * cfg["nodes"] * 3 * K))(
+                               traffic_per_launch("k_batch_per_node_stage")),
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
                            "bytes_per_node_stage": round(BATCH_BYTES_PER_NODE, 2),
                            "launch": "one persistent launch of %d steps (%d stages)" % (K, 3 * K)}
@@ -719,6 +720,11 @@ def run_closure(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     K, Wm = args.steps, args.warmup
     nel = tuple(args.nel) if args.nel else (64, 64, 16)
+    if args.rate_only:
+        rate = closure_throughput(xg, torch, dev, stream, K, Wm, nel)
+        if rank == 0:
+            print(json.dumps({"workload": "closure", "closure_form": rate}))
+        return
     t0 = time.perf_counter()
     nseeds, snaps = 8, 4
     per_snap = args.samples // (nseeds * snaps)
@@ -816,6 +822,8 @@ def main():
     ap.add_argument("--samples", type=int, default=2000000,
                     help="closure workload: training samples")
     ap.add_argument("--epochs", type=int, default=20, help="closure workload: training epochs")
+    ap.add_argument("--rate-only", action="store_true",
+                    help="closure workload: only the step rates (no training or evaluation)")
     ap.add_argument("--eval-steps", type=int, default=500,
                     help="closure workload: coarse steps of the judged run")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -298,14 +298,16 @@ __global__ void k_mlp_reduce(const float* __restrict__ partial, int nblocks, flo
   grad[k] = a;
 }
 
+// Adam; 1 - beta1 and 1 - beta2 come from the host in double precision
+// (1.0f - 0.999f would carry a 5e-5 relative error into v).
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ g, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       const float* __restrict__ g, int n, float lr, float b1, float b2, float omb1,
+                       float omb2, float eps, float c1, float c2) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const float gk = g[k];
-  const float mk = b1 * m[k] + (1.0f - b1) * gk;
-  const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+  const float mk = b1 * m[k] + omb1 * gk;
+  const float vk = b2 * v[k] + omb2 * gk * gk;
   m[k] = mk;
   v[k] = vk;
   p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
@@ -823,7 +825,8 @@ xg_status xg_mlp_adam(float* params, float* m, float* v, const float* grad, int 
   cudaStream_t st = (cudaStream_t)stream;
   const double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
   xg::k_adam<<<(nparams + 255) / 256, 256, 0, st>>>(params, m, v, grad, nparams, (float)lr, (float)beta1,
-                                                    (float)beta2, (float)eps, (float)c1, (float)c2);
+                                                    (float)beta2, (float)(1.0 - beta1), (float)(1.0 - beta2),
+                                                    (float)eps, (float)c1, (float)c2);
   return cuda_status(cudaGetLastError(), "xg_mlp_adam");
 }
 
