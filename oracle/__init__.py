@@ -28,6 +28,10 @@ numpy float64:
                 interpolants, the 21-64-64-5 SiLU network with its
                 back-propagated gradient, Adam, and the bfloat16 inference
                 precision.
+* ``dynamics`` -- the paper's remaining terms: the weak CG Laplacian with
+                the tensor viscosity of Sec. 2.4, fourth-order
+                hyper-diffusion (Eq. 14), the top sponge (Sec. 4.1) and the
+                RI-velocity diagnostic (Sec. 5).
 
 Every function cites the passage it follows.  The pins that tie each function
 to something other than itself live in ``tests/test_oracle_*.py``.
@@ -38,8 +42,11 @@ from Eq. 1, conservation and rest-state invariants, the SSP-RK3 amplification
 polynomial, inertial rotation; for the closure: finite-difference
 gradients with planted mistakes, closed forms of the network and of Adam's
 first step, bfloat16 ties, polynomial exactness of features and
-restriction).  The synthetic config inputs themselves
+restriction; for the dynamics: conservation, symmetry and definiteness of the
+weak Laplacian, exact interior second derivatives of quadratics, spectral
+convergence and the k^4 damping of a Fourier mode, the tensor's closed form,
+the sponge profile, solid-body rotation for the RI velocity).  The synthetic config inputs themselves
 (vortex, heating cells) are inputs, not oracle functions.
 """
 
-from . import lgl, mesh, euler, ssprk3, closure  # noqa: F401
+from . import lgl, mesh, euler, ssprk3, closure, dynamics  # noqa: F401
