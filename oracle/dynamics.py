@@ -30,10 +30,11 @@ from .mesh import apply_D
 
 
 def _global(mesh, local):
-    """Value of an element-local field at the global nodes (all copies of a
-    node are equal for the coordinate fields this is used on)."""
-    out = np.zeros(mesh.Np)
-    out[mesh.intma.ravel()] = np.asarray(local).ravel()
+    """Position of the global nodes from an element-local coordinate field:
+    the smallest of a node's copies (a periodic direction's last element
+    carries the wrapped image of the first node, one period further on)."""
+    out = np.full(mesh.Np, np.inf)
+    np.minimum.at(out, mesh.intma.ravel(), np.asarray(local).ravel())
     return out
 
 

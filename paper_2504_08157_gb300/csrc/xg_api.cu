@@ -320,9 +320,16 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
     F.rhs_only = rhs_only;
     return launch_f32_stage(c, F, st);
   }
-  if (!c->dfm)
-    return launch_stage(c, make_bufs(c, (const double*)q, (const double*)qn, (double*)out, dt,
-                                     alpha, beta, rhs_only), st);
+  if (!c->dfm) {
+    StageBufs B = make_bufs(c, (const double*)q, (const double*)qn, (double*)out, dt, alpha, beta,
+                            rhs_only);
+    if (c->dyn) {
+      const cudaError_t e = dynamics_launch(c, (const double*)q, st);
+      if (e != cudaSuccess) return e;
+      B.E = c->dyn_E;
+    }
+    return launch_stage(c, B, st);
+  }
   DfBufs B;
   B.q = (const df*)q;
   B.qn = (const df*)qn;
@@ -682,6 +689,7 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->flag);
   if (c->hflag) cudaFreeHost(c->hflag);
   closure_free(c);
+  dynamics_free(c);
   delete c;
 }
 

@@ -54,7 +54,19 @@ struct xg_ctx {
   bool closure = false;
   void* cl_pack = nullptr;
   float* cl_C = nullptr;
+  // hyper-diffusion and sponge (XG_FP64 only): line-operator constants,
+  // work arrays and the extra tendency E of the current stage
+  bool dyn = false, dyn_hyper = false;
+  void* dyn_params = nullptr;
+  double* dyn_L1 = nullptr;
+  double* dyn_E = nullptr;
+  double* dyn_gamma = nullptr;   // [n_z] sponge rate per level
 };
+
+// E = H(q) + sponge(q) of the FP64 stage input q into c->dyn_E
+// (xg_dynamics.cu); and freeing its buffers.
+cudaError_t dynamics_launch(xg_ctx* c, const double* q, cudaStream_t st);
+void dynamics_free(xg_ctx* c);
 
 // The closure's correction C = MLP(features(q)) of the stage input q into
 // c->cl_C (xg_closure.cu); and freeing its buffers.

@@ -84,6 +84,7 @@ struct StageBufs {
   int* flag;            // set to 1 when a non-finite value is stored
   double dt, alpha, beta;
   int rhs_only;
+  const double* E = nullptr;  // [5][np] extra tendency (hyper-diffusion, sponge) or null
 };
 
 // (1 + x)^gamma - 1: the binomial series (Horner) for small |x|, where the
@@ -385,6 +386,10 @@ __device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs
                                             int gz, double (&L)[5], bool& bad) {
   const long long np = P.np;
   const double rp = q[I], mu = q[np + I], mv = q[2 * np + I];
+  if (B.E) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[c] += B.E[c * np + I];
+  }
   L[1] = fma(P.f, mv, L[1]);                     // -f k x (rho u): +f rho v
   L[2] = fma(-P.f, mu, L[2]);                    //                 -f rho u
   L[3] = fma(-P.g, rp, L[3]);                    // -rho' g

@@ -1,5 +1,5 @@
-"""ctypes binding of the C ABI in ``include/xg.h``, ``include/xg_batch.h`` and
-``include/xg_closure.h`` (same function names).
+"""ctypes binding of the C ABI in ``include/xg.h``, ``include/xg_batch.h``,
+``include/xg_closure.h`` and ``include/xg_dynamics.h`` (same function names).
 
 Argument marshalling only: every step of the path runs in ``libxg.so``.
 Arrays may be torch tensors (CUDA tensors are passed as device pointers,
@@ -34,7 +34,8 @@ __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_cre
            "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC",
            "xg_features", "xg_restrict", "xg_column_stats", "xg_mlp_loss_grad", "xg_mlp_adam",
            "xg_mlp_forward", "xg_closure_set", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
-           "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS", "XG_HOST", "XG_DEVICE",
+           "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS",
+           "xg_dynamics", "xg_set_dynamics", "xg_dynamics_tendency", "xg_ri_velocity", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -56,6 +57,11 @@ class xg_batch_tuning(ctypes.Structure):
         return dict(schedule=("round_robin", "lpt", "dynamic")[self.schedule],
                     plane_tile=self.plane_tile, ctas_per_sm=self.ctas_per_sm,
                     ms_per_step=self.ms_per_step)
+
+
+class xg_dynamics(ctypes.Structure):
+    _fields_ = [("hyper_c", ctypes.c_double * 3), ("hyper_dt", ctypes.c_double),
+                ("sponge_depth", ctypes.c_double), ("sponge_gamma", ctypes.c_double)]
 
 
 class XgError(RuntimeError):
@@ -143,6 +149,12 @@ def library():
     lib.xg_mlp_forward.argtypes = [P, P, LL, LL, P, P, P, P, LL, I, P]
     lib.xg_closure_set.restype = I
     lib.xg_closure_set.argtypes = [P, P, P, P, P, P]
+    lib.xg_set_dynamics.restype = I
+    lib.xg_set_dynamics.argtypes = [P, ctypes.POINTER(xg_dynamics)]
+    lib.xg_dynamics_tendency.restype = I
+    lib.xg_dynamics_tendency.argtypes = [P, P, I, P]
+    lib.xg_ri_velocity.restype = I
+    lib.xg_ri_velocity.argtypes = [P, I, ctypes.POINTER(D), P, P, P]
     _lib = lib
     return lib
 
@@ -492,3 +504,33 @@ def xg_closure_set(ctx, params=None, in_mean=None, in_scale=None, out_scale=None
         return
     _check(library().xg_closure_set(ctx, _f32(params), _f32(in_mean), _f32(in_scale),
                                     _f32(out_scale), _default_stream(stream)), "xg_closure_set")
+
+
+# ------------------------------------------------------------------ remaining dynamics
+
+def xg_set_dynamics(ctx, hyper_c=(0.0, 0.0, 0.0), hyper_dt=1.0, sponge_depth=0.0, sponge_gamma=0.0,
+                    off=False):
+    """Hyper-diffusion (c_i, dt of Eq. 16) and the top sponge on an XG_FP64
+    context; off=True switches both off."""
+    if off:
+        _check(library().xg_set_dynamics(ctx, None), "xg_set_dynamics")
+        return
+    d = xg_dynamics((ctypes.c_double * 3)(*[float(v) for v in hyper_c]), float(hyper_dt),
+                    float(sponge_depth), float(sponge_gamma))
+    _check(library().xg_set_dynamics(ctx, ctypes.byref(d)), "xg_set_dynamics")
+
+
+def xg_dynamics_tendency(ctx, out, where=None, stream=None):
+    p, w, s = _ptr(out, where, writable=True)
+    _check(library().xg_dynamics_tendency(ctx, p, w, _stream(stream, s)), "xg_dynamics_tendency")
+
+
+def xg_ri_velocity(ctx, nstrips=50, stream=None):
+    """(u_RI, centroid [n_z, 2], strip means [n_z, nstrips]) of the state."""
+    nz = xg_mesh_dims(ctx)[2]
+    u = ctypes.c_double()
+    cent = np.zeros((nz, 2))
+    means = np.zeros((nz, int(nstrips)))
+    _check(library().xg_ri_velocity(ctx, int(nstrips), ctypes.byref(u), cent.ctypes.data,
+                                    means.ctypes.data, _default_stream(stream)), "xg_ri_velocity")
+    return u.value, cent, means
