@@ -32,6 +32,8 @@ numpy float64:
                 the tensor viscosity of Sec. 2.4, fourth-order
                 hyper-diffusion (Eq. 14), the top sponge (Sec. 4.1) and the
                 RI-velocity diagnostic (Sec. 5).
+* ``imex``    -- the IMEX ARK2 time integrator of Sec. 2.3 with the linear
+                fast-wave operator and Krylov stage solves.
 
 Every function cites the passage it follows.  The pins that tie each function
 to something other than itself live in ``tests/test_oracle_*.py``.
@@ -45,8 +47,11 @@ first step, bfloat16 ties, polynomial exactness of features and
 restriction; for the dynamics: conservation, symmetry and definiteness of the
 weak Laplacian, exact interior second derivatives of quadratics, spectral
 convergence and the k^4 damping of a Fourier mode, the tensor's closed form,
-the sponge profile, solid-body rotation for the RI velocity).  The synthetic config inputs themselves
+the sponge profile, solid-body rotation for the RI velocity; for IMEX: the
+tableau's order conditions, both stability functions, second-order
+convergence with a planted wrong gamma losing it, the dense-solve step, and
+the linear operator as the derivative of S at rest).  The synthetic config inputs themselves
 (vortex, heating cells) are inputs, not oracle functions.
 """
 
-from . import lgl, mesh, euler, ssprk3, closure, dynamics  # noqa: F401
+from . import lgl, mesh, euler, ssprk3, closure, dynamics, imex  # noqa: F401
