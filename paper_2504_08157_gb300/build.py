@@ -1,8 +1,8 @@
 """In-tree build of the CUDA library ``libxg.so`` (sm_103a only).
 
-Five translation units (the C ABI with the line kernels for orders 1-8,
+Six translation units (the C ABI with the line kernels for orders 1-8,
 the allocation-free right-hand side, the batched persistent form, the
-learned closure, and hyper-diffusion / sponge / RI velocity),
+learned closure, hyper-diffusion / sponge / RI velocity, and IMEX),
 compiled in parallel with nvcc for ``-gencode arch=compute_103a,code=sm_103a``
 and linked as a shared library next to this file.  The CUDA runtime is
 linked statically so the library loads without the toolkit's library path.
@@ -17,12 +17,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libxg.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("xg_api.cu", "xg_noalloc.cu", "xg_batch.cu",
-                                                         "xg_closure.cu", "xg_dynamics.cu")]
+                                                         "xg_closure.cu", "xg_dynamics.cu",
+                                                         "xg_imex.cu")]
 DEPENDS = SOURCES + [os.path.join(HERE, "csrc", f) for f in
                      ("xg_kernels.cuh", "xg_setup.h", "xg_df.cuh", "xg_kernels_df.cuh",
                       "xg_kernels_f32.cuh", "xg_plane_f32.cuh", "xg_ctx.h")] + [
                      os.path.join(ROOT, "include", f) for f in ("xg.h", "xg_batch.h", "xg_closure.h",
-                                                               "xg_dynamics.h")]
+                                                               "xg_dynamics.h", "xg_imex.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -371,6 +371,10 @@ cudaError_t export_values(xg_ctx* c, const void* src, double* dst, long long n, 
 
 }  // namespace
 
+cudaError_t rhs_fp64(xg_ctx* c, const double* q, double* out, cudaStream_t st) {
+  return run_stage(c, q, nullptr, out, 0.0, 0.0, 1.0, 1, st);
+}
+
 extern "C" {
 
 const char* xg_status_str(xg_status s) {
@@ -690,6 +694,7 @@ void xg_destroy(xg_ctx* c) {
   if (c->hflag) cudaFreeHost(c->hflag);
   closure_free(c);
   dynamics_free(c);
+  imex_free(c);
   delete c;
 }
 

@@ -61,7 +61,13 @@ struct xg_ctx {
   double* dyn_L1 = nullptr;
   double* dyn_E = nullptr;
   double* dyn_gamma = nullptr;   // [n_z] sponge rate per level
+  // IMEX work arrays (xg_imex.cu), allocated on first use
+  void* imex = nullptr;
 };
+
+void imex_free(xg_ctx* c);
+// the FP64 right-hand side S(q) into out (xg_api.cu)
+cudaError_t rhs_fp64(xg_ctx* c, const double* q, double* out, cudaStream_t st);
 
 // E = H(q) + sponge(q) of the FP64 stage input q into c->dyn_E
 // (xg_dynamics.cu); and freeing its buffers.

@@ -1,0 +1,561 @@
+// xg_imex.cu -- IMEX ARK2 time integration with matrix-free GMRES
+// (include/xg_imex.h).
+//
+// The linear operator is evaluated node by node: for each node the
+// assembled derivatives it needs (rho u along x, rho v along y, rho w and
+// theta_0 rho w along z, Theta' along x and y, p'_lin along z) are sums of
+// the pre-scaled derivative rows Dm over the node's segments (a face node
+// adds the segment before, a wall node doubles its row), exactly the
+// structure of the right-hand side's contractions.  One kernel returns
+// c0 v + c1 L(v), so a GMRES product (I - dt g L) v is a single pass.
+//
+// GMRES (restarted, classical Gram-Schmidt twice) runs on the host with
+// the device vectors; the inner products are deterministic (fixed grid,
+// per-block partial sums added on the host in block order) and weight
+// variable v by 1/rms(b_v)^2.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/xg_imex.h"
+#include "xg_ctx.h"
+#include "xg_setup.h"
+
+namespace xg {
+
+constexpr int kDotBlocks = 512;
+constexpr int kDotThreads = 256;
+constexpr int kDotBatch = 8;
+constexpr int kCombMax = 6;
+
+// sum over the node's segment(s) along d of Dm rows times f (times lev[k]
+// for the loaded node's index k along the line, when given): -d/dx_d of the
+// assembled field
+template <int N>
+__device__ __forceinline__ double line_sum(const LineParams& P, int d, const double* __restrict__ f,
+                                           long long base, long long sd, int g,
+                                           const double* __restrict__ lev) {
+  const int nd = P.n[d], nseg = P.nseg[d];
+  int s = g / N;
+  if (s >= nseg) s = nseg - 1;
+  const int a = g - s * N;
+  double acc = 0.0;
+#pragma unroll
+  for (int l = 0; l <= N; ++l) {
+    int k = s * N + l;
+    if (k >= nd) k -= nd;
+    const double v = f[base + sd * k];
+    acc = fma(P.Dm[d][a][l], lev ? lev[k] * v : v, acc);
+  }
+  if (a == 0) {
+    if (s > 0 || P.per[d]) {
+      const int s2 = s > 0 ? s - 1 : nseg - 1;
+#pragma unroll
+      for (int l = 0; l <= N; ++l) {
+        int k = s2 * N + l;
+        if (k >= nd) k -= nd;
+        const double v = f[base + sd * k];
+        acc = fma(P.Dm[d][N][l], lev ? lev[k] * v : v, acc);
+      }
+    } else {
+      acc = acc + acc;
+    }
+  } else if (a == N) {
+    acc = acc + acc;
+  }
+  return acc;
+}
+
+// out = c0 v + c1 L(v); cpl = gamma p0 / Theta0 and th0 = Theta0 / rho0 per level
+template <int N>
+__global__ void __launch_bounds__(128) k_linear(const LineParams P, const double* __restrict__ v,
+                                                const double* __restrict__ cpl,
+                                                const double* __restrict__ th0, double c0, double c1,
+                                                double* __restrict__ out) {
+  const long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (I >= P.np) return;
+  const long long np = P.np;
+  const int nx = P.n[0], ny = P.n[1];
+  const long long nxy = (long long)nx * ny;
+  const int gx = (int)(I % nx);
+  const long long r = I / nx;
+  const int gy = (int)(r % ny), gz = (int)(r / ny);
+  const long long bx = I - gx, by = I - (long long)gy * nx, bz = I - (long long)gz * nxy;
+  const double* ru = v + np;
+  const double* rv = v + 2 * np;
+  const double* rw = v + 3 * np;
+  const double* th = v + 4 * np;
+  const double dxu = line_sum<N>(P, 0, ru, bx, 1, gx, nullptr);
+  const double dyv = line_sum<N>(P, 1, rv, by, nx, gy, nullptr);
+  const double dzw = line_sum<N>(P, 2, rw, bz, nxy, gz, nullptr);
+  const double dzwt = line_sum<N>(P, 2, rw, bz, nxy, gz, th0);
+  const double dxp = cpl[gz] * line_sum<N>(P, 0, th, bx, 1, gx, nullptr);
+  const double dyp = cpl[gz] * line_sum<N>(P, 1, th, by, nx, gy, nullptr);
+  const double dzp = line_sum<N>(P, 2, th, bz, nxy, gz, cpl);
+  double L[5];
+  L[0] = dxu + dyv + dzw;
+  L[1] = dxp;
+  L[2] = dyp;
+  L[3] = fma(-P.g, v[I], dzp);
+  L[4] = fma(th0[gz], dxu + dyv, dzwt);
+  if (!P.per[0] && (gx == 0 || gx == nx - 1)) L[1] = 0.0;
+  if (!P.per[1] && (gy == 0 || gy == ny - 1)) L[2] = 0.0;
+  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[c * np + I] = c0 == 0.0 ? c1 * L[c] : fma(c1, L[c], c0 * v[c * np + I]);
+}
+
+struct Comb {
+  const double* x[kCombMax];
+  double c[kCombMax];
+  int k;
+};
+
+// out = sum_k c_k x_k (out may be one of the x_k)
+__global__ void k_comb(const Comb C, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int k = 0; k < C.k; ++k) a = fma(C.c[k], C.x[k][i], a);
+    out[i] = a;
+  }
+}
+
+struct Dots {
+  const double* v[kDotBatch];
+  int k;
+};
+
+// partial[b][i] = sum over block b's nodes of sum_var wt[var] w * v_i
+__global__ void __launch_bounds__(kDotThreads) k_wdots(const double* __restrict__ w, const Dots D,
+                                                       const double* __restrict__ wt, long long np,
+                                                       double* __restrict__ partial) {
+  __shared__ double red[kDotBatch][kDotThreads];
+  double acc[kDotBatch];
+#pragma unroll
+  for (int i = 0; i < kDotBatch; ++i) acc[i] = 0.0;
+  const long long per = (np + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(np, lo + per);
+  for (int c = 0; c < 5; ++c) {
+    const double s = wt[c];
+    for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) {
+      const double a = s * w[c * np + I];
+#pragma unroll
+      for (int i = 0; i < kDotBatch; ++i)
+        if (i < D.k) acc[i] = fma(a, D.v[i][c * np + I], acc[i]);
+    }
+  }
+  for (int i = 0; i < kDotBatch; ++i) red[i][threadIdx.x] = acc[i];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int i = 0; i < kDotBatch; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < kDotBatch) partial[blockIdx.x * kDotBatch + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// partial[b][c] = sum over block b's nodes of x_c^2
+__global__ void __launch_bounds__(kDotThreads) k_varsq(const double* __restrict__ x, long long np,
+                                                       double* __restrict__ partial) {
+  __shared__ double red[5][kDotThreads];
+  const long long per = (np + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(np, lo + per);
+  for (int c = 0; c < 5; ++c) {
+    double a = 0.0;
+    for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) a = fma(x[c * np + I], x[c * np + I], a);
+    red[c][threadIdx.x] = a;
+  }
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_lin_levels(const double* __restrict__ base, int nz, double gamma, double* __restrict__ cpl,
+                             double* __restrict__ th0) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nz) return;
+  const double rho0 = base[k], Th0 = base[nz + k], p0 = base[2 * nz + k], iTh0 = base[3 * nz + k];
+  cpl[k] = gamma * p0 * iTh0;
+  th0[k] = Th0 / rho0;
+}
+
+}  // namespace xg
+
+namespace {
+
+using xg::LineParams;
+
+struct Imex {
+  int m = 0;
+  long long n = 0;             // 5 np
+  double* V = nullptr;         // m + 1 Krylov vectors
+  double* x = nullptr;         // stage solution
+  double* b = nullptr;         // stage right-hand side
+  double* w = nullptr;         // work
+  double* S[3] = {nullptr, nullptr, nullptr};
+  double* L[2] = {nullptr, nullptr};
+  double* q1 = nullptr;        // q^{n+1}
+  double* cpl = nullptr;       // [nz]
+  double* th0 = nullptr;       // [nz]
+  double* wt = nullptr;        // [5] inner-product weights
+  double* partial = nullptr;   // [kDotBlocks][8]
+  std::vector<double> hpart;
+};
+
+cudaError_t launch_linear(xg_ctx* c, const Imex& X, const double* v, double c0, double c1, double* out,
+                          cudaStream_t st) {
+  const LineParams& P = c->P;
+  const unsigned blocks = (unsigned)((c->np + 127) / 128);
+  switch (c->d.order) {
+    case 1: xg::k_linear<1><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 2: xg::k_linear<2><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 3: xg::k_linear<3><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 4: xg::k_linear<4><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 5: xg::k_linear<5><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 6: xg::k_linear<6><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 7: xg::k_linear<7><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 8: xg::k_linear<8><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t comb(const std::vector<std::pair<double, const double*>>& terms, double* out, long long n,
+                 cudaStream_t st) {
+  // in chunks of kCombMax - 1 after the first, accumulating into out
+  size_t k = 0;
+  bool first = true;
+  while (k < terms.size() || first) {
+    xg::Comb C;
+    memset(&C, 0, sizeof(C));
+    int j = 0;
+    if (!first) {
+      C.x[j] = out;
+      C.c[j++] = 1.0;
+    }
+    while (j < xg::kCombMax && k < terms.size()) {
+      C.x[j] = terms[k].second;
+      C.c[j++] = terms[k].first;
+      ++k;
+    }
+    C.k = j;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 8192);
+    xg::k_comb<<<blocks, 256, 0, st>>>(C, out, n);
+    first = false;
+  }
+  return cudaGetLastError();
+}
+
+// weighted inner products of w with vs[0..k-1]
+cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* vs, int k, double* out,
+                  cudaStream_t st) {
+  for (int i0 = 0; i0 < k; i0 += xg::kDotBatch) {
+    xg::Dots D;
+    memset(&D, 0, sizeof(D));
+    D.k = std::min(xg::kDotBatch, k - i0);
+    for (int i = 0; i < D.k; ++i) D.v[i] = vs[i0 + i];
+    xg::k_wdots<<<xg::kDotBlocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * xg::kDotBlocks * xg::kDotBatch,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < D.k; ++i) {
+      double s = 0.0;
+      for (int b = 0; b < xg::kDotBlocks; ++b) s += X.hpart[(size_t)b * xg::kDotBatch + i];
+      out[i0 + i] = s;
+    }
+  }
+  return cudaSuccess;
+}
+
+// per-variable weights 1 / mean(b_v^2) (1 where b_v vanishes)
+cudaError_t set_weights(Imex& X, long long np, const double* b, cudaStream_t st) {
+  xg::k_varsq<<<xg::kDotBlocks, xg::kDotThreads, 0, st>>>(b, np, X.partial);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * xg::kDotBlocks * 5, cudaMemcpyDeviceToHost,
+                        st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  double wt[5];
+  for (int c = 0; c < 5; ++c) {
+    double s = 0.0;
+    for (int blk = 0; blk < xg::kDotBlocks; ++blk) s += X.hpart[(size_t)blk * 5 + c];
+    const double ms = s / (double)np;
+    wt[c] = ms > 0.0 ? 1.0 / ms : 1.0;
+  }
+  return cudaMemcpyAsync(X.wt, wt, sizeof(wt), cudaMemcpyHostToDevice, st);
+}
+
+// Solve (I - h L) x = b, x holding the initial guess; returns XG_ERR_TIMEOUT
+// when the relative residual stays above tol after the restarts.
+xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters, double* resid,
+                cudaStream_t st, cudaError_t* err) {
+  const long long np = c->np, n = X.n;
+  const int m = X.m;
+  auto vec = [&](int i) { return X.V + (size_t)i * n; };
+  *err = set_weights(X, np, X.b, st);
+  if (*err != cudaSuccess) return XG_ERR_CUDA;
+  double bn2;
+  const double* bp = X.b;
+  *err = wdots(X, np, X.b, &bp, 1, &bn2, st);
+  if (*err != cudaSuccess) return XG_ERR_CUDA;
+  const double bnorm = std::sqrt(bn2);
+  *iters = 0;
+  *resid = 0.0;
+  if (bnorm == 0.0) {
+    *err = cudaMemsetAsync(X.x, 0, sizeof(double) * n, st);
+    return *err == cudaSuccess ? XG_OK : XG_ERR_CUDA;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 1), h2(m + 1);
+  std::vector<const double*> vp(m + 1);
+  for (int rs = 0; rs < maxrs; ++rs) {
+    // r = b - (x - h L x)  into V_0
+    *err = launch_linear(c, X, X.x, 1.0, -h, X.w, st);
+    if (*err == cudaSuccess) *err = comb({{1.0, X.b}, {-1.0, X.w}}, vec(0), n, st);
+    double r2;
+    const double* r0 = vec(0);
+    if (*err == cudaSuccess) *err = wdots(X, np, vec(0), &r0, 1, &r2, st);
+    if (*err != cudaSuccess) return XG_ERR_CUDA;
+    const double beta = std::sqrt(r2);
+    *resid = beta / bnorm;
+    if (*resid <= tol) return XG_OK;
+    *err = comb({{1.0 / beta, vec(0)}}, vec(0), n, st);
+    if (*err != cudaSuccess) return XG_ERR_CUDA;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < m; ++j) {
+      // w = (I - h L) v_j, orthogonalised twice against v_0..v_j
+      *err = launch_linear(c, X, vec(j), 1.0, -h, vec(j + 1), st);
+      if (*err != cudaSuccess) return XG_ERR_CUDA;
+      for (int i = 0; i <= j; ++i) vp[i] = vec(i);
+      std::fill(hcol.begin(), hcol.end(), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        *err = wdots(X, np, vec(j + 1), vp.data(), j + 1, h2.data(), st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+        std::vector<std::pair<double, const double*>> t;
+        t.push_back({1.0, vec(j + 1)});
+        for (int i = 0; i <= j; ++i) {
+          t.push_back({-h2[i], vec(i)});
+          hcol[i] += h2[i];
+        }
+        *err = comb(t, vec(j + 1), n, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+      }
+      double w2;
+      const double* wp = vec(j + 1);
+      *err = wdots(X, np, vec(j + 1), &wp, 1, &w2, st);
+      if (*err != cudaSuccess) return XG_ERR_CUDA;
+      hcol[j + 1] = std::sqrt(w2);
+      ++*iters;
+      if (hcol[j + 1] > 0.0) {
+        *err = comb({{1.0 / hcol[j + 1], vec(j + 1)}}, vec(j + 1), n, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+      }
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = a;
+      }
+      const double den = std::hypot(hcol[j], hcol[j + 1]);
+      cs[j] = den > 0.0 ? hcol[j] / den : 1.0;
+      sn[j] = den > 0.0 ? hcol[j + 1] / den : 0.0;
+      hcol[j] = den;
+      hcol[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+      *resid = std::fabs(g[j + 1]) / bnorm;
+      if (*resid <= tol || hcol[j] == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    // x += V y with H y = g (upper triangular, j columns)
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * m + k] * y[k];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+    }
+    std::vector<std::pair<double, const double*>> t;
+    t.push_back({1.0, X.x});
+    for (int i = 0; i < j; ++i) t.push_back({y[i], vec(i)});
+    *err = comb(t, X.x, n, st);
+    if (*err != cudaSuccess) return XG_ERR_CUDA;
+    if (*resid <= tol) return XG_OK;
+  }
+  return XG_ERR_TIMEOUT;
+}
+
+void imex_free_buffers(Imex* X) {
+  cudaFree(X->V);
+  cudaFree(X->x);
+  cudaFree(X->b);
+  cudaFree(X->w);
+  for (auto& p : X->S) cudaFree(p);
+  for (auto& p : X->L) cudaFree(p);
+  cudaFree(X->q1);
+  cudaFree(X->cpl);
+  cudaFree(X->th0);
+  cudaFree(X->wt);
+  cudaFree(X->partial);
+}
+
+xg_status fail(xg_ctx* c, cudaError_t e, const char* where) {
+  fprintf(stderr, "xg_imex: %s: %s\n", where, cudaGetErrorString(e));
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return XG_ERR_OOM;
+  c->failed = true;
+  return XG_ERR_CUDA;
+}
+
+// allocate (or keep) the work arrays for m Krylov vectors; refresh the
+// per-level coefficients
+cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
+  Imex* X = static_cast<Imex*>(c->imex);
+  if (X && X->m != m) {
+    imex_free_buffers(X);
+    delete X;
+    X = nullptr;
+    c->imex = nullptr;
+  }
+  const long long n = 5 * c->np;
+  if (!X) {
+    X = new (std::nothrow) Imex();
+    if (!X) return cudaErrorMemoryAllocation;
+    c->imex = X;
+    X->m = m;
+    X->n = n;
+    X->hpart.resize((size_t)xg::kDotBlocks * xg::kDotBatch);
+    const size_t vb = sizeof(double) * (size_t)n;
+    cudaError_t e = cudaMalloc((void**)&X->V, vb * (m + 1));
+    double** bufs[] = {&X->x, &X->b, &X->w, &X->S[0], &X->S[1], &X->S[2], &X->L[0], &X->L[1], &X->q1};
+    for (double** p : bufs)
+      if (e == cudaSuccess) e = cudaMalloc((void**)p, vb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->cpl, sizeof(double) * c->n[2]);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->th0, sizeof(double) * c->n[2]);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->wt, sizeof(double) * 5);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->partial, sizeof(double) * xg::kDotBlocks * xg::kDotBatch);
+    if (e != cudaSuccess) {
+      imex_free_buffers(X);
+      delete X;
+      c->imex = nullptr;
+      return e;
+    }
+  }
+  xg::k_lin_levels<<<(c->n[2] + 127) / 128, 128, 0, st>>>(c->base, c->n[2], c->P.gamma, X->cpl, X->th0);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void imex_free(xg_ctx* c) {
+  Imex* X = static_cast<Imex*>(c->imex);
+  if (!X) return;
+  imex_free_buffers(X);
+  delete X;
+  c->imex = nullptr;
+}
+
+extern "C" {
+
+xg_status xg_linear_operator(xg_ctx* c, const double* v, double* out, void* stream) {
+  if (!c || !v || !out) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (!c->has_base) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = prepare(c, c->imex ? static_cast<Imex*>(c->imex)->m : 20, st);
+  if (e == cudaSuccess) e = launch_linear(c, *static_cast<Imex*>(c->imex), v, 0.0, 1.0, out, st);
+  return e == cudaSuccess ? XG_OK : fail(c, e, "xg_linear_operator");
+}
+
+xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opts, xg_imex_stats* stats,
+                       void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !c->has_state) return XG_ERR_ARG;
+  double tol = 1e-10;
+  int m = 20, maxrs = 50;
+  if (opts) {
+    tol = opts->tol;
+    m = opts->krylov;
+    maxrs = opts->max_restarts;
+    if (!(tol > 0.0 && tol < 1.0) || m < 1 || m > 64 || maxrs < 1) return XG_ERR_ARG;
+  }
+  if (stats) memset(stats, 0, sizeof(*stats));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = prepare(c, m, st);
+  if (e != cudaSuccess) return fail(c, e, "xg_step_imex");
+  Imex& X = *static_cast<Imex*>(c->imex);
+  const long long n = X.n;
+  const double G = 1.0 - 1.0 / std::sqrt(2.0), Dl = 1.0 / (2.0 * std::sqrt(2.0));
+  const double Al = (3.0 + 2.0 * std::sqrt(2.0)) / 6.0;
+  const double ae[3][3] = {{0, 0, 0}, {2 * G, 0, 0}, {1 - Al, Al, 0}};
+  const double ai[3][3] = {{0, 0, 0}, {G, G, 0}, {Dl, Dl, G}};
+  const double bw[3] = {Dl, Dl, G};
+  e = cudaMemsetAsync(c->flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(c, e, "xg_step_imex");
+  for (int step = 0; step < nsteps; ++step) {
+    const double* q = c->A;
+    // stage 1 is explicit: Q1 = q
+    e = rhs_fp64(c, q, X.S[0], st);
+    if (e == cudaSuccess) e = launch_linear(c, X, q, 0.0, 1.0, X.L[0], st);
+    const double* Q = q;
+    for (int i = 1; i < 3 && e == cudaSuccess; ++i) {
+      // b = q + dt sum_j (ae_ij (S_j - L_j) + ai_ij L_j)
+      std::vector<std::pair<double, const double*>> t;
+      t.push_back({1.0, q});
+      for (int j = 0; j < i; ++j) {
+        t.push_back({dt * ae[i][j], X.S[j]});
+        t.push_back({dt * (ai[i][j] - ae[i][j]), X.L[j]});
+      }
+      e = comb(t, X.b, n, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(X.x, Q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) break;
+      int it = 0;
+      double res = 0.0;
+      cudaError_t ge = cudaSuccess;
+      const xg_status s = gmres(c, X, dt * ai[i][i], tol, maxrs, &it, &res, st, &ge);
+      if (stats) {
+        stats->iterations += it;
+        stats->max_iterations = std::max(stats->max_iterations, it);
+        stats->solves += 1;
+        stats->max_residual = std::max(stats->max_residual, res);
+      }
+      if (s == XG_ERR_CUDA) return fail(c, ge, "xg_step_imex gmres");
+      if (s != XG_OK) return s;
+      // S and L of the stage value; keep the value as the next solve's first guess
+      e = rhs_fp64(c, X.x, X.S[i], st);
+      if (e == cudaSuccess && i < 2) e = launch_linear(c, X, X.x, 0.0, 1.0, X.L[i], st);
+      if (e == cudaSuccess && i == 1) e = cudaMemcpyAsync(X.w, X.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+      Q = X.w;
+    }
+    if (e == cudaSuccess)
+      e = comb({{1.0, q}, {dt * bw[0], X.S[0]}, {dt * bw[1], X.S[1]}, {dt * bw[2], X.S[2]}}, c->Dq, n, st);
+    if (e != cudaSuccess) return fail(c, e, "xg_step_imex");
+    std::swap(c->A, c->Dq);
+  }
+  e = cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, e, "xg_step_imex");
+  return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
+}
+
+}  // extern "C"

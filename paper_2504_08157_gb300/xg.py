@@ -1,5 +1,6 @@
 """ctypes binding of the C ABI in ``include/xg.h``, ``include/xg_batch.h``,
-``include/xg_closure.h`` and ``include/xg_dynamics.h`` (same function names).
+``include/xg_closure.h``, ``include/xg_dynamics.h`` and ``include/xg_imex.h``
+(same function names).
 
 Argument marshalling only: every step of the path runs in ``libxg.so``.
 Arrays may be torch tensors (CUDA tensors are passed as device pointers,
@@ -35,7 +36,8 @@ __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_cre
            "xg_features", "xg_restrict", "xg_column_stats", "xg_mlp_loss_grad", "xg_mlp_adam",
            "xg_mlp_forward", "xg_closure_set", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
            "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS",
-           "xg_dynamics", "xg_set_dynamics", "xg_dynamics_tendency", "xg_ri_velocity", "XG_HOST", "XG_DEVICE",
+           "xg_dynamics", "xg_set_dynamics", "xg_dynamics_tendency", "xg_ri_velocity",
+           "xg_imex_opts", "xg_imex_stats", "xg_step_imex", "xg_linear_operator", "XG_HOST", "XG_DEVICE",
            "XG_FP64", "XG_FP32", "XG_DF64", "XG_OK", "XG_ERR_ARG", "XG_ERR_CUDA", "XG_ERR_OOM",
            "XG_ERR_NONFINITE", "XG_ERR_TIMEOUT", "XG_ERR_UNSUPPORTED"]
 
@@ -62,6 +64,19 @@ class xg_batch_tuning(ctypes.Structure):
 class xg_dynamics(ctypes.Structure):
     _fields_ = [("hyper_c", ctypes.c_double * 3), ("hyper_dt", ctypes.c_double),
                 ("sponge_depth", ctypes.c_double), ("sponge_gamma", ctypes.c_double)]
+
+
+class xg_imex_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("krylov", ctypes.c_int), ("max_restarts", ctypes.c_int)]
+
+
+class xg_imex_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_longlong), ("max_iterations", ctypes.c_int),
+                ("solves", ctypes.c_int), ("max_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iterations=self.iterations, max_iterations=self.max_iterations,
+                    solves=self.solves, max_residual=self.max_residual)
 
 
 class XgError(RuntimeError):
@@ -155,6 +170,10 @@ def library():
     lib.xg_dynamics_tendency.argtypes = [P, P, I, P]
     lib.xg_ri_velocity.restype = I
     lib.xg_ri_velocity.argtypes = [P, I, ctypes.POINTER(D), P, P, P]
+    lib.xg_step_imex.restype = I
+    lib.xg_step_imex.argtypes = [P, D, I, ctypes.POINTER(xg_imex_opts), ctypes.POINTER(xg_imex_stats), P]
+    lib.xg_linear_operator.restype = I
+    lib.xg_linear_operator.argtypes = [P, P, P, P]
     _lib = lib
     return lib
 
@@ -534,3 +553,23 @@ def xg_ri_velocity(ctx, nstrips=50, stream=None):
     _check(library().xg_ri_velocity(ctx, int(nstrips), ctypes.byref(u), cent.ctypes.data,
                                     means.ctypes.data, _default_stream(stream)), "xg_ri_velocity")
     return u.value, cent, means
+
+
+# ------------------------------------------------------------------ IMEX
+
+def xg_step_imex(ctx, dt, nsteps, tol=1e-10, krylov=20, max_restarts=50, stream=None):
+    """nsteps IMEX ARK2 steps; returns the solver statistics."""
+    o = xg_imex_opts(float(tol), int(krylov), int(max_restarts))
+    st = xg_imex_stats()
+    _check(library().xg_step_imex(ctx, float(dt), int(nsteps), ctypes.byref(o), ctypes.byref(st),
+                                  _default_stream(stream)), "xg_step_imex")
+    return st
+
+
+def xg_linear_operator(ctx, v, out, stream=None):
+    """out = L(v) (device float64 arrays [5][Np])."""
+    pv, wv, sv = _ptr(v)
+    po, wo, _ = _ptr(out, writable=True)
+    if wv != XG_DEVICE or wo != XG_DEVICE:
+        raise ValueError("xg_linear_operator takes device arrays")
+    _check(library().xg_linear_operator(ctx, pv, po, _stream(stream, sv)), "xg_linear_operator")

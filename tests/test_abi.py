@@ -1,5 +1,5 @@
 """CPU tests of the C-ABI library: it builds, loads, exports every function
-that include/xg.h, xg_batch.h, xg_closure.h and xg_dynamics.h declare, and rejects invalid
+that include/xg.h, xg_batch.h, xg_closure.h, xg_dynamics.h and xg_imex.h declare, and rejects invalid
 arguments on the host before any GPU work (no compute calls here)."""
 
 import ctypes
@@ -10,7 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", h) for h in ("xg.h", "xg_batch.h", "xg_closure.h",
-                                                    "xg_dynamics.h")]
+                                                    "xg_dynamics.h", "xg_imex.h")]
 
 
 @pytest.fixture(scope="module")
