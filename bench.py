@@ -412,8 +412,10 @@ def run_xg(args, world, rank, local):
                                 False, compare=True, oracle_check=rank == 0)
         batched.pop("clocks", None)
     closure_rate = None
+    dyn = None
     if not args.no_plain and not args.no_batch:
         closure_rate = closure_throughput(xg, torch, dev, stream, max(1, min(K, 10)), 3)
+        dyn = dynamics_measure(xg, torch, dev, stream)
 
     cpu, l2 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -445,6 +447,7 @@ def run_xg(args, world, rank, local):
                                               if fp32 and plain else None),
                "batched_form": batched,
                "closure_form": closure_rate,
+               "paper_dynamics": dyn,
                "l2_error_vs_oracle": l2,
                "hbm_roofline_frac": round(hbm_frac, 4),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -668,6 +671,53 @@ def run_batch(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ the paper's remaining dynamics
+
+def dynamics_measure(xg, torch, dev, stream, K=5):
+    """FP64 on the cyclone box: explicit SSP-RK3 at dt = 0.1 s against IMEX
+    ARK2 (matrix-free GMRES) at the paper's dt = 0.5 s, with and without
+    hyper-diffusion (c = 1e-4 on the three axes) and a 4 km top sponge
+    (gamma_max = 0.05 1/s); simulated seconds per wall-clock second; and
+    the RI-velocity diagnostic's cost."""
+    wl = workload("tc")
+    out = {}
+
+    def timed(run, ctx):
+        run(ctx, 1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = run(ctx, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K, res
+
+    ctx = make_ctx(xg, torch, wl, dev, xg.XG_FP64)
+    try:
+        ms, _ = timed(lambda c, n: xg.xg_step(c, 0.1, n, stream=stream.cuda_stream), ctx)
+        out["explicit_fp64"] = {"dt": 0.1, "ms_per_step": round(ms, 3),
+                                "simulated_s_per_s": round(0.1 / (ms / 1e3), 2)}
+        for name, dyn in (("imex_fp64", None), ("imex_fp64_hyperdiffusion_sponge", True)):
+            if dyn:
+                xg.xg_set_dynamics(ctx, (1e-4, 1e-4, 1e-4), 0.5, 4000.0, 0.05)
+            ms, st = timed(lambda c, n: xg.xg_step_imex(c, 0.5, n, tol=1e-8, stream=stream.cuda_stream), ctx)
+            out[name] = {"dt": 0.5, "ms_per_step": round(ms, 3),
+                         "simulated_s_per_s": round(0.5 / (ms / 1e3), 2),
+                         "gmres": st.as_dict(), "tol": 1e-8}
+        xg.xg_set_dynamics(ctx, off=True)
+        t0 = time.perf_counter()
+        u, _, _ = xg.xg_ri_velocity(ctx, 50)
+        out["ri_velocity"] = {"value_m_per_s": round(u, 3), "ms": round(1e3 * (time.perf_counter() - t0), 2),
+                              "strips": 50}
+    finally:
+        xg.xg_destroy(ctx)
+    out["config"] = "tc 128x128x16 N=4 FP64"
+    out["speedup_imex_vs_explicit"] = round(out["imex_fp64"]["simulated_s_per_s"] /
+                                            out["explicit_fp64"]["simulated_s_per_s"], 3)
+    return out
 
 
 # ------------------------------------------------------------------ learned-closure form
