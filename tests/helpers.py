@@ -37,7 +37,7 @@ def oracle_steps(wl, nsteps, q=None):
     return ssprk3.run(L, wl["q"] if q is None else q, wl["dt"], nsteps)
 
 
-class GpuRun:
+class GpuContext:
     """One library context for a workload, inputs resident on cuda:0."""
 
     def __init__(self, wl, device="cuda:0", precision=0):

@@ -14,7 +14,7 @@ import pytest
 
 from inputs import workloads as W
 
-from helpers import BatchRun, GpuRun, oracle_rhs, oracle_steps, rel_l2_per_var
+from helpers import BatchRun, GpuContext, oracle_rhs, oracle_steps, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_batch_is_bitwise_the_single_context(cuda_device, wls):
         b.step(3)
         q = b.states()
     for i, wl in enumerate(wls):
-        with GpuRun(wl, precision=FP32) as g:
+        with GpuContext(wl, precision=FP32) as g:
             r1 = g.rhs()
             g.step(3)
             q1 = g.state()
@@ -169,7 +169,7 @@ def test_full_batch_rhs_is_the_single_contexts(cuda_device):
         b.xg.xg_batch_autotune(b.b, b.dts, trial_steps=1)
         got = b.rhs()
     for i, wl in enumerate(wls):
-        with GpuRun(wl, precision=FP32) as g:
+        with GpuContext(wl, precision=FP32) as g:
             assert np.array_equal(got[i], g.rhs()), i
     sizes = np.argsort([g.shape[1] for g in got])
     for i in sizes[:2]:

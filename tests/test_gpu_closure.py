@@ -10,7 +10,7 @@ import pytest
 from inputs import rng, workloads as W
 from oracle import closure as OC, euler as E
 
-from helpers import GpuRun, oracle_of, rel_l2
+from helpers import GpuContext, oracle_of, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_features_match_oracle(cuda_device):
     from paper_2504_08157_gb300 import xg
     for N, per in ((3, (True, False, False)), (4, (False, True, False)), (6, (True, True, True))):
         wl = W.box((3, 2, 2), N, (0.0, 0.0, 0.0), (3000.0, 2000.0, 2000.0), per, seed=70 + N)
-        with GpuRun(wl, precision=FP32) as g:
+        with GpuContext(wl, precision=FP32) as g:
             X = torch.empty((21, g.np), dtype=torch.float32, device=cuda_device)
             xg.xg_features(g.ctx, X)
             q32 = g.state()                       # the FP32 state the kernel saw
@@ -60,7 +60,7 @@ def test_restriction_matches_oracle(cuda_device, per):
     N = 4
     fine = W.box((4, 6, 4), N, (0.0, 0.0, 0.0), (2000.0, 3000.0, 2000.0), per, seed=81)
     coarse = W.box((2, 3, 2), N, (0.0, 0.0, 0.0), (2000.0, 3000.0, 2000.0), per, seed=82)
-    with GpuRun(fine) as gf, GpuRun(coarse) as gc:
+    with GpuContext(fine) as gf, GpuContext(coarse) as gc:
         src = _t(fine["q"], cuda_device)
         dst = torch.empty((5, gc.np), dtype=torch.float64, device=cuda_device)
         xg.xg_restrict(gf.ctx, gc.ctx, src, dst)
@@ -163,7 +163,7 @@ def test_closure_in_the_rhs(cuda_device):
     sin[5:20] = 1e2            # gradients are O(1e-2) per metre
     sout = np.full(5, 1e-3, np.float32)
     d = cuda_device
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         plain = g.rhs()
         xg.xg_closure_set(g.ctx, _t(p, d), _t(mean, d), _t(sin, d), _t(sout, d))
         withc = g.rhs()
@@ -189,7 +189,7 @@ def test_closure_only_on_fp32(cuda_device):
     import torch
     z = torch.zeros(OC.param_count(), dtype=torch.float32, device=cuda_device)
     o = torch.ones(21, dtype=torch.float32, device=cuda_device)
-    with GpuRun(wl, precision=0) as g:
+    with GpuContext(wl, precision=0) as g:
         with pytest.raises(xg.XgError) as e:
             xg.xg_closure_set(g.ctx, z, o, o, o[:5])
         assert e.value.status == xg.XG_ERR_UNSUPPORTED

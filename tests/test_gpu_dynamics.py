@@ -10,7 +10,7 @@ import pytest
 from inputs import workloads as W
 from oracle import dynamics as Y, euler as E, ssprk3
 
-from helpers import GpuRun, oracle_of, rel_l2_per_var
+from helpers import GpuContext, oracle_of, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def _oracle_terms(wl, q=None):
 def test_extra_tendency_matches_oracle(cuda_device, N, per):
     import torch
     wl = _case(N, per)
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         g.xg.xg_set_dynamics(g.ctx, C, DT_H, DEPTH, GAMMA)
         out = torch.empty((5, g.np), dtype=torch.float64, device=cuda_device)
         g.xg.xg_dynamics_tendency(g.ctx, out)
@@ -58,7 +58,7 @@ def test_rhs_and_steps_with_the_terms(cuda_device):
         extra = Y.hyperdiffusion(m, s, tau) + Y.sponge(m, s, DEPTH, GAMMA)
         return E.apply_walls(m, E.rhs(m, s, base, wl["S_theta"], phys) + extra)
 
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         g.xg.xg_set_dynamics(g.ctx, c, wl["dt"], DEPTH, GAMMA)
         r = g.rhs()
         assert np.all(rel_l2_per_var(r, L(wl["q"])) <= 1e-12)
@@ -73,7 +73,7 @@ def test_terms_off_and_unsupported(cuda_device):
     import torch
     from paper_2504_08157_gb300 import xg
     wl = _case()
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         plain = g.rhs()
         xg.xg_set_dynamics(g.ctx, C, DT_H, DEPTH, GAMMA)
         xg.xg_set_dynamics(g.ctx, off=True)
@@ -87,7 +87,7 @@ def test_terms_off_and_unsupported(cuda_device):
                 xg.xg_set_dynamics(g.ctx, **bad)
             assert e.value.status == xg.XG_ERR_ARG
     for prec in (1, 2):
-        with GpuRun(wl, precision=prec) as g:
+        with GpuContext(wl, precision=prec) as g:
             with pytest.raises(xg.XgError) as e:
                 xg.xg_set_dynamics(g.ctx, C, DT_H)
             assert e.value.status == xg.XG_ERR_UNSUPPORTED
@@ -96,7 +96,7 @@ def test_terms_off_and_unsupported(cuda_device):
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 def test_ri_velocity_matches_oracle(cuda_device, prec):
     wl = W.tc(nel=(12, 12, 4), state="initial")
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         u, cent, means = g.xg.xg_ri_velocity(g.ctx, 50)
         q = g.state()
     m, _, _ = oracle_of(wl)

@@ -13,7 +13,7 @@ import pytest
 from inputs import workloads as W
 from oracle import euler as E
 
-from helpers import GpuRun, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
+from helpers import GpuContext, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +29,7 @@ def test_fp32_rhs_every_order(cuda_device, N):
     their bar is 5e-5."""
     wl = W.box((2, 3, 2), N, (0.0, 0.0, 0.0), (2000.0, 3000.0, 2000.0), (True, False, True),
                seed=40 + N)
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         got = g.rhs()
     err = rel_l2_per_var(got, oracle_rhs(wl))
     assert np.all(err <= (RHS_TOL32 if N > 1 else 5e-5)), err
@@ -44,7 +44,7 @@ def test_fp32_rhs_every_order(cuda_device, N):
 def test_fp32_rhs_sizes_and_boundaries(cuda_device, nel, periodic):
     L = tuple(1000.0 * n for n in nel)
     wl = W.box(nel, 4, (0.0, 0.0, 0.0), L, periodic, seed=sum(nel) + 3)
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         got = g.rhs()
     err = rel_l2_per_var(got, oracle_rhs(wl))
     assert np.all(err <= RHS_TOL32), err
@@ -52,7 +52,7 @@ def test_fp32_rhs_sizes_and_boundaries(cuda_device, nel, periodic):
 
 def test_fp32_rhs_tc_scaled(cuda_device):
     wl = W.tc(nel=(16, 16, 4), state="random")
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         got = g.rhs()
     err = rel_l2_per_var(got, oracle_rhs(wl))
     assert np.all(err <= RHS_TOL32), err
@@ -66,11 +66,11 @@ def test_fp32_bubble_rhs_and_200_steps(cuda_device):
     errors are bounded as regression guards: state within 2e-5, its change
     within 1e-2."""
     wl = W.bubble(state="random")
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         r = g.rhs()
     assert np.all(rel_l2_per_var(r, oracle_rhs(wl)) <= RHS_TOL32)
     wl = W.bubble()
-    with GpuRun(wl, precision=FP32) as g:
+    with GpuContext(wl, precision=FP32) as g:
         r = g.rhs()
         g.step(200)
         q = g.state()
@@ -102,7 +102,7 @@ def test_diagnostics_match_oracle_mass_sums(cuda_device, prec):
     wl = W.tc(nel=(6, 5, 4), state="random")
     m, _, _ = oracle_of(wl)
     M = E.mass(m)
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         d = np.array(g.xg.xg_diagnostics(g.ctx))
         q = g.state()
     ref = q @ M
@@ -116,7 +116,7 @@ def test_mass_conserved_on_gpu(cuda_device, prec, tol):
     """Walled bubble box: the FP64 sum of M rho' is unchanged after 20 steps,
     relative to the total mass (FP32 to its own rounding)."""
     wl = W.bubble()
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         before = g.xg.xg_diagnostics(g.ctx)[0]
         g.step(20)
         after = g.xg.xg_diagnostics(g.ctx)[0]

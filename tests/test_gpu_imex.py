@@ -9,7 +9,7 @@ import pytest
 from inputs import workloads as W
 from oracle import euler as E, imex as X
 
-from helpers import GpuRun, oracle_of, rel_l2_per_var
+from helpers import GpuContext, oracle_of, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_linear_operator_matches_oracle(cuda_device, per, N):
     import torch
     wl = _case(per, N)
     _, _, L = _oracle(wl)
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         v = torch.from_numpy(wl["q"]).to(cuda_device)
         out = torch.empty_like(v)
         g.xg.xg_linear_operator(g.ctx, v, out)
@@ -46,7 +46,7 @@ def test_steps_match_oracle(cuda_device, factor):
     wl = _case()
     _, S, L = _oracle(wl)
     dt = wl["dt"] * factor
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         st = g.xg.xg_step_imex(g.ctx, dt, 3, tol=1e-12)
         q = g.state()
     ref = wl["q"]
@@ -62,11 +62,11 @@ def test_steps_match_oracle(cuda_device, factor):
 def test_imex_takes_steps_the_explicit_scheme_cannot(cuda_device):
     wl = _case(seed=33)
     dt = wl["dt"] * 40.0
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         g.xg.xg_step_imex(g.ctx, dt, 20, tol=1e-10)
         q = g.state()
         assert np.all(np.isfinite(q)) and np.abs(q[1:3]).max() < 10.0
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         with pytest.raises(g.xg.XgError) as e:
             g.xg.xg_step(g.ctx, dt, 20)
         assert e.value.status == g.xg.XG_ERR_NONFINITE
@@ -74,7 +74,7 @@ def test_imex_takes_steps_the_explicit_scheme_cannot(cuda_device):
 
 def test_bounded_solve_reports_timeout_and_keeps_the_state(cuda_device):
     wl = _case()
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         before = g.state()
         with pytest.raises(g.xg.XgError) as e:
             g.xg.xg_step_imex(g.ctx, wl["dt"] * 20, 1, tol=1e-15, krylov=1, max_restarts=1)
@@ -86,7 +86,7 @@ def test_bounded_solve_reports_timeout_and_keeps_the_state(cuda_device):
 def test_imex_arguments_and_precisions(cuda_device):
     from paper_2504_08157_gb300 import xg
     wl = _case()
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         for kw in (dict(tol=0.0), dict(tol=1.0), dict(krylov=0), dict(krylov=65), dict(max_restarts=0)):
             with pytest.raises(xg.XgError) as e:
                 xg.xg_step_imex(g.ctx, 0.1, 1, **kw)
@@ -95,7 +95,7 @@ def test_imex_arguments_and_precisions(cuda_device):
             xg.xg_step_imex(g.ctx, -0.1, 1)
         assert e.value.status == xg.XG_ERR_ARG
     for prec in (1, 2):
-        with GpuRun(wl, precision=prec) as g:
+        with GpuContext(wl, precision=prec) as g:
             with pytest.raises(xg.XgError) as e:
                 xg.xg_step_imex(g.ctx, 0.1, 1)
             assert e.value.status == xg.XG_ERR_UNSUPPORTED

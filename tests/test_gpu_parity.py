@@ -16,7 +16,7 @@ import pytest
 from inputs import workloads as W
 from oracle import euler as E, lgl, mesh as M
 
-from helpers import GpuRun, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
+from helpers import GpuContext, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +26,7 @@ PREC = pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "df64"])
 
 
 def _check_rhs(wl, prec=0):
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         got = g.rhs()
     ref = oracle_rhs(wl)
     err = rel_l2_per_var(got, ref)
@@ -94,7 +94,7 @@ def test_rhs_bubble_after_100_oracle_steps(cuda_device, prec):
 @pytest.mark.slow
 def test_bubble_100_steps(cuda_device, prec):
     wl = W.bubble()
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(100)
         got = g.state()
     ref = oracle_steps(wl, 100)
@@ -107,7 +107,7 @@ def test_bubble_100_steps(cuda_device, prec):
 @PREC
 def test_tc_scaled_20_steps(cuda_device, prec):
     wl = W.tc(nel=(8, 8, 4), state="random")
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(20)
         got = g.state()
     ref = oracle_steps(wl, 20)
@@ -120,7 +120,7 @@ def test_tc_scaled_20_steps(cuda_device, prec):
 def test_steps_other_orders(cuda_device, N, prec):
     wl = W.box((3, 2, 2), N, (0.0, 0.0, 0.0), (3000.0, 2000.0, 2000.0), (True, True, False),
                seed=20 + N)
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(10)
         got = g.state()
     ref = oracle_steps(wl, 10)
@@ -151,7 +151,7 @@ def _sample_nodes(n, rng, count):
 
 
 def _full_size_sampled(wl, prec):
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         got = g.rhs()
         n = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[0] // 5
         assert g.np == n
@@ -223,7 +223,7 @@ def test_full_size_tc_step_conserves_mass(cuda_device, full_tc, prec):
 
     Wx, Wy, Wz = W1(128, True), W1(128, True), W1(16, False)
     Mm = (Wz[:, None, None] * Wy[None, :, None] * Wx[None, None, :]).reshape(-1)
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(1)
         q1 = g.state()
     rho0 = wl["rho0"][np.arange(Mm.size) // (512 * 512)]
@@ -239,7 +239,7 @@ def test_deterministic(cuda_device, prec):
     wl = W.tc(nel=(8, 8, 4), state="random")
     outs = []
     for _ in range(2):
-        with GpuRun(wl, precision=prec) as g:
+        with GpuContext(wl, precision=prec) as g:
             g.step(5)
             outs.append(g.state())
     assert np.array_equal(outs[0], outs[1])
@@ -248,13 +248,13 @@ def test_deterministic(cuda_device, prec):
 @PREC
 def test_checkpoint_resume_bitwise(cuda_device, prec):
     wl = W.bubble(nel=(4, 4, 4))
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(10)
         straight = g.state()
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         g.step(5)
         mid = g.state()
-    with GpuRun(dict(wl, q=mid), precision=prec) as g:
+    with GpuContext(dict(wl, q=mid), precision=prec) as g:
         g.step(5)
         resumed = g.state()
     if prec == 0:
@@ -269,7 +269,7 @@ def test_checkpoint_resume_bitwise(cuda_device, prec):
 @PREC
 def test_rhs_does_not_modify_state(cuda_device, prec):
     wl = W.bubble(nel=(4, 4, 4), state="random")
-    with GpuRun(wl, precision=prec) as g:
+    with GpuContext(wl, precision=prec) as g:
         before = g.state()
         g.rhs()
         assert np.array_equal(g.state(), before)
@@ -283,7 +283,7 @@ def test_nonfinite_is_reported(cuda_device, prec):
     wl = W.bubble(nel=(2, 2, 2))
     q = wl["q"].copy()
     q[1, 17] = np.nan
-    with GpuRun(dict(wl, q=q), precision=prec) as g:
+    with GpuContext(dict(wl, q=q), precision=prec) as g:
         with pytest.raises(xg.XgError) as e:
             g.step(1)
         assert e.value.status == xg.XG_ERR_NONFINITE
@@ -298,7 +298,7 @@ def test_host_pointers_and_side_stream(cuda_device):
     import torch
     from paper_2504_08157_gb300 import xg
     wl = W.tc(nel=(4, 4, 3), state="random")
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         ref = g.rhs()
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -311,7 +311,7 @@ def test_host_pointers_and_side_stream(cuda_device):
 def test_two_contexts_coexist(cuda_device):
     a = W.bubble(nel=(2, 2, 2), state="random")
     b = W.tc(nel=(4, 4, 2), state="random")
-    with GpuRun(a) as ga, GpuRun(b) as gb:
+    with GpuContext(a) as ga, GpuContext(b) as gb:
         ra, rb = ga.rhs(), gb.rhs()
     assert np.all(rel_l2_per_var(ra, oracle_rhs(a)) <= RHS_TOL)
     assert np.all(rel_l2_per_var(rb, oracle_rhs(b)) <= RHS_TOL)
@@ -319,7 +319,7 @@ def test_two_contexts_coexist(cuda_device):
 
 def test_zero_steps_is_identity(cuda_device):
     wl = W.bubble(nel=(2, 2, 2), state="random")
-    with GpuRun(wl) as g:
+    with GpuContext(wl) as g:
         g.step(0)
         assert np.array_equal(g.state(), wl["q"])
 
@@ -333,9 +333,9 @@ def test_contexts_of_one_order_coexist(cuda_device, prec):
                 seed=91)
     small = W.box((1, 2, 2), 4, (0.0, 0.0, 0.0), (1000.0, 2000.0, 2000.0), (False, True, False),
                   seed=92)
-    with GpuRun(big, precision=prec) as g:
+    with GpuContext(big, precision=prec) as g:
         r0 = g.rhs()
-        with GpuRun(small, precision=prec) as s:
+        with GpuContext(small, precision=prec) as s:
             s.rhs()
             r1 = g.rhs()
     assert np.array_equal(r0, r1)

@@ -11,7 +11,7 @@ import pytest
 
 from inputs import workloads as W
 
-from helpers import GpuRun, rel_l2_per_var
+from helpers import GpuContext, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +45,7 @@ def test_noalloc_rhs_matches_context_rhs(cuda_device):
     second = W.bubble(state="random")                 # 33^3 nodes, walls, no heating
     for k, wl in enumerate((first, second)):
         got, free0, free1 = _noalloc_rhs(xg, torch, cuda_device, wl)
-        with GpuRun(wl) as g:
+        with GpuContext(wl) as g:
             ref = g.rhs()
         err = rel_l2_per_var(got, ref)
         assert np.all(np.isfinite(got))
