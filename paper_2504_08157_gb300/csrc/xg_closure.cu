@@ -48,46 +48,60 @@ static_assert(kOffB3 + kOut == kParams, "parameter layout");
 
 // ------------------------------------------------------------------ features
 
-// Assembled derivative along direction d of the field f at global index g
-// of a line whose first node is f[base] (stride sd): the rows of the scaled
-// matrix Dm = -(2/h) D (rows 0 and N halved) over the node's segment, plus
-// row N of the segment before at a shared face, or twice the one-sided row
-// at a wall; the sign undoes Dm's minus.
+// The stencil of the assembled derivative along direction d at global
+// index g of a line starting at offset base (stride sd): the node's segment
+// (row a of the scaled matrix Dm = -(2/h) D, rows 0 and N halved), at a
+// shared face also the segment before (its row N), at a wall the one
+// segment's row doubled.  Built once per direction and applied to all five
+// variables.
 template <int N>
-__device__ __forceinline__ float line_derivative(const FParams& P, int d, const float* __restrict__ f,
-                                                 long long base, long long sd, int g) {
+struct LineStencil {
+  int off[2 * (N + 1)];   // within one variable's array (np < 2^31)
+  float r0[N + 1], r1[N + 1];
+  bool two;
+  float scale;
+};
+
+template <int N>
+__device__ __forceinline__ void line_stencil(const FParams& P, int d, long long base, long long sd, int g,
+                                             LineStencil<N>& L) {
   const int nd = P.n[d], nseg = P.nseg[d];
   int s = g / N;
   if (s >= nseg) s = nseg - 1;
   const int a = g - s * N;
-  float acc = 0.0f;
 #pragma unroll
   for (int l = 0; l <= N; ++l) {
     int k = s * N + l;
     if (k >= nd) k -= nd;
-    acc = fmaf(P.Dm[d][a][l], f[base + sd * k], acc);
+    L.off[l] = (int)(base + sd * k);
+    L.r0[l] = P.Dm[d][a][l];
   }
-  if (a == 0) {
-    if (s > 0 || P.per[d]) {
-      const int s2 = s > 0 ? s - 1 : nseg - 1;
+  L.two = a == 0 && (s > 0 || P.per[d]);
+  L.scale = (a == N || (a == 0 && !L.two)) ? -2.0f : -1.0f;   // the sign undoes Dm's minus
+  const int s2 = s > 0 ? s - 1 : nseg - 1;
 #pragma unroll
-      for (int l = 0; l <= N; ++l) {
-        int k = s2 * N + l;
-        if (k >= nd) k -= nd;
-        acc = fmaf(P.Dm[d][N][l], f[base + sd * k], acc);
-      }
-    } else {
-      acc = acc + acc;
-    }
-  } else if (a == N) {
-    acc = acc + acc;
+  for (int l = 0; l <= N; ++l) {
+    int k = s2 * N + l;
+    if (k >= nd) k -= nd;
+    L.off[N + 1 + l] = L.two ? (int)(base + sd * k) : L.off[l];
+    L.r1[l] = L.two ? P.Dm[d][N][l] : 0.0f;
   }
-  return -acc;
 }
 
-// The 21 features of node I, handed to emit(f, value) one variable at a
-// time (the loop over variables is not unrolled, so only one variable's
-// loads and results are live at once).
+template <int N>
+__device__ __forceinline__ float line_apply(const LineStencil<N>& L, const float* __restrict__ f) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int l = 0; l <= N; ++l) acc = fmaf(L.r0[l], f[L.off[l]], acc);
+  if (L.two) {
+#pragma unroll
+    for (int l = 0; l <= N; ++l) acc = fmaf(L.r1[l], f[L.off[N + 1 + l]], acc);
+  }
+  return L.scale * acc;
+}
+
+// The 21 features of node I, handed to emit(f, value): per direction the
+// stencil once, then that direction's derivative of all five variables.
 template <int N, typename Emit>
 __device__ __forceinline__ void node_features(const FParams& P, const float* __restrict__ q,
                                               const float* __restrict__ S, long long I, Emit emit) {
@@ -96,14 +110,16 @@ __device__ __forceinline__ void node_features(const FParams& P, const float* __r
   const int gx = (int)(I % nx);
   const long long r = I / nx;
   const int gy = (int)(r % ny), gz = (int)(r / ny);
-  const long long bx = I - gx, by = I - (long long)gy * nx, bz = I - (long long)gz * nx * ny;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) emit(v, q[v * np + I]);
 #pragma unroll 1
-  for (int v = 0; v < 5; ++v) {
-    const float* f = q + v * np;
-    emit(v, f[I]);
-    emit(5 + 3 * v, line_derivative<N>(P, 0, f, bx, 1, gx));
-    emit(6 + 3 * v, line_derivative<N>(P, 1, f, by, nx, gy));
-    emit(7 + 3 * v, line_derivative<N>(P, 2, f, bz, (long long)nx * ny, gz));
+  for (int d = 0; d < 3; ++d) {
+    LineStencil<N> L;
+    if (d == 0) line_stencil<N>(P, 0, I - gx, 1, gx, L);
+    else if (d == 1) line_stencil<N>(P, 1, I - (long long)gy * nx, nx, gy, L);
+    else line_stencil<N>(P, 2, I - (long long)gz * nx * ny, (long long)nx * ny, gz, L);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) emit(5 + 3 * v + d, line_apply<N>(L, q + v * np));
   }
   emit(20, S ? S[I] : 0.0f);
 }

@@ -27,6 +27,16 @@ constexpr int kPlaneThreads = 256;
 constexpr int kPlaneBatch = 2;
 
 // Shared-memory layout of a tile of E x E elements (floats), see f_plane_tile.
+// a / b for 0 <= a < 2^22 and 1 <= b <= 64 from a float reciprocal (the
+// tile index arithmetic; exact: the quotient estimate is corrected once)
+__device__ __forceinline__ int small_div(int a, int b, float rb) {
+  int q = (int)((float)a * rb);
+  const int r = a - q * b;
+  if (r < 0) --q;
+  else if (r >= b) ++q;
+  return q;
+}
+
 template <int N, int E_ = plane_elems_f32(N)>
 struct PlaneLayoutF {
   static constexpr int E = E_;
@@ -81,6 +91,7 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
   const int wx = ekx * N + N + 1, wy = eky * N + N + 1;
   const int nrow = oy * wx;                       // owned rows, full width
   const int nitem = nrow + ox * (wy - oy);        // + owned columns, remaining rows
+  const float rwx = 1.0f / (float)wx, rox = 1.0f / (float)ox;
   for (int base = tid; base < nitem; base += BATCH * nthr) {
     int ib[BATCH], jb[BATCH];
     long long Ib[BATCH];
@@ -90,11 +101,11 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
       const int idx = base + u * nthr;
       int i = -N - 1, j = 0;                      // i = -N - 1 marks "nothing to do"
       if (idx < nrow) {
-        i = idx % wx - N;
-        j = idx / wx;
+        j = small_div(idx, wx, rwx);
+        i = idx - j * wx - N;
       } else if (idx < nitem) {
-        const int r = (idx - nrow) / ox;
-        i = (idx - nrow) % ox;
+        const int r = small_div(idx - nrow, ox, rox);
+        i = (idx - nrow) - r * ox;
         j = r < N ? r - N : oy + (r - N);          // N rows before, then the rows after
       }
       const bool needx = j >= 0 && j < oy && (i >= 0 || hxl) && i >= -N;
@@ -152,7 +163,7 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
 
   // ---- each owned node: x part + y part from the flux tiles
   for (int idx = tid; idx < ox * oy; idx += nthr) {
-    const int i = idx % ox, j = idx / ox;
+    const int j = small_div(idx, ox, rox), i = idx - j * ox;
     const long long I = zoff + (x0 + i) + (long long)nx * (y0 + j);
     const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
     const int sy = min(j / N, eky - 1), ay = j - sy * N;
