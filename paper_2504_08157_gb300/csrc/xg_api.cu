@@ -186,7 +186,7 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
   prof_mark(c, 0, false, st);
   xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
   prof_mark(c, 0, true, st);
-  constexpr int K = xg::tile_segments(N);
+  constexpr int K = xg::df_tile_segments(N);
   const dim3 blk(xg::kTileCols, K * N + 1);
   const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
   dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
@@ -207,7 +207,7 @@ void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
   prof_mark(c, 0, false, st);
   xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
   prof_mark(c, 0, true, st);
-  constexpr int K = xg::tile_segments(N);
+  constexpr int K = xg::f32_tile_segments(N);
   const dim3 blk(xg::kTileCols, K * N + 1);
   const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
   dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);

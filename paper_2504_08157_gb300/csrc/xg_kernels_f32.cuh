@@ -330,10 +330,16 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   }
 }
 
+// The single-context z tiles hold at most 9 planes: 4 CTAs of 288 threads
+// per SM (measured: 0.297 vs 0.338 ms per launch on the 128x128x16 order-4
+// box against 17-plane tiles).
+__host__ __device__ constexpr int f32_tile_segments(int N) { return N >= 8 ? 1 : 8 / N; }
+
 template <int N, int DIR>
-__global__ void __launch_bounds__(kTileCols * (16 + 1)) k_f_tline(const FParams P, const FBufs B) {
-  __shared__ float Fs[5 * (tile_segments(N) * N + N + 1) * kTileCols];
-  f_tline_tile<N, DIR, false>(P, B, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, Fs);
+__global__ void __launch_bounds__(kTileCols * (8 + 1), 4) k_f_tline(const FParams P, const FBufs B) {
+  constexpr int K = f32_tile_segments(N);
+  __shared__ float Fs[5 * (K * N + N + 1) * kTileCols];
+  f_tline_tile<N, DIR, false, K>(P, B, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, Fs);
 }
 
 // FP64 <-> FP32 conversion of n values (data entering or leaving).
