@@ -126,15 +126,18 @@ xg_status xg_set_forcing(xg_ctx* ctx, const double* S_theta, int where, void* st
 
 /* Eq. 12 for the current state: dqdt [5][Np] = M^-1 DSS(w J S(q)) with the
  * wall condition (the wall-normal momentum tendency is zero at wall nodes).
- * Does not modify the state.  With XG_HOST the call waits for the copy.
- * Errors: XG_ERR_ARG (NULL, no state yet), XG_ERR_CUDA. */
+ * Does not modify the state.  With XG_HOST the call waits for the copy;
+ * with the closure of xg_closure.h on it always waits.
+ * Errors: XG_ERR_ARG (NULL, no state yet), XG_ERR_TIMEOUT (the closure
+ * kernel's bounded tensor-core wait ran out), XG_ERR_CUDA. */
 xg_status xg_rhs(xg_ctx* ctx, double* dqdt, int where, void* stream);
 
 /* nsteps SSP-RK3 steps of size dt (each step three fused stage passes:
  * q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
  * q <- 1/3 q + 2/3 (q2 + dt L(q2))).  Waits for the GPU once at the end to
  * read the non-finite flag.  Errors: XG_ERR_ARG (dt not finite, nsteps < 0,
- * no state yet), XG_ERR_NONFINITE, XG_ERR_CUDA. */
+ * no state yet), XG_ERR_NONFINITE, XG_ERR_TIMEOUT (the closure kernel's
+ * bounded tensor-core wait ran out), XG_ERR_CUDA. */
 xg_status xg_step(xg_ctx* ctx, double dt, int nsteps, void* stream);
 
 /* Copy the current state to q [5][Np], on `stream` (XG_HOST waits for it).

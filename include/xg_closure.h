@@ -22,7 +22,8 @@
  * Inference (xg_mlp_forward with XG_MLP_BF16, and the closure inside
  * xg_rhs / xg_step) rounds the weights, the normalised features and the
  * hidden activations to bfloat16 and multiplies them on the tensor cores
- * with FP32 accumulation; biases, SiLU and the output scaling are FP32.
+ * (tcgen05.mma, FP32 accumulation in tensor memory); biases, SiLU and the
+ * output scaling are FP32.
  *
  * Arrays: feature and target sets are structure of arrays with a leading
  * dimension: X [21][ld] holds sample s of feature f at X[f * ld + s];
@@ -87,8 +88,9 @@ xg_status xg_mlp_adam(float* params, float* m, float* v, const float* grad, int 
 
 /* The correction out_scale * MLP(clamp((X - in_mean) * in_scale)) for n samples
  * into Y [5][ldy]: XG_MLP_FP32 (the training arithmetic) or XG_MLP_BF16
- * (the inference arithmetic, tensor cores).  Errors: XG_ERR_ARG,
- * XG_ERR_CUDA. */
+ * (the inference arithmetic, tensor cores).  Waits for the GPU.  Errors:
+ * XG_ERR_ARG, XG_ERR_TIMEOUT (a bounded wait for the tensor cores ran out),
+ * XG_ERR_OOM, XG_ERR_CUDA. */
 xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long long n,
                          const float* in_mean, const float* in_scale, const float* out_scale,
                          float* Y, long long ldy, int precision, void* stream);

@@ -566,6 +566,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
+  if (c->closure) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
   if (!c->dfm && !c->f32) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
   } else {
@@ -575,6 +576,12 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (where == XG_HOST) {
     XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
                                cudaMemcpyDeviceToHost, st));
+  }
+  if (c->closure) {   // reports the closure kernel's timeout (bit 1 of the flag); waits
+    XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XG_CUDA(c, cudaStreamSynchronize(st));
+    prof_fold(c);
+    return (*c->hflag & 2) ? XG_ERR_TIMEOUT : XG_OK;
   }
   if (where == XG_HOST || c->profiling) {
     XG_CUDA(c, cudaStreamSynchronize(st));
@@ -601,6 +608,7 @@ xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   XG_CUDA(c, cudaStreamSynchronize(st));
   prof_fold(c);
+  if (*c->hflag & 2) return XG_ERR_TIMEOUT;   // the closure kernel's bounded wait ran out
   return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
 }
 

@@ -10,12 +10,12 @@
 //     thread so the sums are deterministic), the fixed-order reduction of
 //     the block partials (k_mlp_reduce), Adam (k_adam), column statistics
 //     (k_col_stats);
-//   * inference on the tensor cores (mma m16n8k16, bfloat16 inputs, FP32
-//     accumulation): 16-node row tiles per warp; the first layer's
-//     accumulators, after bias and SiLU, are repacked in registers as the
-//     second layer's A fragments (and likewise into the third), so hidden
-//     activations never leave the registers.  k_closure computes the
-//     features of 128 nodes per CTA straight from the state and runs the
+//   * inference on the fifth-generation tensor cores (tcgen05.mma, bfloat16
+//     operands in shared memory, FP32 accumulators in TMEM): persistent CTAs
+//     of 128 threads take 128 samples per tile, one row of every product per
+//     thread; bias, SiLU and the bfloat16 rounding of the hidden activations
+//     run on the CUDA cores between the layers.  k_closure computes the
+//     features of each tile's nodes straight from the state and runs the
 //     network on them; k_mlp_bf16 runs it on given features.
 #include <algorithm>
 #include <cmath>
@@ -31,6 +31,7 @@
 #include "../../include/xg_closure.h"
 #include "xg_ctx.h"
 #include "xg_setup.h"
+#include "xg_tc.cuh"
 
 namespace xg {
 
@@ -384,18 +385,36 @@ __global__ void k_mlp_fp32(const float* __restrict__ params, const float* __rest
   }
 }
 
-// ------------------------------------------------------------------ inference (tensor cores)
+// ------------------------------------------------------------------ inference (tcgen05)
+//
+// Inference runs on the fifth-generation tensor cores.  A persistent CTA of
+// 128 threads takes 128 samples at a time: they are the M = 128 rows of every
+// product, one row per thread and per TMEM lane.  Per tile:
+//   features -> A (bfloat16, shared memory)              all threads
+//   D = A W1h^T   (K 32, N 64)                           one thread issues tcgen05.mma
+//   A <- bf16(SiLU(2 (D + b1/2)))                        all threads: tcgen05.ld, FP32
+//   D = A W2h^T   (K 64, N 64)
+//   A <- bf16(SiLU(2 (D + b2/2)))
+//   D = A W3^T    (K 64, N 16; outputs 5..15 are zero rows of W3)
+//   y = (D + b3) * out_scale                             all threads, coalesced stores
+// W1h and W2h are the bfloat16 weights halved (exact), so the accumulator
+// holds h = z / 2 and SiLU(z) = h + h tanh(h) needs no further scaling.  The
+// accumulator takes 64 TMEM columns; shared memory (31.5 KB per CTA) lets at
+// most 7 CTAs share an SM (448 of its 512 columns), the launch bound 4.
+constexpr int kTcRows = 128;             // samples per tile, the MMA's M
+constexpr int kK1 = 32;                  // layer-1 K: 21 features, zero padded
+constexpr int kN3 = 16;                  // layer-3 N: 5 outputs, zero padded
+constexpr int kTcCols = 64;              // TMEM columns per CTA
+constexpr unsigned long long kTcWaitNs = 1000000000ull;   // 1 s per wait
 
 // Packed inference constants (one device blob, copied to shared memory):
-// bfloat16 W1 [64][40] (inputs 21..39 zero), W2 [64][72], W3 [8][72]
-// (outputs 5..7 and columns 64..71 zero), then FP32 b1 [64], b2 [64],
-// b3 [8], in_mean [24], in_scale [24], out_scale [8].
-constexpr int kLd1 = 40, kLd2 = 72;
+// the bfloat16 weights in the canonical K-major layout (tc::kmajor), then
+// FP32 b1/2, b2/2, b3, in_mean, in_scale, out_scale.
 struct InferPack {
-  __nv_bfloat16 W1[kHid * kLd1];
-  __nv_bfloat16 W2[kHid * kLd2];
-  __nv_bfloat16 W3[8 * kLd2];
-  float b1[kHid], b2[kHid], b3[8];
+  __nv_bfloat16 W1[kHid * kK1];
+  __nv_bfloat16 W2[kHid * kHid];
+  __nv_bfloat16 W3[kN3 * kHid];
+  float hb1[kHid], hb2[kHid], b3[8];
   float mean[24], scale[24], oscale[8];
 };
 static_assert(sizeof(InferPack) % 16 == 0, "InferPack is copied as int4");
@@ -403,21 +422,21 @@ static_assert(sizeof(InferPack) % 16 == 0, "InferPack is copied as int4");
 __global__ void k_pack(const float* __restrict__ p, const float* __restrict__ mean,
                        const float* __restrict__ scale, const float* __restrict__ oscale,
                        InferPack* __restrict__ out) {
-  for (int k = threadIdx.x; k < kHid * kLd1; k += blockDim.x) {
-    const int o = k / kLd1, i = k % kLd1;
-    out->W1[k] = __float2bfloat16_rn(i < kIn ? p[kOffW1 + o * kIn + i] : 0.0f);
+  for (int k = threadIdx.x; k < kHid * kK1; k += blockDim.x) {
+    const int o = k / kK1, i = k % kK1;
+    out->W1[tc::kmajor(kHid, o, i)] = __float2bfloat16_rn(i < kIn ? 0.5f * p[kOffW1 + o * kIn + i] : 0.0f);
   }
-  for (int k = threadIdx.x; k < kHid * kLd2; k += blockDim.x) {
-    const int o = k / kLd2, i = k % kLd2;
-    out->W2[k] = __float2bfloat16_rn(i < kHid ? p[kOffW2 + o * kHid + i] : 0.0f);
+  for (int k = threadIdx.x; k < kHid * kHid; k += blockDim.x) {
+    const int o = k / kHid, i = k % kHid;
+    out->W2[tc::kmajor(kHid, o, i)] = __float2bfloat16_rn(0.5f * p[kOffW2 + o * kHid + i]);
   }
-  for (int k = threadIdx.x; k < 8 * kLd2; k += blockDim.x) {
-    const int o = k / kLd2, i = k % kLd2;
-    out->W3[k] = __float2bfloat16_rn(o < kOut && i < kHid ? p[kOffW3 + o * kHid + i] : 0.0f);
+  for (int k = threadIdx.x; k < kN3 * kHid; k += blockDim.x) {
+    const int o = k / kHid, i = k % kHid;
+    out->W3[tc::kmajor(kN3, o, i)] = __float2bfloat16_rn(o < kOut ? p[kOffW3 + o * kHid + i] : 0.0f);
   }
   for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
-    out->b1[k] = p[kOffB1 + k];
-    out->b2[k] = p[kOffB2 + k];
+    out->hb1[k] = 0.5f * p[kOffB1 + k];
+    out->hb2[k] = 0.5f * p[kOffB2 + k];
   }
   for (int k = threadIdx.x; k < 24; k += blockDim.x) {
     out->mean[k] = k < kIn ? mean[k] : 0.0f;
@@ -429,102 +448,24 @@ __global__ void k_pack(const float* __restrict__ p, const float* __restrict__ me
   }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// SiLU for inference: z sigma(z) = (z/2)(1 + tanh(z/2)) with the hardware
-// tanh approximation (relative error ~2^-11), below the bfloat16 rounding
-// that follows it.
-__device__ __forceinline__ float silu_fast(float z) {
-  const float h = 0.5f * z;
+// SiLU(2h) = h (1 + tanh h) with the hardware tanh approximation (relative
+// error ~2^-11), below the bfloat16 rounding that follows it.
+__device__ __forceinline__ float silu_of_half(float h) {
   float t;
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
   return fmaf(h, t, h);
 }
 
-// One 16-row tile: A rows in shared memory (bfloat16, row stride kLd1),
-// outputs y[2][2] for rows g and g + 8, columns 2c and 2c + 1 (lane = 4 g + c).
-__device__ __forceinline__ void mlp_tile(const InferPack& K, const __nv_bfloat16* A, float (&y)[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
-  uint32_t a[2][4];
-#pragma unroll
-  for (int kt = 0; kt < 2; ++kt) {
-    a[kt][0] = A32[(g * kLd1 + 16 * kt + 2 * c) / 2];
-    a[kt][1] = A32[((g + 8) * kLd1 + 16 * kt + 2 * c) / 2];
-    a[kt][2] = A32[(g * kLd1 + 16 * kt + 2 * c + 8) / 2];
-    a[kt][3] = A32[((g + 8) * kLd1 + 16 * kt + 2 * c + 8) / 2];
-  }
-  const uint32_t* W1 = reinterpret_cast<const uint32_t*>(K.W1);
-  const uint32_t* W2 = reinterpret_cast<const uint32_t*>(K.W2);
-  const uint32_t* W3 = reinterpret_cast<const uint32_t*>(K.W3);
-  uint32_t h[4][4];   // A fragments of the next layer (k-tiles of 16)
-  {
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float bl = K.b1[8 * j + 2 * c], bh = K.b1[8 * j + 2 * c + 1];
-      acc[j][0] = bl; acc[j][1] = bh; acc[j][2] = bl; acc[j][3] = bh;
-#pragma unroll
-      for (int kt = 0; kt < 2; ++kt) {
-        const int row = 8 * j + g;
-        mma_bf16(acc[j], a[kt][0], a[kt][1], a[kt][2], a[kt][3], W1[(row * kLd1 + 16 * kt + 2 * c) / 2],
-                 W1[(row * kLd1 + 16 * kt + 2 * c + 8) / 2]);
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      h[kk][0] = pack_bf16(silu_fast(acc[2 * kk][0]), silu_fast(acc[2 * kk][1]));
-      h[kk][1] = pack_bf16(silu_fast(acc[2 * kk][2]), silu_fast(acc[2 * kk][3]));
-      h[kk][2] = pack_bf16(silu_fast(acc[2 * kk + 1][0]), silu_fast(acc[2 * kk + 1][1]));
-      h[kk][3] = pack_bf16(silu_fast(acc[2 * kk + 1][2]), silu_fast(acc[2 * kk + 1][3]));
-    }
-  }
-  {
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float bl = K.b2[8 * j + 2 * c], bh = K.b2[8 * j + 2 * c + 1];
-      acc[j][0] = bl; acc[j][1] = bh; acc[j][2] = bl; acc[j][3] = bh;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const int row = 8 * j + g;
-        mma_bf16(acc[j], h[kk][0], h[kk][1], h[kk][2], h[kk][3], W2[(row * kLd2 + 16 * kk + 2 * c) / 2],
-                 W2[(row * kLd2 + 16 * kk + 2 * c + 8) / 2]);
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      h[kk][0] = pack_bf16(silu_fast(acc[2 * kk][0]), silu_fast(acc[2 * kk][1]));
-      h[kk][1] = pack_bf16(silu_fast(acc[2 * kk][2]), silu_fast(acc[2 * kk][3]));
-      h[kk][2] = pack_bf16(silu_fast(acc[2 * kk + 1][0]), silu_fast(acc[2 * kk + 1][1]));
-      h[kk][3] = pack_bf16(silu_fast(acc[2 * kk + 1][2]), silu_fast(acc[2 * kk + 1][3]));
-    }
-  }
-  const float bl = K.b3[2 * c], bh = K.b3[2 * c + 1];
-  y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk)
-    mma_bf16(y, h[kk][0], h[kk][1], h[kk][2], h[kk][3], W3[(g * kLd2 + 16 * kk + 2 * c) / 2],
-             W3[(g * kLd2 + 16 * kk + 2 * c + 8) / 2]);
-}
-
-constexpr int kInferThreads = 128;   // 4 warps x 2 row tiles of 16 = 128 samples per CTA
-
-struct InferSmem {
+struct TcSmem {
   InferPack K;
-  __nv_bfloat16 A[kInferThreads * kLd1];
+  __nv_bfloat16 A[kTcRows * kHid];   // features (first 4 K-chunks) or hidden activations
+  unsigned long long bar;            // mbarrier: MMA completion
+  uint32_t tmem;                     // TMEM base address
 };
 
 __device__ __forceinline__ void load_pack(InferPack& dst, const InferPack* src) {
@@ -533,81 +474,142 @@ __device__ __forceinline__ void load_pack(InferPack& dst, const InferPack* src) 
   for (int k = threadIdx.x; k < (int)(sizeof(InferPack) / 16); k += blockDim.x) d[k] = s[k];
 }
 
-// the normalised features of this thread's sample as bfloat16 row of A
-__device__ __forceinline__ void store_row(InferSmem& S, const float (&x)[kIn]) {
-  __nv_bfloat16* row = S.A + threadIdx.x * kLd1;
+// One layer's products: makes this thread's writes of A visible to the
+// tensor cores, synchronises the CTA, issues the K/16 MMAs from thread 0 and
+// waits for them.  False (on every thread) when a wait ran out; the kernel
+// then reports XG_ERR_TIMEOUT through the flag and stops.
+__device__ __forceinline__ bool tc_layer(TcSmem& S, uint32_t w_addr, uint32_t w_lbo, int ksteps,
+                                         uint32_t idesc, uint32_t& phase) {
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t bar = tc::smem_addr(&S.bar);
+  if (threadIdx.x == 0) {
+    const uint32_t a_addr = tc::smem_addr(S.A);
+    constexpr uint32_t a_lbo = kTcRows * 16;
+    for (int k = 0; k < ksteps; ++k) {
+      tc::mma_bf16(S.tmem, tc::smem_desc(a_addr + 2 * k * a_lbo, a_lbo, 128),
+                   tc::smem_desc(w_addr + 2 * k * w_lbo, w_lbo, 128), idesc, k > 0);
+    }
+    tc::commit(bar);
+  }
+  const bool ok = tc::mbar_wait(bar, phase, kTcWaitNs);
+  phase ^= 1u;
+  const int bad = __syncthreads_or(!ok);
+  tc::fence_after_sync();
+  return !bad;
+}
+
+// The hidden layer's epilogue: this thread's row of D (64 columns) plus the
+// halved bias, SiLU, bfloat16 into its row of A.
+__device__ __forceinline__ void tc_hidden(TcSmem& S, uint32_t lane_addr, const float* hb) {
+  char* A = reinterpret_cast<char*>(S.A);
 #pragma unroll
-  for (int f = 0; f < 32; f += 2) {
-    const float lo = f < kIn ? norm_in(x[f], S.K.mean[f], S.K.scale[f]) : 0.0f;
-    const float hi = f + 1 < kIn ? norm_in(x[f + 1], S.K.mean[f + 1], S.K.scale[f + 1]) : 0.0f;
-    *reinterpret_cast<__nv_bfloat162*>(row + f) = __floats2bfloat162_rn(lo, hi);
+  for (int c0 = 0; c0 < kHid; c0 += 16) {
+    uint32_t r[16];
+    tc::tmem_ld16(lane_addr + c0, r);
+    tc::tmem_wait_ld();
+    uint32_t pk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      pk[j] = pack_bf16(silu_of_half(__uint_as_float(r[2 * j]) + hb[c0 + 2 * j]),
+                        silu_of_half(__uint_as_float(r[2 * j + 1]) + hb[c0 + 2 * j + 1]));
+    const int off = (c0 >> 3) * (kTcRows * 16) + threadIdx.x * 16;
+    *reinterpret_cast<uint4*>(A + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(A + off + kTcRows * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
   }
 }
 
-// the network on the CTA's 128 rows; writes out_scale * y to Y[o * ldy + s0 + row]
-__device__ __forceinline__ void run_rows(const InferSmem& S, float* __restrict__ Y, long long ldy,
-                                         long long s0, long long n) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-#pragma unroll 1
-  for (int t = 0; t < 2; ++t) {
-    const int r0 = 32 * warp + 16 * t;
-    float y[4];
-    mlp_tile(S.K, S.A + r0 * kLd1, y);
+// The persistent inference loop over the tiles of n samples: feat(s, emit)
+// hands the raw features f = 0..20 of sample s < n to emit(f, value);
+// Y[o * ldy + s] = out_scale_o * y_o.  On a wait that runs out, sets bit 1
+// (value 2) of *flag and returns after freeing its TMEM.  blockDim.x = kTcRows.
+template <typename Feat>
+__device__ __forceinline__ void tc_infer(TcSmem& S, const InferPack* __restrict__ pack, long long n,
+                                         float* __restrict__ Y, long long ldy, int* flag, Feat feat) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  load_pack(S.K, pack);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long s = s0 + r0 + g + 8 * h;
-      if (s >= n) continue;
+  for (int k = kIn; k < kK1; ++k) S.A[tc::kmajor(kTcRows, tid, k)] = __float2bfloat16_rn(0.0f);
+  if (tid == 0) tc::mbar_init(tc::smem_addr(&S.bar), 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&S.tmem), kTcCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t lane_addr = S.tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t w1 = tc::smem_addr(S.K.W1), w2 = tc::smem_addr(S.K.W2), w3 = tc::smem_addr(S.K.W3);
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long ntiles = (n + kTcRows - 1) / kTcRows;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long long s = t * kTcRows + tid;
+    if (s < n) {
+      feat(s, [&](int f, float v) {
+        S.A[tc::kmajor(kTcRows, tid, f)] = __float2bfloat16_rn(norm_in(v, S.K.mean[f], S.K.scale[f]));
+      });
+    } else {
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int o = 2 * c + e;
-        if (o < kOut) Y[o * ldy + s] = y[2 * h + e] * S.K.oscale[o];
-      }
+      for (int f = 0; f < kIn; ++f) S.A[tc::kmajor(kTcRows, tid, f)] = __float2bfloat16_rn(0.0f);
+    }
+    ok = tc_layer(S, w1, kHid * 16, kK1 / 16, tc::idesc_bf16(kTcRows, kHid), phase);
+    if (!ok) break;
+    tc_hidden(S, lane_addr, S.K.hb1);
+    ok = tc_layer(S, w2, kHid * 16, kHid / 16, tc::idesc_bf16(kTcRows, kHid), phase);
+    if (!ok) break;
+    tc_hidden(S, lane_addr, S.K.hb2);
+    ok = tc_layer(S, w3, kN3 * 16, kHid / 16, tc::idesc_bf16(kTcRows, kN3), phase);
+    if (!ok) break;
+    uint32_t r[8];
+    tc::tmem_ld8(lane_addr, r);
+    tc::tmem_wait_ld();
+    if (s < n) {
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) Y[o * ldy + s] = (__uint_as_float(r[o]) + S.K.b3[o]) * S.K.oscale[o];
     }
   }
-}
-
-__global__ void __launch_bounds__(kInferThreads) k_mlp_bf16(const InferPack* __restrict__ pack,
-                                                           const float* __restrict__ X, long long ld,
-                                                           long long n, float* __restrict__ Y, long long ldy) {
-  __shared__ __align__(16) InferSmem S;
-  load_pack(S.K, pack);
+  if (!ok && tid == 0) atomicOr(flag, 2);
+  tc::fence_before_sync();
   __syncthreads();
-  const long long s0 = blockIdx.x * (long long)kInferThreads;
-  const long long s = s0 + threadIdx.x;
-  float x[kIn];
-#pragma unroll
-  for (int f = 0; f < kIn; ++f) x[f] = s < n ? X[f * ld + s] : S.K.mean[f];
-  store_row(S, x);
-  __syncthreads();
-  run_rows(S, Y, ldy, s0, n);
-}
-
-// Features of 128 consecutive nodes, straight from the state, normalised
-// into the bfloat16 rows of A as they are computed; then the network: the
-// closure correction C [5][np].
-template <int N>
-__global__ void __launch_bounds__(kInferThreads, 4) k_closure(const FParams P, const InferPack* __restrict__ pack,
-                                                             const float* __restrict__ q,
-                                                             const float* __restrict__ Sth,
-                                                             float* __restrict__ C) {
-  __shared__ __align__(16) InferSmem S;
-  load_pack(S.K, pack);
-  __syncthreads();
-  const long long s0 = blockIdx.x * (long long)kInferThreads;
-  const long long I = s0 + threadIdx.x;
-  __nv_bfloat16* row = S.A + threadIdx.x * kLd1;
-#pragma unroll
-  for (int f = kIn; f < 32; ++f) row[f] = __float2bfloat16_rn(0.0f);
-  if (I < P.np) {
-    node_features<N>(P, q, Sth, I, [&](int f, float v) {
-      row[f] = __float2bfloat16_rn(norm_in(v, S.K.mean[f], S.K.scale[f]));
-    });
-  } else {
-#pragma unroll
-    for (int f = 0; f < kIn; ++f) row[f] = __float2bfloat16_rn(0.0f);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(S.tmem, kTcCols);
   }
-  __syncthreads();
-  run_rows(S, C, P.np, s0, P.np);
+}
+
+constexpr int kTcCtasPerSm = 4;
+
+__global__ void __launch_bounds__(kTcRows, kTcCtasPerSm)
+    k_mlp_bf16(const InferPack* __restrict__ pack, const float* __restrict__ X, long long ld, long long n,
+               float* __restrict__ Y, long long ldy, int* flag) {
+  __shared__ __align__(128) TcSmem S;
+  tc_infer(S, pack, n, Y, ldy, flag, [&](long long s, auto&& emit) {
+#pragma unroll
+    for (int f = 0; f < kIn; ++f) emit(f, X[f * ld + s]);
+  });
+}
+
+// The closure correction C [5][np]: the features of each tile's 128 nodes
+// straight from the state, then the network.
+template <int N>
+__global__ void __launch_bounds__(kTcRows, kTcCtasPerSm)
+    k_closure(const FParams P, const InferPack* __restrict__ pack, const float* __restrict__ q,
+              const float* __restrict__ Sth, float* __restrict__ C, int* flag) {
+  __shared__ __align__(128) TcSmem S;
+  tc_infer(S, pack, P.np, C, P.np, flag,
+           [&](long long I, auto&& emit) { node_features<N>(P, q, Sth, I, emit); });
+}
+
+// Persistent grid: kTcCtasPerSm CTAs per SM, at most one per tile.  (The
+// occupancy calculator reports one CTA per SM for these kernels, although
+// their registers and shared memory admit kTcCtasPerSm, and the hardware
+// does co-schedule them; the grid is therefore sized from the launch bound.)
+inline int tc_grid(long long n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (n + kTcRows - 1) / kTcRows;
+  return (int)std::max(1LL, std::min(tiles, (long long)kTcCtasPerSm * std::max(sms, 1)));
 }
 
 }  // namespace xg
@@ -619,18 +621,20 @@ using xg::InferPack;
 // Called by the FP32 stage before its passes when the closure is on:
 // C = correction of the stage's input state.
 cudaError_t closure_launch(xg_ctx* c, const float* q, cudaStream_t st) {
-  const unsigned blocks = (unsigned)((c->np + xg::kInferThreads - 1) / xg::kInferThreads);
   const float* S = c->has_forcing ? (const float*)c->S : nullptr;
   const InferPack* K = (const InferPack*)c->cl_pack;
+  const long long np = c->np;
   switch (c->d.order) {
-    case 1: xg::k_closure<1><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 2: xg::k_closure<2><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 3: xg::k_closure<3><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 4: xg::k_closure<4><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 5: xg::k_closure<5><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 6: xg::k_closure<6><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 7: xg::k_closure<7><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
-    case 8: xg::k_closure<8><<<blocks, xg::kInferThreads, 0, st>>>(c->Pf, K, q, S, c->cl_C); break;
+#define XG_CLOSURE_CASE(n)                                                                              \
+  case n: {                                                                                             \
+    if (!c->cl_grid) c->cl_grid = xg::tc_grid(np);                                                      \
+    const unsigned g = (unsigned)c->cl_grid;                                                            \
+    xg::k_closure<n><<<g, xg::kTcRows, 0, st>>>(c->Pf, K, q, S, c->cl_C, c->flag);                       \
+    break;                                                                                              \
+  }
+    XG_CLOSURE_CASE(1) XG_CLOSURE_CASE(2) XG_CLOSURE_CASE(3) XG_CLOSURE_CASE(4)
+    XG_CLOSURE_CASE(5) XG_CLOSURE_CASE(6) XG_CLOSURE_CASE(7) XG_CLOSURE_CASE(8)
+#undef XG_CLOSURE_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -858,16 +862,24 @@ xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long
                                                                  out_scale, Y, ldy);
     return cuda_status(cudaGetLastError(), "xg_mlp_forward");
   }
-  InferPack* K = nullptr;
-  cudaError_t e = cudaMalloc((void**)&K, sizeof(InferPack));
+  // the packed network, then the timeout flag
+  char* blob = nullptr;
+  cudaError_t e = cudaMalloc((void**)&blob, sizeof(InferPack) + 16);
+  int hflag = 0;
   if (e == cudaSuccess) {
-    xg::k_pack<<<1, 256, 0, st>>>(params, in_mean, in_scale, out_scale, K);
-    xg::k_mlp_bf16<<<(unsigned)((n + xg::kInferThreads - 1) / xg::kInferThreads), xg::kInferThreads, 0, st>>>(
-        K, X, ld, n, Y, ldy);
-    e = cudaGetLastError();
+    InferPack* K = (InferPack*)blob;
+    int* flag = (int*)(blob + sizeof(InferPack));
+    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+      xg::k_pack<<<1, 256, 0, st>>>(params, in_mean, in_scale, out_scale, K);
+      xg::k_mlp_bf16<<<xg::tc_grid(n), xg::kTcRows, 0, st>>>(K, X, ld, n, Y, ldy, flag);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
-  cudaFree(K);
+  cudaFree(blob);
+  if (e == cudaSuccess && hflag) return XG_ERR_TIMEOUT;
   return cuda_status(e, "xg_mlp_forward");
 }
 

@@ -54,6 +54,7 @@ struct xg_ctx {
   bool closure = false;
   void* cl_pack = nullptr;
   float* cl_C = nullptr;
+  int cl_grid = 0;       // persistent grid of the closure kernel
   // hyper-diffusion and sponge (XG_FP64 only): line-operator constants,
   // work arrays and the extra tendency E of the current stage
   bool dyn = false, dyn_hyper = false;

@@ -326,7 +326,7 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
     bool bad = false;
     const df r0 = B.base[g];
     f_finish_vals(P, B, qv, qnv, sv, r0.h, B.out, I, x, other, g, t, bad, cv);
-    if (bad) *B.flag = 1;
+    if (bad) atomicOr(B.flag, 1);   // bit 0; the closure kernel reports a timeout in bit 1
   }
 }
 

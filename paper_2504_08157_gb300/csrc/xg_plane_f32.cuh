@@ -49,29 +49,39 @@ struct PlaneLayoutF {
   static constexpr size_t bytes = sizeof(float) * (size_t)total;
 };
 
-// One tile (bx, by) of level z, run by threads tid = 0 .. nthr-1 of the
-// block; sm holds PlaneLayoutF<N, E>::bytes.  CG: L2-only loads of q (see
-// ldf).  The block synchronises once, between the pointwise and the
-// contraction phases; the caller synchronises before reusing sm.
-template <int N, int E, int BATCH, bool CG>
-__device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, int bx, int by, int z,
-                                             float* sm_plane, int tid, int nthr) {
-  using L = PlaneLayoutF<N, E>;
-  constexpr int LO = L::LO, LX = L::LX;
-  float* FX = sm_plane;                   // [c][j][i + N]
-  float* FY = FX + L::FX;                 // [c][j + N][i]
-  auto fx = [&](int c, int j, int ii) -> float& { return FX[(c * LO + j) * LX + ii]; };
-  auto fy = [&](int c, int jj, int i) -> float& { return FY[(c * LX + jj) * LO + i]; };
+// Extent of tile (bx, by): its first element and node along x and y, the
+// elements it owns, the owned node extents ox, oy (the wall node of a
+// walled end included) and whether the segment before each direction's
+// first node exists (interior tile, or periodic).
+struct PlaneTile {
+  int ekx, eky, x0, y0, ox, oy;
+  bool wallx, wally, hxl, hyl;
+  template <int N, int E>
+  __device__ __forceinline__ void init(const FParams& P, int bx, int by) {
+    const int ex0 = bx * E, ey0 = by * E;
+    ekx = min(E, P.nseg[0] - ex0);
+    eky = min(E, P.nseg[1] - ey0);
+    x0 = ex0 * N;
+    y0 = ey0 * N;
+    wallx = !P.per[0] && ex0 + ekx == P.nseg[0];
+    wally = !P.per[1] && ey0 + eky == P.nseg[1];
+    ox = ekx * N + (wallx ? 1 : 0);
+    oy = eky * N + (wally ? 1 : 0);
+    hxl = ex0 > 0 || P.per[0];
+    hyl = ey0 > 0 || P.per[1];
+  }
+};
 
+// The pointwise phase of tile T of level z: the primitives of every node of
+// the cross-shaped region, W = (v, w, p') of the owned nodes, and the fluxes
+// handed to fxs(j, ii, F[5]) (x-fluxes of owned row j at ii = i + N) and
+// fys(jj, i, F[5]) (y-fluxes of owned column i at jj = j + N).
+template <int N, int BATCH, bool CG, typename StoreX, typename StoreY>
+__device__ __forceinline__ void f_plane_pointwise(const FParams& P, const FBufs& B, const PlaneTile& T, int z,
+                                                  int tid, int nthr, StoreX fxs, StoreY fys) {
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const int ex0 = bx * E, ey0 = by * E;
-  const int ekx = min(E, P.nseg[0] - ex0), eky = min(E, P.nseg[1] - ey0);
-  const int x0 = ex0 * N, y0 = ey0 * N;
-  const bool wallx = !P.per[0] && ex0 + ekx == P.nseg[0];
-  const bool wally = !P.per[1] && ey0 + eky == P.nseg[1];
-  const int ox = ekx * N + (wallx ? 1 : 0), oy = eky * N + (wally ? 1 : 0);
-  const bool hxl = ex0 > 0 || P.per[0];
-  const bool hyl = ey0 > 0 || P.per[1];
+  const int ekx = T.ekx, eky = T.eky, x0 = T.x0, y0 = T.y0, ox = T.ox, oy = T.oy;
+  const bool hxl = T.hxl, hyl = T.hyl;
   const long long np = P.np;
   const long long zoff = (long long)nx * ny * z;
   const df rho0d = B.base[z], Th0d = B.base[nz + z], p0 = B.base[2 * nz + z];
@@ -79,7 +89,6 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
   const float rho0 = rho0d.h + rho0d.l, Th0 = Th0d.h + Th0d.l;
   const float* __restrict__ q = B.q;
   float* __restrict__ Wo = B.W;
-  float* __restrict__ To = B.T;
 
   // ---- pointwise over the cross: local (i, j) with i in [-N, ekx N] and
   // j in [-N, eky N]; x-fluxes on owned rows (i extended by the segment
@@ -142,24 +151,52 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
         Wo[2 * np + I] = pp;
       }
       if (iny) {                                  // x-fluxes on owned rows
-        const int ii = i + N;
-        fx(0, j, ii) = mu;
-        fx(1, j, ii) = fmaf(mu, u_, pp);
-        fx(2, j, ii) = mv * u_;
-        fx(3, j, ii) = mw * u_;
-        fx(4, j, ii) = Th * u_;
+        const float F[5] = {mu, fmaf(mu, u_, pp), mv * u_, mw * u_, Th * u_};
+        fxs(j, i + N, F);
       }
       if (inx) {                                  // y-fluxes on owned columns
-        const int jj = j + N;
-        fy(0, jj, i) = mv;
-        fy(1, jj, i) = mu * v;
-        fy(2, jj, i) = fmaf(mv, v, pp);
-        fy(3, jj, i) = mw * v;
-        fy(4, jj, i) = Th * v;
+        const float F[5] = {mv, mu * v, fmaf(mv, v, pp), mw * v, Th * v};
+        fys(j + N, i, F);
       }
     }
   }
+}
+
+// One tile (bx, by) of level z, run by threads tid = 0 .. nthr-1 of the
+// block; sm holds PlaneLayoutF<N, E>::bytes.  CG: L2-only loads of q (see
+// ldf).  The block synchronises once, between the pointwise and the
+// contraction phases; the caller synchronises before reusing sm.
+template <int N, int E, int BATCH, bool CG>
+__device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, int bx, int by, int z,
+                                             float* sm_plane, int tid, int nthr) {
+  using L = PlaneLayoutF<N, E>;
+  constexpr int LO = L::LO, LX = L::LX;
+  float* FX = sm_plane;                   // [c][j][i + N]
+  float* FY = FX + L::FX;                 // [c][j + N][i]
+  auto fx = [&](int c, int j, int ii) -> float& { return FX[(c * LO + j) * LX + ii]; };
+  auto fy = [&](int c, int jj, int i) -> float& { return FY[(c * LX + jj) * LO + i]; };
+
+  PlaneTile T;
+  T.init<N, E>(P, bx, by);
+  f_plane_pointwise<N, BATCH, CG>(
+      P, B, T, z, tid, nthr,
+      [&](int j, int ii, const float (&F)[5]) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fx(c, j, ii) = F[c];
+      },
+      [&](int jj, int i, const float (&F)[5]) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fy(c, jj, i) = F[c];
+      });
   __syncthreads();
+
+  const int nx = P.n[0], ny = P.n[1];
+  const int ekx = T.ekx, eky = T.eky, x0 = T.x0, y0 = T.y0, ox = T.ox, oy = T.oy;
+  const bool hxl = T.hxl, hyl = T.hyl;
+  const long long np = P.np;
+  const long long zoff = (long long)nx * ny * z;
+  const float rox = 1.0f / (float)ox;
+  float* __restrict__ To = B.T;
 
   // ---- each owned node: x part + y part from the flux tiles
   for (int idx = tid; idx < ox * oy; idx += nthr) {

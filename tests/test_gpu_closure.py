@@ -128,7 +128,8 @@ def test_column_stats(cuda_device):
     assert np.allclose(std, x.std(axis=1), rtol=1e-10)
 
 
-@pytest.mark.parametrize("n", [1, 127, 1000])
+# 150,000 samples are 1,172 tiles of 128: more than one per persistent CTA
+@pytest.mark.parametrize("n", [1, 127, 1000, 150_000])
 def test_forward_fp32_and_bf16_match_oracle(cuda_device, n):
     import torch
     from paper_2504_08157_gb300 import xg
