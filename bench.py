@@ -47,7 +47,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", f)
                for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh", "xg_kernels_f32.cuh",
-                         "xg_plane_f32.cuh", "xg_batch.cu", "xg_closure.cu", "xg_tc.cuh")]
+                         "xg_plane_f32.cuh", "xg_batch.cu", "xg_closure.cu", "xg_tc.cuh", "xg_plane_tc.cuh")]
 KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 # the kernels behind the three timing slots in each precision (the FP32 form
 # fuses the x and y passes into one plane kernel; slot 1 stays empty)
@@ -247,15 +247,17 @@ def time_oracle(wl, min_seconds=10.0, max_steps=50):
     return dof_u * 3 * steps / dt / 1e9, steps, dt, q
 
 
-def oracle_error_of_gpu(wl, xg, torch, dev, precision):
+def oracle_error_of_gpu(wl, xg, torch, dev, precision, contract=0):
     """Relative L2 per variable between one GPU right-hand side and the
-    oracle's on the CPU sample."""
+    oracle's on the CPU sample (contract: the FP32 contraction arithmetic)."""
     from oracle import euler as E, mesh as M
     m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"])
     ref = E.rhs(m, wl["q"], E.Base(wl["rho0"], wl["Theta0"]), wl["S_theta"],
                 E.Physics(**wl["phys"]))
     ctx = make_ctx(xg, torch, wl, dev, precision)
     try:
+        if contract:
+            xg.xg_set_contraction(ctx, contract)
         out = torch.empty((5, xg.xg_mesh_np(ctx)), dtype=torch.float64, device=dev)
         xg.xg_rhs(ctx, out)
         got = out.cpu().numpy()
@@ -395,17 +397,23 @@ def run_xg(args, world, rank, local):
 
     # the other precisions on the same workload and GPU: plain FP64 (the
     # comparison the metric asks for) and the FP32 precision form
-    def side_run(p, dtype):
+    def side_run(p, dtype, contract=0):
         Kp = max(1, min(K, 10))
         c2 = make_ctx(xg, torch, wl, dev, p)
+        if contract:
+            xg.xg_set_contraction(c2, contract)
         msp, kmsp, klp, _ = timed_steps(xg, torch, c2, dt, Kp, 3, stream, world, local, False)
         xg.xg_destroy(c2)
         return {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": dtype,
                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
-                "kernel_ms_per_launch": {KERNEL_NAMES[p][i]: round(kmsp[i] / max(klp[i], 1), 4)
+                "kernel_ms_per_launch": {(("k_f_plane_xy_tc",) + KERNEL_NAMES[p][1:] if contract
+                                          else KERNEL_NAMES[p])[i]: round(kmsp[i] / max(klp[i], 1), 4)
                                          for i in range(3) if klp[i]}}
     plain = side_run(xg.XG_FP64, "f64") if prec != xg.XG_FP64 and not args.no_plain else None
     fp32 = side_run(xg.XG_FP32, "f32") if prec != xg.XG_FP32 and not args.no_plain else None
+    if fp32 is not None and wl["N"] == 4:
+        # the same form with the x and y contractions on the tensor cores
+        fp32["tf32x3_contraction"] = side_run(xg.XG_FP32, "f32", xg.XG_CONTRACT_TF32X3)
     batched = None
     if not args.no_plain and not args.no_batch:
         batched = batch_measure(xg, torch, dev, stream, world, local, max(1, min(K, 10)), 3,
@@ -424,6 +432,9 @@ def run_xg(args, world, rank, local):
         l2 = {"df64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_DF64),
               "fp64": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP64),
               "fp32": oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32),
+              "fp32_tf32x3_contraction": (oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32,
+                                                              xg.XG_CONTRACT_TF32X3)
+                                          if sw["N"] == 4 else None),
               "what": "relative L2 difference of one GPU right-hand side from the FP64 oracle "
                       "on the CPU sample, per variable (rho', rho u, rho v, rho w, Theta'); "
                       "at the vortex state the rho' and Theta' tendencies are residuals of "

@@ -152,6 +152,21 @@ xg_status xg_get_state(xg_ctx* ctx, double* q, int where, void* stream);
  * XG_ERR_CUDA. */
 xg_status xg_diagnostics(xg_ctx* ctx, double out[5], void* stream);
 
+/* Arithmetic of the x and y derivative contractions of an XG_FP32 context
+ * (Eqs. 8-12: the flux values of an element segment times the rows of the
+ * scaled derivative matrix).
+ *   XG_CONTRACT_FMA     FP32 fused multiply-adds on the CUDA cores (default)
+ *   XG_CONTRACT_TF32X3  the tensor cores (tcgen05.mma, TF32 operands, FP32
+ *                       accumulation in tensor memory), each flux and matrix
+ *                       entry split into a TF32 head and tail and three
+ *                       products summed (head*head + tail*head + head*tail);
+ *                       order 4 only
+ * The z contraction stays on the CUDA cores.  Errors: XG_ERR_ARG (NULL, an
+ * unknown mode), XG_ERR_UNSUPPORTED (XG_CONTRACT_TF32X3 on a context that
+ * is not XG_FP32 or not of order 4). */
+enum { XG_CONTRACT_FMA = 0, XG_CONTRACT_TF32X3 = 1 };
+xg_status xg_set_contraction(xg_ctx* ctx, int mode);
+
 /* Kernel timing (Sec. 5.4 measures its kernels against a roofline; this is
  * the hook for doing the same here).  enable = 1 brackets every kernel that
  * xg_rhs and xg_step launch with CUDA events on the launching stream; the

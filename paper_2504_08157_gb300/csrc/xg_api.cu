@@ -16,6 +16,7 @@
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
 #include "xg_kernels_df.cuh"
+#include "xg_plane_tc.cuh"
 #include "xg_setup.h"
 #include "xg_ctx.h"
 
@@ -177,6 +178,8 @@ cudaError_t configure_n(xg_ctx* c) {
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_df_line_x<N>, c->xsmem);
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_line_x<N>, c->xsmem / 2);
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_plane_xy<N>, xg::PlaneLayoutF<N>::bytes);
+  if (N == xg::PlaneTcLayout::N && e == cudaSuccess)
+    e = xg::raise_dynamic_smem(xg::k_f_plane_xy_tc, xg::PlaneTcLayout::bytes);
   return e;
 }
 
@@ -205,7 +208,12 @@ void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
   constexpr int E = xg::plane_elems_f32(N);
   dim3 gp((c->d.nel[0] + E - 1) / E, (c->d.nel[1] + E - 1) / E, c->n[2]);
   prof_mark(c, 0, false, st);
-  xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
+  if (N == xg::PlaneTcLayout::N && c->contract == XG_CONTRACT_TF32X3) {
+    static_assert(xg::plane_elems_f32(4) == xg::PlaneTcLayout::E, "same tiles");
+    xg::k_f_plane_xy_tc<<<gp, xg::kPlaneThreads, xg::PlaneTcLayout::bytes, st>>>(c->Pf, B);
+  } else {
+    xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
+  }
   prof_mark(c, 0, true, st);
   constexpr int K = xg::f32_tile_segments(N);
   const dim3 blk(xg::kTileCols, K * N + 1);
@@ -566,7 +574,8 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
-  if (c->closure) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+  const bool tc_waits = c->closure || c->contract != XG_CONTRACT_FMA;   // kernels with bounded waits
+  if (tc_waits) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
   if (!c->dfm && !c->f32) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
   } else {
@@ -577,7 +586,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
     XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
                                cudaMemcpyDeviceToHost, st));
   }
-  if (c->closure) {   // reports the closure kernel's timeout (bit 1 of the flag); waits
+  if (tc_waits) {   // reports a tensor-core wait that ran out (bit 1 of the flag); waits
     XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     XG_CUDA(c, cudaStreamSynchronize(st));
     prof_fold(c);
@@ -629,6 +638,15 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
     XG_CUDA(c, cudaMemcpyAsync(q, c->Bq, sizeof(double) * (size_t)n5, cudaMemcpyDeviceToHost, st));
   }
   if (where == XG_HOST) XG_CUDA(c, cudaStreamSynchronize(st));
+  return XG_OK;
+}
+
+xg_status xg_set_contraction(xg_ctx* c, int mode) {
+  if (!c) return XG_ERR_ARG;
+  if (mode != XG_CONTRACT_FMA && mode != XG_CONTRACT_TF32X3) return XG_ERR_ARG;
+  if (mode == XG_CONTRACT_TF32X3 && (!c->f32 || c->d.order != xg::PlaneTcLayout::N))
+    return XG_ERR_UNSUPPORTED;
+  c->contract = mode;
   return XG_OK;
 }
 

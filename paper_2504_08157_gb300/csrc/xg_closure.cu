@@ -405,7 +405,6 @@ constexpr int kTcRows = 128;             // samples per tile, the MMA's M
 constexpr int kK1 = 32;                  // layer-1 K: 21 features, zero padded
 constexpr int kN3 = 16;                  // layer-3 N: 5 outputs, zero padded
 constexpr int kTcCols = 64;              // TMEM columns per CTA
-constexpr unsigned long long kTcWaitNs = 1000000000ull;   // 1 s per wait
 
 // Packed inference constants (one device blob, copied to shared memory):
 // the bfloat16 weights in the canonical K-major layout (tc::kmajor), then
@@ -494,7 +493,7 @@ __device__ __forceinline__ bool tc_layer(TcSmem& S, uint32_t w_addr, uint32_t w_
     }
     tc::commit(bar);
   }
-  const bool ok = tc::mbar_wait(bar, phase, kTcWaitNs);
+  const bool ok = tc::mbar_wait(bar, phase, tc::kWaitNs);
   phase ^= 1u;
   const int bad = __syncthreads_or(!ok);
   tc::fence_after_sync();

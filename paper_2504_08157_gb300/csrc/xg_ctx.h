@@ -23,6 +23,7 @@ struct xg_ctx {
   xg::FParams Pf;        // launch constants of the FP32 kernels
   bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
   bool f32 = false;      // precision XG_FP32: device arrays hold floats
+  int contract = 0;      // XG_FP32: arithmetic of the x and y contractions (XG_CONTRACT_*)
   double* A = nullptr;   // q^n (the state)
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer

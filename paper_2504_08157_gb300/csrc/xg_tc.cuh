@@ -21,6 +21,9 @@
 namespace xg {
 namespace tc {
 
+// bound of every wait for the tensor cores (a completion takes microseconds)
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
 __host__ __device__ constexpr int kmajor(int R, int r, int k) {
   return (k >> 3) * (R * 8) + (r >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
@@ -45,6 +48,40 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | (1u << 10)                           // B format: BF16
          | ((uint32_t)(N >> 3) << 17)           // N / 8
          | ((uint32_t)(M >> 4) << 24);          // M / 16
+}
+
+// The same for 32-bit elements (TF32 operands): a core matrix row holds 4.
+__host__ __device__ constexpr int kmajor32(int R, int r, int k) {
+  return (k >> 2) * (R * 4) + (r >> 3) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// Instruction descriptor of kind::tf32: TF32 A and B (both K-major), FP32
+// accumulator, dense, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                              // D format: F32
+         | (2u << 7)                            // A format: TF32
+         | (2u << 10)                           // B format: TF32
+         | ((uint32_t)(N >> 3) << 17)           // N / 8
+         | ((uint32_t)(M >> 4) << 24);          // M / 16
+}
+
+// x rounded to the nearest TF32 value (10 explicit mantissa bits)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// D[tmem] (+)= A[adesc] * B[bdesc]^T with TF32 operands, issued by one thread
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
 }
 
 // D[tmem] (+)= A[adesc] * B[bdesc]^T, issued by one thread

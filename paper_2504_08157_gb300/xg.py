@@ -24,11 +24,12 @@ XG_HOST, XG_DEVICE = 0, 1
 XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
 XG_SCHED_ROUND_ROBIN, XG_SCHED_LPT, XG_SCHED_DYNAMIC = 0, 1, 2
 XG_MLP_FP32, XG_MLP_BF16 = 0, 1
+XG_CONTRACT_FMA, XG_CONTRACT_TF32X3 = 0, 1
 XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5, 5893
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library",
+           "xg_step", "xg_get_state", "xg_set_contraction", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library",
            "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
            "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
            "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
@@ -117,6 +118,8 @@ def library():
     lib.xg_step.argtypes = [P, D, I, P]
     lib.xg_get_state.restype = I
     lib.xg_get_state.argtypes = [P, P, I, P]
+    lib.xg_set_contraction.restype = I
+    lib.xg_set_contraction.argtypes = [P, I]
     lib.xg_profile.restype = I
     lib.xg_profile.argtypes = [P, I]
     lib.xg_kernel_times.restype = I
@@ -297,6 +300,10 @@ def xg_step(ctx, dt, nsteps, stream=None):
 def xg_get_state(ctx, q, where=None, stream=None):
     p, w, s = _ptr(q, where, writable=True)
     _check(library().xg_get_state(ctx, p, w, _stream(stream, s)), "xg_get_state")
+
+
+def xg_set_contraction(ctx, mode):
+    _check(library().xg_set_contraction(ctx, int(mode)), "xg_set_contraction")
 
 
 def xg_profile(ctx, enable):

@@ -123,3 +123,56 @@ def test_mass_conserved_on_gpu(cuda_device, prec, tol):
     m, _, base = oracle_of(wl)
     total = np.dot(E.mass(m), base.rho0[m.gidx[2]] + wl["q"][0])
     assert abs(after - before) <= tol * total, (before, after, total)
+
+
+# ------------------------------------------------------------------ tensor-core contractions
+
+TF32X3 = 1   # XG_CONTRACT_TF32X3
+
+
+@pytest.mark.parametrize("nel,periodic", [
+    ((1, 1, 1), (False, False, False)),
+    ((2, 2, 2), (True, True, True)),
+    ((3, 2, 5), (False, False, False)),
+    ((9, 10, 2), (True, False, False)),     # one full 8 x 8 element tile and ragged ones
+    ((17, 9, 2), (False, True, True)),
+])
+def test_fp32_tf32x3_contraction_rhs(cuda_device, nel, periodic):
+    """The x and y contractions on the tensor cores (TF32 head/tail split,
+    three products): within the FP32 form's bar of the oracle, on tiles that
+    are full, ragged, walled and periodic."""
+    L = tuple(1000.0 * n for n in nel)
+    wl = W.box(nel, 4, (0.0, 0.0, 0.0), L, periodic, seed=7 * sum(nel) + 1)
+    with GpuContext(wl, precision=FP32) as g:
+        g.xg.xg_set_contraction(g.ctx, TF32X3)
+        got = g.rhs()
+    err = rel_l2_per_var(got, oracle_rhs(wl))
+    assert np.all(err <= RHS_TOL32), err
+
+
+def test_fp32_tf32x3_contraction_tc_scaled_and_steps(cuda_device):
+    """The cyclone box (scaled) at a random state: one RHS within the bar;
+    20 steps stay within 1e-5 of the CUDA-core contraction's run."""
+    wl = W.tc(nel=(16, 16, 4), state="random")
+    with GpuContext(wl, precision=FP32) as g:
+        g.xg.xg_set_contraction(g.ctx, TF32X3)
+        got = g.rhs()
+        g.step(20)
+        q_tc = g.state()
+    assert np.all(rel_l2_per_var(got, oracle_rhs(wl)) <= RHS_TOL32)
+    with GpuContext(wl, precision=FP32) as g:
+        g.step(20)
+        q_fma = g.state()
+    assert np.all(rel_l2_per_var(q_tc - wl["q"], q_fma - wl["q"]) <= 1e-4)
+    assert np.all(rel_l2_per_var(q_tc, q_fma) <= 1e-5)
+
+
+def test_tf32x3_contraction_is_fp32_order_4_only(cuda_device):
+    from paper_2504_08157_gb300 import xg
+    for prec, N in ((FP64, 4), (DF64, 4), (FP32, 3)):
+        wl = W.box((2, 2, 2), N, (0.0, 0.0, 0.0), (2000.0, 2000.0, 2000.0), (True, True, False))
+        with GpuContext(wl, precision=prec) as g:
+            with pytest.raises(xg.XgError) as e:
+                xg.xg_set_contraction(g.ctx, TF32X3)
+            assert e.value.status == xg.XG_ERR_UNSUPPORTED
+            xg.xg_set_contraction(g.ctx, 0)
