@@ -340,18 +340,21 @@ def run_xg(args, world, rank, local):
     gdof = lambda ms, k: dof_u * 3 * k * world / (ms / 1e3) / 1e9
 
     ctx = make_ctx(xg, torch, wl, dev, prec)
+    knames = KERNEL_NAMES[prec]
+    if prec == xg.XG_FP32 and args.contraction == "tf32x3":
+        xg.xg_set_contraction(ctx, xg.XG_CONTRACT_TF32X3)
+        knames = ("k_f_plane_xy_tc",) + knames[1:]
     ms_max, kms, klaunch, clk = timed_steps(xg, torch, ctx, dt, K, Wm, stream, world, local, True)
     value = gdof(ms_max, K)
 
     # roofline of the dominant kernel (largest share of device time)
     k = int(np.argmax(kms))
     name = KERNELS[k]
-    kname = KERNEL_NAMES[prec][k]
+    kname = knames[k]
     avg_ms = kms[k] / max(klaunch[k], 1)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    per_launch = {KERNEL_NAMES[prec][i]: round(kms[i] / max(klaunch[i], 1), 4)
-                  for i in range(3) if klaunch[i]}
+    per_launch = {knames[i]: round(kms[i] / max(klaunch[i], 1), 4) for i in range(3) if klaunch[i]}
     if prec == xg.XG_FP64:
         flops = flops_per_node(name, wl["N"]) * cfg["nodes"]
         achieved = flops / (avg_ms / 1e3) / 1e12
@@ -448,7 +451,9 @@ def run_xg(args, world, rank, local):
                "steps": K, "warmup": Wm, "ms_per_step": round(ms_max / K, 4),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": {xg.XG_FP64: "f64", xg.XG_DF64: "f32x2", xg.XG_FP32: "f32"}[prec],
-               "precision": args.precision, "data": "synthetic", "impl": "xg",
+               "precision": args.precision,
+               "contraction": args.contraction if prec == xg.XG_FP32 else None,
+               "data": "synthetic", "impl": "xg",
                "config": cfg,
                "gdof_paper_convention": round(dof_p * 3 * K * world / (ms_max / 1e3) / 1e9, 4),
                "plain_fp64": plain,
@@ -892,6 +897,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
                     help="df64: FP64-accurate double-float on the FP32 pipes (default); "
                          "fp64: native FP64; fp32: the FP32 precision form")
+    ap.add_argument("--contraction", choices=["fma", "tf32x3"], default="fma",
+                    help="with --precision fp32: x and y contractions on the CUDA cores (fma) or "
+                         "on the tensor cores (tf32x3, order 4)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain-FP64 and FP32-form comparison runs")
     ap.add_argument("--instances", type=int, default=96,
