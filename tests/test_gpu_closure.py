@@ -212,3 +212,13 @@ def test_trained_closure_reduces_the_held_out_tendency_error(cuda_device):
     ev = CL.evaluate(W.closure_case, 9, (10, 10, 5), model, 20, cuda_device)
     print("state error after 20 steps: plain", ev["plain"], "closure", ev["closure"])
     assert all(np.isfinite(ev["closure"]))
+    # the plain right-hand side as fallback: the gain chosen on a validation run is one of
+    # the candidates, its validation run is no worse than the plain one (gain 0 competes),
+    # and gain 0 reproduces the plain coarse run bit for bit
+    g, sel = CL.select_gain(W.closure_case, 10, (10, 10, 5), model, 20, cuda_device,
+                            gains=(0.0, 0.1, 1.0))
+    assert g in (0.0, 0.1, 1.0) and set(sel) == {0.0, 0.1, 1.0}
+    score = lambda e: sum(a / b for a, b in zip(e, sel[0.0])) / 5
+    assert score(sel[g]) <= 1.0
+    again = CL.evaluate_gains(W.closure_case, 9, (10, 10, 5), model, 20, cuda_device, (0.0,))
+    assert again[0.0] == ev["plain"]
