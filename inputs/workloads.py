@@ -85,6 +85,22 @@ def tc(nel=(128, 128, 16), N=4, state="initial", seed=1, heating_seed=2504):
                 phys=dict(PHYS, f=5.0e-5), dt=0.1, q=q, rho0=rho0, Theta0=Th0, S_theta=S)
 
 
+def tc_paper(nel=(80, 80, 24), N=5, heating_seed=2504):
+    """The cyclone box on the grid of the paper's timing runs (Sec. 4.1 and
+    Table 1): 800 x 800 x 20 km, doubly periodic, 80 x 80 x 24 elements of
+    order 5 (2 km horizontal and 167 m vertical node spacing); the same
+    stable sounding, vortex and heating recipe as ``tc``."""
+    lo, hi = (-400.0e3, -400.0e3, 0.0), (400.0e3, 400.0e3, 20.0e3)
+    periodic = (True, True, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.stable_sounding(ax[2], nbv=0.01)
+    n_xy = ax[0].size * ax[1].size
+    q = atm.vortex_state(X, Y, Z, rho0, n_xy, (0.0, 0.0))
+    S = atm.heating(X, Y, Z, (0.0, 0.0), seed=heating_seed)
+    return dict(name="tc_paper", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=5.0e-5), dt=0.5, q=q, rho0=rho0, Theta0=Th0, S_theta=S)
+
+
 def box(nel, N, lo, hi, periodic, f=1.0e-4, seed=7, heating_amp=1.0e-3, sounding="stable"):
     """Generic box with a seeded smooth random state (for parity sweeps over
     orders, sizes and boundary types)."""
