@@ -176,7 +176,6 @@ template <int N>
 cudaError_t configure_n(xg_ctx* c) {
   cudaError_t e = xg::raise_dynamic_smem(xg::k_line_x<N>, c->xsmem);
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_df_line_x<N>, c->xsmem);
-  if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_line_x<N>, c->xsmem / 2);
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_plane_xy<N>, xg::PlaneLayoutF<N>::bytes);
   if (N == xg::PlaneTcLayout::N && e == cudaSuccess)
     e = xg::raise_dynamic_smem(xg::k_f_plane_xy_tc, xg::PlaneTcLayout::bytes);

@@ -1,6 +1,8 @@
 // xg_kernels_f32.cuh -- the precision form: FP32 state and volume arithmetic.
 //
-// Same method and three-pass stage as xg_kernels.cuh.  The state
+// Same method as xg_kernels.cuh in two passes per stage: the x and y parts
+// in the plane kernel of xg_plane_f32.cuh, then the tiled z pass here (z
+// part, sources, closure correction, walls, stage store).  The state
 // perturbations (rho', rho u, rho v, rho w, Theta'), the fluxes, the LGL
 // contractions, the assembly, the sources and the SSP-RK combination are
 // FP32 (4 bytes per value, FMA on the FP32 pipes).  The pressure
@@ -73,92 +75,6 @@ __device__ __forceinline__ float f_row_from(const FParams& P, int a, const float
 #pragma unroll
   for (int l = 0; l <= N; ++l) acc = fmaf(P.Dm[D][a][l], f[l], acc);
   return acc;
-}
-
-// ---------------------------------------------------------------- x lines
-template <int N>
-__global__ void __launch_bounds__(kXThreads) k_f_line_x(const FParams P, const FBufs B) {
-  extern __shared__ float smf[];
-  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const int nseg = P.nseg[0];
-  const int y = blockIdx.x, z = blockIdx.y;
-  const long long np = P.np;
-  const long long row = (long long)nx * (y + (long long)ny * z);
-  const int ld = nx + 1;
-  float* F = smf;            // [5][ld], later rows 0..N-1 of every segment in place
-  float* RN = smf + 5 * ld;  // [5][nseg] row N
-  const df rho0d = B.base[z], Th0d = B.base[nz + z], p0 = B.base[2 * nz + z];
-  const df iTh0 = B.base[3 * nz + z];
-  const float rho0 = rho0d.h + rho0d.l, Th0 = Th0d.h + Th0d.l;
-  const float* __restrict__ q = B.q;
-  float* __restrict__ Wo = B.W;
-  float* __restrict__ To = B.T;
-
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const long long I = row + i;
-    const float rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
-    const float tp = q[4 * np + I];
-    const float ir = __frcp_rn(rho0 + rp);
-    const float u = mu * ir, v = mv * ir, w = mw * ir;
-    const float pp = f_pressure_pert(P, tp, p0, iTh0);
-    Wo[I] = v;
-    Wo[np + I] = w;
-    Wo[2 * np + I] = pp;
-    F[i] = mu;
-    F[ld + i] = fmaf(mu, u, pp);
-    F[2 * ld + i] = mv * u;
-    F[3 * ld + i] = mw * u;
-    F[4 * ld + i] = (Th0 + tp) * u;
-    if (P.per[0] && i == 0) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) F[c * ld + nx] = F[c * ld];
-    }
-  }
-  __syncthreads();
-
-  for (int s0 = 0; s0 < nseg; s0 += blockDim.x) {
-    const int s = s0 + threadIdx.x;
-    float rows[5][N + 1];
-    if (s < nseg) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        float f[N + 1];
-#pragma unroll
-        for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
-#pragma unroll
-        for (int a = 0; a <= N; ++a) rows[c][a] = f_row_from<N, 0>(P, a, f, 0.0f);
-      }
-    }
-    __syncthreads();
-    if (s < nseg) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-#pragma unroll
-        for (int a = 0; a < N; ++a) F[c * ld + s * N + a] = rows[c][a];
-        RN[c * nseg + s] = rows[c][N];
-      }
-    }
-    __syncthreads();
-  }
-
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const int s = i / N, a = i - s * N;
-    const long long I = row + i;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      float v;
-      if (s == nseg) {
-        v = 2.0f * RN[c * nseg + nseg - 1];
-      } else if (a != 0) {
-        v = F[c * ld + i];
-      } else {
-        const float r0 = F[c * ld + i];
-        const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
-        v = left >= 0 ? r0 + RN[c * nseg + left] : 2.0f * r0;
-      }
-      To[c * np + I] = v;
-    }
-  }
 }
 
 // ---------------------------------------------------------------- y and z lines, tiled
