@@ -28,10 +28,10 @@
 
 namespace xg {
 
-constexpr int kDotBlocks = 512;
+constexpr int kDotBlocksMax = 2048;   // partial-sum slots; a launch uses 4 blocks per SM
 constexpr int kDotThreads = 256;
-constexpr int kDotBatch = 8;
-constexpr int kCombMax = 6;
+constexpr int kDotBatch = 16;   // vectors per multi-dot launch
+constexpr int kCombMax = 17;    // terms per combination launch
 
 // sum over the node's segment(s) along d of Dm rows times f (times lev[k]
 // for the loaded node's index k along the line, when given): -d/dx_d of the
@@ -116,12 +116,19 @@ struct Comb {
   int k;
 };
 
-// out = sum_k c_k x_k (out may be one of the x_k)
-__global__ void k_comb(const Comb C, double* out, long long n) {
+// out = sum_k c_k x_k over the first K terms of C (out may be one of the
+// x_k); K fixed at compile time so that the K loads of an element are issued
+// together.
+template <int K>
+__global__ void __launch_bounds__(256) k_comb(const Comb C, double* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
+    double x[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) x[k] = C.x[k][i];
     double a = 0.0;
-    for (int k = 0; k < C.k; ++k) a = fma(C.c[k], C.x[k][i], a);
+#pragma unroll
+    for (int k = 0; k < K; ++k) a = fma(C.c[k], x[k], a);
     out[i] = a;
   }
 }
@@ -131,33 +138,45 @@ struct Dots {
   int k;
 };
 
-// partial[b][i] = sum over block b's nodes of sum_var wt[var] w * v_i
+// partial[b][i] = sum over block b's nodes of sum_var wt[var] w * v_i for
+// the K vectors of D, in a fixed order (deterministic for a given grid): the
+// K loads of a node are issued together, warps reduce by shuffles, the
+// block's warps in order.
+template <int K>
 __global__ void __launch_bounds__(kDotThreads) k_wdots(const double* __restrict__ w, const Dots D,
                                                        const double* __restrict__ wt, long long np,
                                                        double* __restrict__ partial) {
-  __shared__ double red[kDotBatch][kDotThreads];
-  double acc[kDotBatch];
+  __shared__ double red[K][kDotThreads / 32];
+  double acc[K];
 #pragma unroll
-  for (int i = 0; i < kDotBatch; ++i) acc[i] = 0.0;
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
   const long long per = (np + gridDim.x - 1) / gridDim.x;
   const long long lo = blockIdx.x * per, hi = min(np, lo + per);
   for (int c = 0; c < 5; ++c) {
     const double s = wt[c];
+    const long long off = c * np;
     for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) {
-      const double a = s * w[c * np + I];
+      double v[K];
 #pragma unroll
-      for (int i = 0; i < kDotBatch; ++i)
-        if (i < D.k) acc[i] = fma(a, D.v[i][c * np + I], acc[i]);
+      for (int i = 0; i < K; ++i) v[i] = D.v[i][off + I];
+      const double a = s * w[off + I];
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] = fma(a, v[i], acc[i]);
     }
   }
-  for (int i = 0; i < kDotBatch; ++i) red[i][threadIdx.x] = acc[i];
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h)
-      for (int i = 0; i < kDotBatch; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + h];
-    __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+    if (lane == 0) red[i][warp] = acc[i];
   }
-  if (threadIdx.x < kDotBatch) partial[blockIdx.x * kDotBatch + threadIdx.x] = red[threadIdx.x][0];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+    partial[blockIdx.x * kDotBatch + threadIdx.x] = t;
+  }
 }
 
 // partial[b][c] = sum over block b's nodes of x_c^2
@@ -208,7 +227,8 @@ struct Imex {
   double* cpl = nullptr;       // [nz]
   double* th0 = nullptr;       // [nz]
   double* wt = nullptr;        // [5] inner-product weights
-  double* partial = nullptr;   // [kDotBlocks][8]
+  double* partial = nullptr;   // [kDotBlocksMax][8]
+  int dot_blocks = 512;        // blocks of the reductions: 4 per SM
   std::vector<double> hpart;
 };
 
@@ -250,7 +270,15 @@ cudaError_t comb(const std::vector<std::pair<double, const double*>>& terms, dou
     }
     C.k = j;
     const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 8192);
-    xg::k_comb<<<blocks, 256, 0, st>>>(C, out, n);
+    switch (C.k) {
+#define XG_COMB_CASE(K) \
+  case K: xg::k_comb<K><<<blocks, 256, 0, st>>>(C, out, n); break;
+      XG_COMB_CASE(1) XG_COMB_CASE(2) XG_COMB_CASE(3) XG_COMB_CASE(4) XG_COMB_CASE(5) XG_COMB_CASE(6)
+      XG_COMB_CASE(7) XG_COMB_CASE(8) XG_COMB_CASE(9) XG_COMB_CASE(10) XG_COMB_CASE(11) XG_COMB_CASE(12)
+      XG_COMB_CASE(13) XG_COMB_CASE(14) XG_COMB_CASE(15) XG_COMB_CASE(16)
+      default: xg::k_comb<xg::kCombMax><<<blocks, 256, 0, st>>>(C, out, n); break;
+#undef XG_COMB_CASE
+    }
     first = false;
   }
   return cudaGetLastError();
@@ -264,16 +292,24 @@ cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* v
     memset(&D, 0, sizeof(D));
     D.k = std::min(xg::kDotBatch, k - i0);
     for (int i = 0; i < D.k; ++i) D.v[i] = vs[i0 + i];
-    xg::k_wdots<<<xg::kDotBlocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
+    switch (D.k) {
+#define XG_WDOTS_CASE(K) \
+  case K: xg::k_wdots<K><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial); break;
+      XG_WDOTS_CASE(1) XG_WDOTS_CASE(2) XG_WDOTS_CASE(3) XG_WDOTS_CASE(4) XG_WDOTS_CASE(5)
+      XG_WDOTS_CASE(6) XG_WDOTS_CASE(7) XG_WDOTS_CASE(8) XG_WDOTS_CASE(9) XG_WDOTS_CASE(10)
+      XG_WDOTS_CASE(11) XG_WDOTS_CASE(12) XG_WDOTS_CASE(13) XG_WDOTS_CASE(14) XG_WDOTS_CASE(15)
+      default: xg::k_wdots<xg::kDotBatch><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
+#undef XG_WDOTS_CASE
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * xg::kDotBlocks * xg::kDotBatch,
+      e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * X.dot_blocks * xg::kDotBatch,
                           cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < D.k; ++i) {
       double s = 0.0;
-      for (int b = 0; b < xg::kDotBlocks; ++b) s += X.hpart[(size_t)b * xg::kDotBatch + i];
+      for (int b = 0; b < X.dot_blocks; ++b) s += X.hpart[(size_t)b * xg::kDotBatch + i];
       out[i0 + i] = s;
     }
   }
@@ -282,17 +318,17 @@ cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* v
 
 // per-variable weights 1 / mean(b_v^2) (1 where b_v vanishes)
 cudaError_t set_weights(Imex& X, long long np, const double* b, cudaStream_t st) {
-  xg::k_varsq<<<xg::kDotBlocks, xg::kDotThreads, 0, st>>>(b, np, X.partial);
+  xg::k_varsq<<<X.dot_blocks, xg::kDotThreads, 0, st>>>(b, np, X.partial);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * xg::kDotBlocks * 5, cudaMemcpyDeviceToHost,
+    e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * X.dot_blocks * 5, cudaMemcpyDeviceToHost,
                         st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
   double wt[5];
   for (int c = 0; c < 5; ++c) {
     double s = 0.0;
-    for (int blk = 0; blk < xg::kDotBlocks; ++blk) s += X.hpart[(size_t)blk * 5 + c];
+    for (int blk = 0; blk < X.dot_blocks; ++blk) s += X.hpart[(size_t)blk * 5 + c];
     const double ms = s / (double)np;
     wt[c] = ms > 0.0 ? 1.0 / ms : 1.0;
   }
@@ -441,7 +477,10 @@ cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
     c->imex = X;
     X->m = m;
     X->n = n;
-    X->hpart.resize((size_t)xg::kDotBlocks * xg::kDotBatch);
+    X->hpart.resize((size_t)xg::kDotBlocksMax * xg::kDotBatch);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+    X->dot_blocks = std::min(xg::kDotBlocksMax, std::max(1, 4 * sms));
     const size_t vb = sizeof(double) * (size_t)n;
     cudaError_t e = cudaMalloc((void**)&X->V, vb * (m + 1));
     double** bufs[] = {&X->x, &X->b, &X->w, &X->S[0], &X->S[1], &X->S[2], &X->L[0], &X->L[1], &X->q1};
@@ -450,7 +489,7 @@ cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->cpl, sizeof(double) * c->n[2]);
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->th0, sizeof(double) * c->n[2]);
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->wt, sizeof(double) * 5);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&X->partial, sizeof(double) * xg::kDotBlocks * xg::kDotBatch);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->partial, sizeof(double) * xg::kDotBlocksMax * xg::kDotBatch);
     if (e != cudaSuccess) {
       imex_free_buffers(X);
       delete X;
