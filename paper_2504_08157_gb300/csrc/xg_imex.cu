@@ -141,8 +141,9 @@ struct Dots {
 // partial[b][i] = sum over block b's nodes of sum_var wt[var] w * v_i for
 // the K vectors of D, in a fixed order (deterministic for a given grid): the
 // K loads of a node are issued together, warps reduce by shuffles, the
-// block's warps in order.
-template <int K>
+// block's warps in order.  SELF (K = 1, v_0 = w): the weighted |w|^2 from one
+// read of w.
+template <int K, bool SELF = false>
 __global__ void __launch_bounds__(kDotThreads) k_wdots(const double* __restrict__ w, const Dots D,
                                                        const double* __restrict__ wt, long long np,
                                                        double* __restrict__ partial) {
@@ -157,9 +158,10 @@ __global__ void __launch_bounds__(kDotThreads) k_wdots(const double* __restrict_
     const long long off = c * np;
     for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) {
       double v[K];
+      const double wi = w[off + I];
 #pragma unroll
-      for (int i = 0; i < K; ++i) v[i] = D.v[i][off + I];
-      const double a = s * w[off + I];
+      for (int i = 0; i < K; ++i) v[i] = SELF ? wi : D.v[i][off + I];
+      const double a = s * wi;
 #pragma unroll
       for (int i = 0; i < K; ++i) acc[i] = fma(a, v[i], acc[i]);
     }
@@ -292,7 +294,9 @@ cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* v
     memset(&D, 0, sizeof(D));
     D.k = std::min(xg::kDotBatch, k - i0);
     for (int i = 0; i < D.k; ++i) D.v[i] = vs[i0 + i];
-    switch (D.k) {
+    if (D.k == 1 && D.v[0] == w) {
+      xg::k_wdots<1, true><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
+    } else switch (D.k) {
 #define XG_WDOTS_CASE(K) \
   case K: xg::k_wdots<K><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial); break;
       XG_WDOTS_CASE(1) XG_WDOTS_CASE(2) XG_WDOTS_CASE(3) XG_WDOTS_CASE(4) XG_WDOTS_CASE(5)
