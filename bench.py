@@ -825,13 +825,19 @@ def run_closure(args, world, rank, local):
     t_train = time.perf_counter() - t0
     # the plain right-hand side as fallback: the output gain (0 = plain) chosen on a validation
     # run, then the test run judged at gains 0 (plain), 1 (the trained network) and the chosen
-    gain, sel = CL.select_gain(W.closure_case, 101, nel, model, args.eval_steps, dev)
-    ev = CL.evaluate_gains(W.closure_case, 100, nel, model, args.eval_steps, dev,
+    # candidates: the trained network and the same with its mean correction removed
+    cands = {"trained": model, "centered": CL.centered(model, X, dev)}
+    picks = {k: CL.select_gain(W.closure_case, 101, nel, m, args.eval_steps, dev) for k, m in cands.items()}
+    score = lambda e, p: sum(a / max(b, 1e-300) for a, b in zip(e, p)) / 5
+    best = min(picks, key=lambda k: score(picks[k][1][picks[k][0]], picks[k][1][0.0]))
+    gain = picks[best][0]
+    ev = CL.evaluate_gains(W.closure_case, 100, nel, cands[best], args.eval_steps, dev,
                            tuple(sorted({0.0, 1.0, gain})))
     vs_refined = {"plain": ev[0.0], "closure": ev[1.0], "closure_at_chosen_gain": ev[gain],
-                  "chosen_gain": gain,
+                  "chosen_gain": gain, "chosen_model": best,
                   "gain_selection": {"validation_run_seed": 101,
-                                     "errors": {repr(g): e for g, e in sel.items()}},
+                                     "errors": {k: {repr(g): e for g, e in picks[k][1].items()}
+                                                for k in picks}},
                   "what": "relative L2 distance of each coarse run's state from the restricted "
                           "refined state after %d coarse steps, per variable, relative to the "
                           "refined run's change (test run seed 100); gain g scales the closure's "

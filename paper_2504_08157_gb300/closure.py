@@ -177,6 +177,22 @@ def train(X, T, dev, epochs=20, batch=4096, lr=2e-3, seed=11, holdout=0.1):
                 holdout_zero=base_ho, holdout=hist[-1][2] if hist else base_ho)
 
 
+def centered(model, X, dev):
+    """The model with the mean of its correction over the samples X removed
+    (the output bias b3 shifted by the mean inference output, per variable):
+    a network whose correction drifts the coarse run in one direction loses
+    that drift."""
+    torch = _torch()
+    n = X.shape[1]
+    Y = torch.empty((5, n), dtype=torch.float32, device=dev)
+    xg.xg_mlp_forward(model["params"], X, model["in_mean"], model["in_scale"], model["out_scale"], Y,
+                      precision=xg.XG_MLP_BF16)
+    mean = Y.double().mean(dim=1)
+    p = model["params"].clone()
+    p[P - 5:] -= (mean / model["out_scale"].double()).float()
+    return dict(model, params=p)
+
+
 def evaluate_gains(case, seed, coarse_nel, model, coarse_steps, dev, gains):
     """The refined run once, then one coarse run per gain g: the closure's
     output scaled by g (g = 0 is the plain coarse run), all from the
