@@ -312,3 +312,53 @@ def test_planted_mistakes_are_caught(mms, monkeypatch, mistake):
         patch = lambda mp: mp.setattr(E, "local_tendency", lt)
     bad = _mms_error_with(mms, monkeypatch, patch)
     assert np.max(bad / good) > 3.0, (mistake, good, bad)
+
+
+# ---------------------------------------------------------------- linear acoustics
+
+def _acoustic_error(nel, N, eps=1e-5):
+    """A right-going sound wave in a uniform resting atmosphere without
+    gravity: rho' = e rho0 s, rho u = e rho0 c s, Theta' = e Theta0 s with
+    s = sin(k x) and c^2 = gamma p0 / rho0 obeys dq/dt = -c dq/dx to first
+    order in e.  The oracle's tendency (its odd part in e, by a central
+    difference, so the O(e^2) terms cancel) against -c dq/dx, max relative
+    error over the three wave variables."""
+    L = 4000.0
+    m = M.build_mesh((nel, 1, 1), N, (0.0, 0.0, 0.0), (L, 500.0, 500.0), (True, True, True))
+    X = np.zeros(m.Np)
+    X[m.intma.reshape(-1)] = m.xyz[0].reshape(-1)
+    phys = E.Physics(**dict(PHYS0, g=0.0), f=0.0)
+    rho0, Th0 = 1.2, 1.2 * 300.0
+    # the sound speed from the constants, not from the oracle's own gamma or pressure
+    gam = PHYS0["cp"] / PHYS0["cv"]
+    p0 = PHYS0["p_a"] * (PHYS0["R"] * Th0 / PHYS0["p_a"]) ** gam
+    c = math.sqrt(gam * p0 / rho0)
+    base = E.Base(np.full(m.n[2], rho0), np.full(m.n[2], Th0))
+    k = 2 * math.pi / L
+    s, ds = np.sin(k * X), k * np.cos(k * X)
+    amp = np.array([rho0, rho0 * c, 0.0, 0.0, Th0])
+    q = amp[:, None] * s[None, :]
+    r = (E.rhs(m, eps * q, base, None, phys) - E.rhs(m, -eps * q, base, None, phys)) / (2 * eps)
+    exact = -c * amp[:, None] * ds[None, :]
+    return max(np.max(np.abs(r[v] - exact[v])) / np.max(np.abs(exact[v])) for v in (0, 1, 4))
+
+
+def test_linear_acoustics_speed_and_order():
+    """The sound speed c = sqrt(gamma p0 / rho0) and the sign of propagation
+    (a wrong gamma, a missing pressure term or a flipped flux fails the
+    coarse check), and design-order convergence of the dispersion error."""
+    e8, e16 = _acoustic_error(8, 4), _acoustic_error(16, 4)
+    assert e8 < 4e-4, e8            # a 1 % error in c alone would give 1e-2
+    assert math.log2(e8 / e16) > 3.5, (e8, e16)
+
+
+@pytest.mark.parametrize("mistake", ["gamma", "pressure"])
+def test_acoustics_catches_planted_mistakes(monkeypatch, mistake):
+    """A 1 % error in the oracle's gamma, or 2 % in its equation of state,
+    moves the sound speed and fails the acoustic pin."""
+    if mistake == "gamma":
+        monkeypatch.setattr(E.Physics, "gamma", property(lambda self: 1.01 * self.cp / self.cv))
+    else:
+        orig = E.pressure
+        monkeypatch.setattr(E, "pressure", lambda Th, phys: 1.02 * orig(Th, phys))
+    assert _acoustic_error(8, 4) > 4e-3
