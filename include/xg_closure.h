@@ -104,6 +104,14 @@ xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long
 xg_status xg_closure_set(xg_ctx* ctx, const float* params, const float* in_mean,
                          const float* in_scale, const float* out_scale, void* stream);
 
+/* The failure path of the tensor-core kernels' bounded waits, exercised on
+ * purpose: one CTA allocates tensor memory, waits at most limit_ns
+ * nanoseconds (1 .. 1e9) on an mbarrier that nothing completes, then frees
+ * the tensor memory and returns.  Returns XG_ERR_TIMEOUT when the wait ran
+ * out (the expected result) and leaves the device usable.  Waits for the GPU.
+ * Errors: XG_ERR_ARG, XG_ERR_CUDA. */
+xg_status xg_tc_wait_selftest(long long limit_ns, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -599,6 +599,30 @@ __global__ void __launch_bounds__(kTcRows, kTcCtasPerSm)
            [&](long long I, auto&& emit) { node_features<N>(P, q, Sth, I, emit); });
 }
 
+// The bounded wait of the tensor-core kernels, made to run out: one CTA
+// allocates TMEM, initialises an mbarrier that nothing will complete, waits
+// for it with the limit, records the timeout in *status and frees its TMEM
+// (the path every tcgen05 kernel here takes when a wait gives up).
+__global__ void k_tc_wait_selftest(unsigned long long limit_ns, int* status) {
+  __shared__ unsigned long long bar;
+  __shared__ uint32_t tmem;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tmem), 32);
+  if (threadIdx.x == 0) tc::mbar_init(tc::smem_addr(&bar), 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const bool ok = tc::mbar_wait(tc::smem_addr(&bar), 0, limit_ns);
+  const int bad = __syncthreads_or(!ok);
+  if (threadIdx.x == 0) *status = bad ? 2 : 0;
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 32);
+  }
+}
+
 // Persistent grid: kTcCtasPerSm CTAs per SM, at most one per tile.  (The
 // occupancy calculator reports one CTA per SM for these kernels, although
 // their registers and shared memory admit kTcCtasPerSm, and the hardware
@@ -880,6 +904,23 @@ xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long
   cudaFree(blob);
   if (e == cudaSuccess && hflag) return XG_ERR_TIMEOUT;
   return cuda_status(e, "xg_mlp_forward");
+}
+
+xg_status xg_tc_wait_selftest(long long limit_ns, void* stream) {
+  if (limit_ns < 1 || limit_ns > 1000000000LL) return XG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  int h = -1;
+  cudaError_t e = cudaMalloc((void**)&d, sizeof(int));
+  if (e == cudaSuccess) {
+    xg::k_tc_wait_selftest<<<1, 128, 0, st>>>((unsigned long long)limit_ns, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(e, "xg_tc_wait_selftest");
+  return h == 2 ? XG_ERR_TIMEOUT : XG_OK;
 }
 
 xg_status xg_closure_set(xg_ctx* c, const float* params, const float* in_mean, const float* in_scale,

@@ -35,7 +35,7 @@ __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_cre
            "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
            "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC",
            "xg_features", "xg_restrict", "xg_column_stats", "xg_mlp_loss_grad", "xg_mlp_adam",
-           "xg_mlp_forward", "xg_closure_set", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
+           "xg_mlp_forward", "xg_closure_set", "xg_tc_wait_selftest", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
            "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS",
            "xg_dynamics", "xg_set_dynamics", "xg_dynamics_tendency", "xg_ri_velocity",
            "xg_imex_opts", "xg_imex_stats", "xg_step_imex", "xg_linear_operator", "XG_HOST", "XG_DEVICE",
@@ -165,6 +165,8 @@ def library():
     lib.xg_mlp_adam.argtypes = [P, P, P, P, I, I, D, D, D, D, P]
     lib.xg_mlp_forward.restype = I
     lib.xg_mlp_forward.argtypes = [P, P, LL, LL, P, P, P, P, LL, I, P]
+    lib.xg_tc_wait_selftest.restype = I
+    lib.xg_tc_wait_selftest.argtypes = [LL, P]
     lib.xg_closure_set.restype = I
     lib.xg_closure_set.argtypes = [P, P, P, P, P, P]
     lib.xg_set_dynamics.restype = I
@@ -520,6 +522,14 @@ def xg_mlp_forward(params, X, in_mean, in_scale, out_scale, Y, precision=XG_MLP_
                                     _f32(in_mean), _f32(in_scale), _f32(out_scale),
                                     _f32(Y, XG_CLOSURE_OUT), int(ldy), int(precision),
                                     _default_stream(stream)), "xg_mlp_forward")
+
+
+def xg_tc_wait_selftest(limit_ns, stream=None):
+    """Status of a tensor-core wait made to run out (XG_ERR_TIMEOUT expected)."""
+    st = library().xg_tc_wait_selftest(int(limit_ns), _default_stream(stream))
+    if st not in (XG_OK, XG_ERR_TIMEOUT):
+        _check(st, "xg_tc_wait_selftest")
+    return st
 
 
 def xg_closure_set(ctx, params=None, in_mean=None, in_scale=None, out_scale=None, stream=None):

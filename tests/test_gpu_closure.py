@@ -222,3 +222,21 @@ def test_trained_closure_reduces_the_held_out_tendency_error(cuda_device):
     assert score(sel[g]) <= 1.0
     again = CL.evaluate_gains(W.closure_case, 9, (10, 10, 5), model, 20, cuda_device, (0.0,))
     assert again[0.0] == ev["plain"]
+
+
+def test_tensor_core_wait_times_out_cleanly(cuda_device):
+    """A tensor-core wait that nothing completes gives up after its limit,
+    frees its tensor memory and reports XG_ERR_TIMEOUT; the device then runs
+    the tensor-core inference as before."""
+    import torch
+    from paper_2504_08157_gb300 import xg
+    assert xg.xg_tc_wait_selftest(2_000_000) == xg.XG_ERR_TIMEOUT
+    p, X, T, mean, sin, sout = _random_net(3, 300)
+    d = cuda_device
+    Y = torch.empty((5, 300), dtype=torch.float32, device=d)
+    xg.xg_mlp_forward(_t(p, d), _t(X, d), _t(mean, d), _t(sin, d), _t(sout, d), Y, precision=xg.XG_MLP_BF16)
+    ref16 = OC.forward_bf16(p, OC.normalise(X.T, mean, sin)) * sout.astype(np.float64)
+    got = Y.cpu().numpy().T
+    assert np.linalg.norm(got - ref16) <= 3e-3 * np.linalg.norm(ref16)
+    with pytest.raises(xg.XgError):
+        xg.xg_tc_wait_selftest(0)
