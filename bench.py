@@ -225,6 +225,20 @@ def cpu_sample_workload(name):
     return W.bubble()
 
 
+def random_state_errors(name, xg, torch, dev):
+    """oracle_error_of_gpu per precision on the CPU sample of the cyclone box
+    at a seeded smooth random state plus the vortex (None for the other
+    workloads)."""
+    from inputs import workloads as W
+    if name != "tc":
+        return None
+    sw = W.tc(nel=(16, 16, 16), state="random")
+    out = {p: oracle_error_of_gpu(sw, xg, torch, dev, v)
+           for p, v in (("df64", xg.XG_DF64), ("fp64", xg.XG_FP64), ("fp32", xg.XG_FP32))}
+    out["fp32_tf32x3_contraction"] = oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32, xg.XG_CONTRACT_TF32X3)
+    return out
+
+
 def time_oracle(wl, min_seconds=10.0, max_steps=50):
     """SSP-RK3 steps of the oracle until min_seconds have passed; returns
     (unique-DOF GDOF/s per stage, steps, seconds, final state)."""
@@ -438,6 +452,9 @@ def run_xg(args, world, rank, local):
               "fp32_tf32x3_contraction": (oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32,
                                                               xg.XG_CONTRACT_TF32X3)
                                           if sw["N"] == 4 else None),
+              # the same sample at a seeded smooth random state plus the vortex, where no
+              # tendency is a cancellation residual
+              "random_state": random_state_errors(args.workload, xg, torch, dev),
               "what": "relative L2 difference of one GPU right-hand side from the FP64 oracle "
                       "on the CPU sample, per variable (rho', rho u, rho v, rho w, Theta'); "
                       "at the vortex state the rho' and Theta' tendencies are residuals of "
