@@ -86,9 +86,12 @@ def test_fp32_bubble_rhs_and_200_steps(cuda_device):
 
 
 @pytest.mark.slow
-def test_fp32_full_size_tc_rhs_sampled(cuda_device):
+@pytest.mark.parametrize("contraction", [0, 1], ids=["fma", "tf32x3"])
+def test_fp32_full_size_tc_rhs_sampled(cuda_device, contraction):
+    """The full cyclone box in the bench's launch configuration, sampled
+    nodes, both contraction modes."""
     import test_gpu_parity as P
-    got, ref, _ = P._full_size_sampled(W.tc(state="random"), FP32)
+    got, ref, _ = P._full_size_sampled(W.tc(state="random"), FP32, contraction)
     err = rel_l2_per_var(got, ref)
     assert np.all(err <= RHS_TOL32), err
 

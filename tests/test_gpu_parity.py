@@ -150,8 +150,10 @@ def _sample_nodes(n, rng, count):
     return np.unique(np.array(ids, dtype=np.int64))
 
 
-def _full_size_sampled(wl, prec):
+def _full_size_sampled(wl, prec, contraction=0):
     with GpuContext(wl, precision=prec) as g:
+        if contraction:
+            g.xg.xg_set_contraction(g.ctx, contraction)
         got = g.rhs()
         n = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[0] // 5
         assert g.np == n
