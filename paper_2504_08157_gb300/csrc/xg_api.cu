@@ -209,7 +209,7 @@ void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
   prof_mark(c, 0, false, st);
   if (N == xg::PlaneTcLayout::N && c->contract == XG_CONTRACT_TF32X3) {
     static_assert(xg::plane_elems_f32(4) == xg::PlaneTcLayout::E, "same tiles");
-    xg::k_f_plane_xy_tc<<<gp, xg::kPlaneThreads, xg::PlaneTcLayout::bytes, st>>>(c->Pf, B);
+    xg::k_f_plane_xy_tc<<<gp, xg::kPlaneTcThreads, xg::PlaneTcLayout::bytes, st>>>(c->Pf, B);
   } else {
     xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
   }

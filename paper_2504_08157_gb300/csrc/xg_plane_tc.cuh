@@ -36,6 +36,11 @@
 
 namespace xg {
 
+// 8 warps: the epilogue splits the 11 products of a direction between warps
+// 0-3 and 4-7 (one TMEM lane quarter each), and threads 0..164 take the
+// 165 halo rows
+constexpr int kPlaneTcThreads = 256;
+
 struct PlaneTcLayout {
   static constexpr int N = 4, E = 8;
   static constexpr int LO = E * N + 1;               // owned extent across a line: 33
@@ -52,6 +57,7 @@ struct PlaneTcLayout {
   static constexpr size_t bytes = sizeof(float) * FLOATS + 16;   // + mbarrier, TMEM address
 };
 static_assert(PlaneTcLayout::N * 4 == 16, "segments must start 16 bytes apart");
+static_assert(PlaneTcLayout::LINES <= kPlaneTcThreads, "one thread per halo row");
 static_assert(PlaneTcLayout::RN + PlaneTcLayout::E + 1 <= PlaneTcLayout::PT, "row-N slots fit a line");
 
 // The products of one direction: D[16 b ...] for the 11 blocks, three split
@@ -245,7 +251,7 @@ __device__ __forceinline__ void f_plane_tile_tc(const FParams& P, const FBufs& B
   }
 }
 
-__global__ void __launch_bounds__(kPlaneThreads, 2) k_f_plane_xy_tc(const FParams P, const FBufs B) {
+__global__ void __launch_bounds__(kPlaneTcThreads, 2) k_f_plane_xy_tc(const FParams P, const FBufs B) {
   extern __shared__ __align__(128) float sm_plane_tc[];
   f_plane_tile_tc<false>(P, B, blockIdx.x, blockIdx.y, blockIdx.z, sm_plane_tc);
 }
