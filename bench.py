@@ -884,6 +884,41 @@ def run_closure(args, world, rank, local):
         print(json.dumps(out))
 
 
+def run_paper_imex(args, world, rank, local):
+    """The paper's timing workload alone (Table 1: 80 x 80 x 24 elements of
+    order 5, IMEX ARK2 at dt = 0.5 s with hyper-diffusion and the sponge, FP64):
+    ms per step over K steps after W warm-up steps, with the GMRES counts."""
+    import torch
+    from inputs import workloads as W
+    from paper_2504_08157_gb300 import build, xg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    stream = torch.cuda.current_stream(dev)
+    wp = W.tc_paper()
+    ctx = make_ctx(xg, torch, wp, dev, xg.XG_FP64)
+    try:
+        xg.xg_set_dynamics(ctx, (1e-4, 1e-4, 1e-4), 0.5, 4000.0, 0.05)
+        xg.xg_step_imex(ctx, 0.5, args.warmup, tol=1e-8, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = xg.xg_step_imex(ctx, 0.5, args.steps, tol=1e-8, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    finally:
+        xg.xg_destroy(ctx)
+    if rank == 0:
+        dof_u, dof_p = W.dof_counts(wp["nel"], wp["N"], wp["periodic"])
+        print(json.dumps({"workload": "paper_imex", "ms_per_step": round(ms, 3), "steps": args.steps,
+                          "warmup": args.warmup, "gmres": st.as_dict(), "dof_paper": dof_p,
+                          "config": "tc_paper 80x80x24 N=5, FP64, IMEX ARK2 dt=0.5 s, hyper-diffusion "
+                                    "+ 4 km sponge, GMRES tol 1e-8",
+                          "paper_ms_per_step": 536.0}))
+
+
 def run_reference(args, world, rank, local):
     """The FP64 oracle on the host cores, one bounded sample per step."""
     if rank != 0:
@@ -942,7 +977,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["xg", "reference"], default="xg")
-    ap.add_argument("--workload", choices=["tc", "bubble", "batch", "closure"], default="tc")
+    ap.add_argument("--workload", choices=["tc", "bubble", "batch", "closure", "paper_imex"], default="tc")
     ap.add_argument("--samples", type=int, default=2000000,
                     help="closure workload: training samples")
     ap.add_argument("--epochs", type=int, default=20, help="closure workload: training epochs")
@@ -976,6 +1011,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.workload == "closure":
         run_closure(args, world, rank, local)
+    elif args.workload == "paper_imex":
+        run_paper_imex(args, world, rank, local)
     else:
         run_xg(args, world, rank, local)
 
