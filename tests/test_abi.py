@@ -41,6 +41,16 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_binding_covers_every_declared_function(lib):
+    """The Python binding gives every declared function its ctypes signature
+    (restype and argtypes) and a wrapper of the same name."""
+    from paper_2504_08157_gb300 import xg
+    for name in declared_functions():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert hasattr(xg, name), name
+
+
 def test_status_strings(lib):
     from paper_2504_08157_gb300 import xg
     for s in range(7):
