@@ -161,3 +161,4 @@ def test_restriction_reproduces_polynomials():
     f = lambda x, y, z: x ** 3 - 2 * x * y ** 2 * z + z ** 3 * y ** 3 + 0.5
     got = C.restrict(fine_axes, coarse_axes, f(X, Y, Z).reshape(1, -1))[0]
     assert np.allclose(got, f(Xc, Yc, Zc).reshape(-1), atol=1e-11)
+
