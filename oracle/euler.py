@@ -111,16 +111,17 @@ def local_tendency(mesh, q, base, S_theta, phys, elements=None):
     F = fluxes(rho0, Theta0, qe, phys)
     dxi_dx = mesh.dxi_dx if elements is None else mesh.dxi_dx[:, :, elements]
     # Alg. 2 reference derivatives, then div F = sum_d sum_j dxi_j/dx_d dF^d/dxi_j
+    dt = np.result_type(qe, mesh.D)      # float64, or np.longdouble when extended
     div = []
     for m in range(5):
-        acc = np.zeros(intma.shape)
+        acc = np.zeros(intma.shape, dtype=dt)
         for d in range(3):
             for j in range(3):
                 acc += dxi_dx[j, d] * apply_D(mesh.D, F[m][d], j)
         div.append(acc)
     rho = rho0 + qe[0]
     Sth = S_theta[intma] if S_theta is not None else 0.0
-    S = np.empty((5,) + intma.shape)
+    S = np.empty((5,) + intma.shape, dtype=dt)
     S[0] = -div[0]
     S[1] = -div[1] + phys.f * qe[2]          # -f k x (rho u), x component
     S[2] = -div[2] - phys.f * qe[1]          # y component
@@ -137,10 +138,11 @@ def assemble(mesh, S_local, elements=None):
     intma = mesh.intma if elements is None else mesh.intma[elements]
     detJ = mesh.detJ if elements is None else mesh.detJ[elements]
     wJ = mesh.w3[None] * detJ
-    R = np.zeros((S_local.shape[0], mesh.Np))
+    dt = np.result_type(S_local, wJ)
+    R = np.zeros((S_local.shape[0], mesh.Np), dtype=dt)
     for m in range(S_local.shape[0]):
         np.add.at(R[m], intma.ravel(), (wJ * S_local[m]).ravel())
-    M = np.zeros(mesh.Np)
+    M = np.zeros(mesh.Np, dtype=wJ.dtype)
     np.add.at(M, intma.ravel(), wJ.ravel())
     return R, M
 
@@ -181,7 +183,7 @@ def divergence(mesh, F):
     F [3, Np] (the operator of steps 2-6 alone, for the metric pins)."""
     intma = mesh.intma
     Fe = [F[d][intma] for d in range(3)]
-    acc = np.zeros(intma.shape)
+    acc = np.zeros(intma.shape, dtype=np.result_type(Fe[0], mesh.D))
     for d in range(3):
         for j in range(3):
             acc += mesh.dxi_dx[j, d] * apply_D(mesh.D, Fe[d], j)
@@ -191,5 +193,5 @@ def divergence(mesh, F):
 
 def mass(mesh):
     """Diagonal mass M_I = DSS(w J) (Eq. 9 with collocated quadrature)."""
-    _, M = assemble(mesh, np.zeros((1,) + mesh.intma.shape))
+    _, M = assemble(mesh, np.zeros((1,) + mesh.intma.shape, dtype=mesh.D.dtype))
     return M

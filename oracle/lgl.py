@@ -25,9 +25,16 @@ indexed [output point i, input point l], so (D f)_i = sum_l D[i, l] f_l.
 import numpy as np
 
 
+def _real(x):
+    """x as a floating array: float64 unless it already is a wider float
+    (the extended-precision evaluation keeps np.longdouble throughout)."""
+    x = np.asarray(x)
+    return x if x.dtype == np.longdouble else np.asarray(x, dtype=np.float64)
+
+
 def legendre(n, x):
     """P_n(x) by the three-term (Bonnet) recurrence."""
-    x = np.asarray(x, dtype=np.float64)
+    x = _real(x)
     p0 = np.ones_like(x)
     if n == 0:
         return p0
@@ -56,6 +63,26 @@ def lgl_points(N):
     return x
 
 
+def lgl_points_extended(N):
+    """The LGL points in extended precision (np.longdouble): the FP64 points
+    of lgl_points polished by Newton's method on P_N'(x) in np.longdouble,
+    with P_N' = N (x P_N - P_{N-1}) / (x^2 - 1) and, from Legendre's equation
+    (1 - x^2) P'' - 2 x P' + N (N+1) P = 0, P_N'' = (2 x P_N' - N (N+1) P_N)
+    / (1 - x^2).  Quadratic convergence: four steps from FP64 accuracy reach
+    the working precision."""
+    x = np.asarray(lgl_points(N), dtype=np.longdouble)
+    if N < 2:
+        return x
+    inner = x[1:-1]
+    for _ in range(4):
+        p, pm = legendre(N, inner), legendre(N - 1, inner)
+        dp = N * (inner * p - pm) / (inner * inner - 1)
+        d2p = (2 * inner * dp - N * (N + 1) * p) / (1 - inner * inner)
+        inner = inner - dp / d2p
+    x[1:-1] = inner
+    return x
+
+
 def lgl_weights(N, x=None):
     """LGL quadrature weights w_j = 2 / (N (N+1) P_N(x_j)^2) (Eq. 8)."""
     if x is None:
@@ -66,7 +93,7 @@ def lgl_weights(N, x=None):
 def derivative_matrix(x):
     """D[i, l] = h_l'(x_i) for the Lagrange cardinal basis on points x
     (Alg. 2's dphi/dxi, transposed), barycentric form."""
-    x = np.asarray(x, dtype=np.float64)
+    x = _real(x)
     n = x.size
     diff = x[:, None] - x[None, :]
     np.fill_diagonal(diff, 1.0)

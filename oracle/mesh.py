@@ -111,22 +111,31 @@ def elements_around(nel, N, periodic, nodes):
 
 
 def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-               periodic=(False, False, False), A=None, elements=None):
+               periodic=(False, False, False), A=None, elements=None, dtype=np.float64):
     """Build the CG mesh of a box of nel = (nel_x, nel_y, nel_z) order-N
     hexahedra (Sec. 2.2) and its per-node metric terms.  With ``elements``
     (global element ids) only those elements are stored; the global node
-    numbering is that of the whole box."""
+    numbering is that of the whole box.
+
+    dtype=np.longdouble builds the same mesh in extended precision (LGL
+    points from lgl_points_extended; box corners, A and every derived array
+    in np.longdouble), for evaluating the same definitions with rounding far
+    below FP64's where a result is a small residual of large terms; the
+    euler functions then compute in extended precision when given
+    np.longdouble state arrays."""
     nel = tuple(int(v) for v in nel)
     periodic = tuple(bool(p) for p in periodic)
     if min(nel) < 1 or N < 1:
         raise ValueError("need nel >= 1 and N >= 1")
-    lo = np.asarray(lo, dtype=np.float64)
-    hi = np.asarray(hi, dtype=np.float64)
-    A = np.eye(3) if A is None else np.asarray(A, dtype=np.float64)
+    if dtype not in (np.float64, np.longdouble):
+        raise ValueError("dtype must be np.float64 or np.longdouble")
+    lo = np.asarray(lo, dtype=dtype)
+    hi = np.asarray(hi, dtype=dtype)
+    A = np.eye(3, dtype=dtype) if A is None else np.asarray(A, dtype=dtype)
     n = tuple(N * nel[d] + (0 if periodic[d] else 1) for d in range(3))
     Np = n[0] * n[1] * n[2]
 
-    xi = lgl.lgl_points(N)
+    xi = lgl.lgl_points(N) if dtype == np.float64 else lgl.lgl_points_extended(N)
     w = lgl.lgl_weights(N, xi)
     D = lgl.derivative_matrix(xi)
 
@@ -144,7 +153,7 @@ def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
     gz = (N * ez[:, None, None, None] + a[None, :, None, None]) % n[2]
     intma = gx + n[0] * (gy + n[1] * gz)
 
-    h = (hi - lo) / np.asarray(nel, dtype=np.float64)
+    h = (hi - lo) / np.asarray(nel, dtype=dtype)
     bx = lo[0] + (ex[:, None, None, None] + (xi[None, None, None, :] + 1.0) / 2.0) * h[0]
     by = lo[1] + (ey[:, None, None, None] + (xi[None, None, :, None] + 1.0) / 2.0) * h[1]
     bz = lo[2] + (ez[:, None, None, None] + (xi[None, :, None, None] + 1.0) / 2.0) * h[2]
@@ -162,16 +171,39 @@ def build_mesh(nel, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
     return m
 
 
+def _det_inv3(jac):
+    """Determinant and inverse of 3 x 3 matrices jac[i, j, ...] by cofactors
+    (any float dtype; numpy's linalg has no extended-precision routines):
+    det = sum_j jac[0, j] C[0, j], inv[j, i] = C[i, j] / det with the
+    cofactors C[i, j] = (-1)^(i+j) minor(i, j)."""
+    C = np.empty_like(jac)
+    for i in range(3):
+        for j in range(3):
+            r = [k for k in range(3) if k != i]
+            c = [k for k in range(3) if k != j]
+            minor = jac[r[0], c[0]] * jac[r[1], c[1]] - jac[r[0], c[1]] * jac[r[1], c[0]]
+            C[i, j] = minor if (i + j) % 2 == 0 else -minor
+    det = jac[0, 0] * C[0, 0] + jac[0, 1] * C[0, 1] + jac[0, 2] * C[0, 2]
+    inv = np.empty_like(jac)
+    for i in range(3):
+        for j in range(3):
+            inv[j, i] = C[i, j] / det
+    return det, inv
+
+
 def _metrics(m):
     """Per-node Jacobian matrix dx_i/dxi_j from the node coordinates with D,
     its determinant J (Eq. 8) and inverse dxi_j/dx_i (Eq. 5)."""
-    jac = np.empty((3, 3) + m.xyz.shape[1:])  # [x_i, xi_j, ...]
+    jac = np.empty((3, 3) + m.xyz.shape[1:], dtype=m.xyz.dtype)  # [x_i, xi_j, ...]
     for i in range(3):
         for j in range(3):
             jac[i, j] = apply_D(m.D, m.xyz[i], j)
-    jm = np.moveaxis(jac, (0, 1), (-2, -1))    # [..., i, j]
-    m.detJ = np.linalg.det(jm)
-    inv = np.linalg.inv(jm)                    # [..., j, i] = dxi_j/dx_i
-    m.dxi_dx = np.moveaxis(inv, (-2, -1), (0, 1))
+    if jac.dtype == np.float64:
+        jm = np.moveaxis(jac, (0, 1), (-2, -1))    # [..., i, j]
+        m.detJ = np.linalg.det(jm)
+        inv = np.linalg.inv(jm)                    # [..., j, i] = dxi_j/dx_i
+        m.dxi_dx = np.moveaxis(inv, (-2, -1), (0, 1))
+    else:
+        m.detJ, m.dxi_dx = _det_inv3(jac)
     w = m.w
     m.w3 = w[:, None, None] * w[None, :, None] * w[None, None, :]

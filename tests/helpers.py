@@ -31,6 +31,34 @@ def oracle_rhs(wl, q=None):
     return E.rhs(m, wl["q"] if q is None else q, base, wl["S_theta"], phys)
 
 
+def oracle_of_extended(wl, elements=None):
+    """The oracle's mesh, physics and reference state for an evaluation in
+    extended precision (np.longdouble): the same definitions with rounding
+    far below FP64's, the reference where a tendency is a small residual of
+    cancelling parts (the pure-vortex state)."""
+    m = M.build_mesh(wl["nel"], wl["N"], wl["lo"], wl["hi"], wl["periodic"], elements=elements,
+                     dtype=np.longdouble)
+    return m, E.Physics(**wl["phys"]), E.Base(wl["rho0"], wl["Theta0"])
+
+
+def _ld(a):
+    return None if a is None else np.asarray(a, dtype=np.longdouble)
+
+
+def oracle_rhs_extended(wl, q=None):
+    """E.rhs in extended precision, returned as float64."""
+    m, phys, base = oracle_of_extended(wl)
+    return E.rhs(m, _ld(wl["q"] if q is None else q), base, _ld(wl["S_theta"]), phys).astype(np.float64)
+
+
+def oracle_rhs_at_nodes_extended(wl, nodes, q=None):
+    """E.rhs_at_nodes in extended precision on the elements around the nodes."""
+    el = M.elements_around(wl["nel"], wl["N"], wl["periodic"], nodes)
+    m, phys, base = oracle_of_extended(wl, elements=el)
+    return E.rhs_at_nodes(m, _ld(wl["q"] if q is None else q), base, _ld(wl["S_theta"]), phys,
+                          nodes).astype(np.float64)
+
+
 def oracle_steps(wl, nsteps, q=None):
     m, phys, base = oracle_of(wl)
     L = lambda s: E.rhs(m, s, base, wl["S_theta"], phys)
