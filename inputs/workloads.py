@@ -117,6 +117,31 @@ def box(nel, N, lo, hi, periodic, f=1.0e-4, seed=7, heating_amp=1.0e-3, sounding
                 Theta0=Th0, S_theta=S)
 
 
+def eos_span(nel=(4, 3, 8), N=4, seed=11, lo_ratio=1.0e-4, hi_ratio=0.3):
+    """A box whose Theta' reaches |Theta'/Theta_0| = ``lo_ratio`` at the
+    bottom level and ``hi_ratio`` at the top (an amplitude geometric in
+    height, times a seeded smooth pattern in [-1, 1] kept at least 1e-3 in
+    magnitude), so that the equation of state is evaluated on both sides of
+    any switch point in between; the other variables are a seeded smooth
+    random state.  Walls on all sides, stable sounding."""
+    lo, hi = (0.0, 0.0, 0.0), (4000.0, 3000.0, 8000.0)
+    periodic = (False, False, False)
+    X, Y, Z, ax = grid.node_coords(nel, N, lo, hi, periodic)
+    rho0, Th0 = atm.stable_sounding(ax[2], nbv=0.01)
+    q = atm.smooth_random_state(X, Y, Z, lo, hi, periodic, seed)
+    s = atm.smooth_random_state(X, Y, Z, lo, hi, (True, True, True), seed + 1,
+                                amps=(1.0, 0, 0, 0, 0))[0]
+    s = s / np.max(np.abs(s))
+    s = np.sign(s) * np.maximum(np.abs(s), 1.0e-3)
+    nxy = ax[0].size * ax[1].size
+    gz = np.arange(X.size) // nxy
+    t = Z / hi[2]
+    ratio = lo_ratio * (hi_ratio / lo_ratio) ** t
+    q[4] = Th0[gz] * ratio * s
+    return dict(name="eos_span", nel=tuple(nel), N=N, lo=lo, hi=hi, periodic=periodic,
+                phys=dict(PHYS, f=1.0e-4), dt=0.02, q=q, rho0=rho0, Theta0=Th0, S_theta=None)
+
+
 def dof_counts(nel, N, periodic):
     """(unique-node DOF, element-local DOF): 5 variables times the unique
     global nodes, and the paper's convention N_e (N+1)^3 x 5 (Sec. 5.2)."""

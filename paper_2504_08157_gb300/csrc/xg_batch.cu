@@ -233,7 +233,7 @@ size_t batch_smem(int lo, int hi, int half) {
     const int E = batch_plane_elems(N, half);
     const size_t TS = (size_t)E * N;
     const size_t plane = sizeof(float) * 2 * 5 * (TS + 1) * (TS + N + 1);
-    const size_t z = sizeof(float) * 5 * (size_t)(batch_z_segments(N) * N + N + 1) * kTileCols;
+    const size_t z = sizeof(float) * (size_t)tline_smem_floats(N, batch_z_segments(N));
     m = std::max(m, std::max(plane, z));
   }
   return kInstBytes + m;

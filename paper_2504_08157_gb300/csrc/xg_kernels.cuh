@@ -18,7 +18,8 @@
 //   k_line_x  one CTA per x-line: pointwise primitives (u, v, w, p') of every
 //             node, x-fluxes staged in shared memory, one thread per element
 //             segment for the 1-D contraction (Alg. 2), face averaging;
-//             writes the x part of the tendency to T and (v, w, p') to W.
+//             writes the x part of the tendency to T and (v, w, p', theta =
+//             Theta/rho) to W.
 //   k_line_y  one thread per (x, z) column marching along y over a chunk of
 //             element segments, carrying the shared face node's flux and
 //             one-sided derivative; adds the y part into T.
@@ -53,6 +54,11 @@ struct LineParams {
   int n[3];       // global nodes per direction
   int nseg[3];    // elements per direction
   int per[3];     // 1 = periodic
+  // y ends that are faces of an element partition (a domain split into
+  // y-slabs, Sec. 3.1): the face node's y part is completed by the
+  // neighbouring partition's one-sided row (xg_partition_*) instead of the
+  // wall's doubled row, and no wall condition applies there
+  int open_y[2];
   long long np;   // n[0] n[1] n[2]
   // Dm[d][a][l] = -(2/h_d) D[a][l] (x 1/2 for a = 0 and a = N)
   double Dm[3][kMaxOrder + 1][kMaxOrder + 1];
@@ -77,7 +83,7 @@ struct StageBufs {
   const double* q;      // [5][np] state the tendency is taken of
   const double* qn;     // [5][np] q^n of the RK combination (alpha != 0)
   double* out;          // [5][np] new state, or dq/dt when rhs_only
-  double* W;            // [3][np] v, w, p' (written by k_line_x)
+  double* W;            // [4][np] v, w, p', theta = Theta/rho (written by k_line_x)
   double* T;            // [5][np] x + y parts of the tendency
   const double* S;      // [np] heating S_theta (K/s)
   const double* base;   // [4][nz]: rho0, Theta0, p0, 1/Theta0 per level
@@ -85,6 +91,10 @@ struct StageBufs {
   double dt, alpha, beta;
   int rhs_only;
   const double* E = nullptr;  // [5][np] extra tendency (hyper-diffusion, sponge) or null
+  // open_y[1]: the one-sided row N of the slab's last y segment at every
+  // (x, z) of the end face, [5][n_z][n_x] (written by k_line_y instead of the
+  // wall's doubled row)
+  double* face_hi = nullptr;
 };
 
 // (1 + x)^gamma - 1: the binomial series (Horner) for small |x|, where the
@@ -168,6 +178,53 @@ __device__ __forceinline__ double row_N(const LineParams& P, const double (&f)[N
   return acc;
 }
 
+// ---------------------------------------------------------------- difference form
+// The rho' and Theta' tendencies are residuals of cancelling flux
+// derivatives where the flow is nearly non-divergent (in a vortex the x and
+// y parts nearly cancel), so their rounding must stay far below the size of
+// each part.  Every row of the LGL derivative matrix sums to zero (D 1 = 0,
+// the derivative of a constant), so a row may be applied to the flux minus
+// its value at the segment's first node:
+//     sum_l Dm[a][l] f_l = sum_{l>=1} Dm[a][l] (f_l - f_0);
+// the roundings then scale with the flux's variation across the segment
+// instead of the flux.  The Theta' flux Theta u_d is written theta (rho u_d)
+// with theta = Theta / rho (W[3]), and its differences as
+//     F_l - F_0 = theta_l (m_l - m_0) + (theta_l - theta_0) m_0,
+// so the product's rounding scales with the variation as well.  The exact
+// value is unchanged.
+//
+// diffs(m, th, dm, dF): dm[l] = m_l - m_0 and dF[l] = theta_l m_l - theta_0
+// m_0 in that form, l = 0..N (dm[0] = dF[0] = 0).
+template <int N>
+__device__ __forceinline__ void seg_diffs(const double (&m)[N + 1], const double (&th)[N + 1],
+                                          double (&dm)[N + 1], double (&dF)[N + 1]) {
+  dm[0] = 0.0;
+  dF[0] = 0.0;
+#pragma unroll
+  for (int l = 1; l <= N; ++l) {
+    dm[l] = m[l] - m[0];
+    dF[l] = fma(th[l], dm[l], (th[l] - th[0]) * m[0]);
+  }
+}
+
+// start + sum_{l>=1} Dm[d][a][l] d[l] (d[0] = 0 is not used)
+template <int N, int D>
+__device__ __forceinline__ double drow_from(const LineParams& P, int a, const double (&d)[N + 1],
+                                            double start) {
+  double acc = start;
+#pragma unroll
+  for (int l = 1; l <= N; ++l) acc = fma(P.Dm[D][a][l], d[l], acc);
+  return acc;
+}
+
+template <int N, int D>
+__device__ __forceinline__ double drow_N(const LineParams& P, const double (&d)[N + 1]) {
+  double acc = P.Dm[D][N][1] * d[1];
+#pragma unroll
+  for (int l = 2; l <= N; ++l) acc = fma(P.Dm[D][N][l], d[l], acc);
+  return acc;
+}
+
 // ---------------------------------------------------------------- x lines
 // grid (n_y, n_z), block kXThreads, dynamic shared memory
 // 8 * (5 (n_x + 1) + 5 nseg_x) bytes.
@@ -203,14 +260,16 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
     const double u = mu * ir, v = mv * ir, w = mw * ir;
     const double pp = p0 * eos_phi(P, tp * iTh0);
     const double Th = Th0 + tp;
+    const double th = Th * ir;
     Wo[I] = v;
     Wo[np + I] = w;
     Wo[2 * np + I] = pp;
+    Wo[3 * np + I] = th;
     F[i] = mu;
     F[ld + i] = fma(mu, u, pp);
     F[2 * ld + i] = mv * u;
     F[3 * ld + i] = mw * u;
-    F[4 * ld + i] = Th * u;
+    F[4 * ld + i] = th;              // theta: the Theta' flux is theta (rho u)
     if (P.per[0] && i == 0) {
       F[nx] = F[0];
       F[ld + nx] = F[ld];
@@ -229,8 +288,19 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
     const int s = s0 + threadIdx.x;
     double rows[5][N + 1];
     if (s < nseg) {
+      {   // rho' and Theta' in difference form
+        double m[N + 1], th[N + 1], dm[N + 1], dF[N + 1];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+        for (int l = 0; l <= N; ++l) {
+          m[l] = F[s * N + l];
+          th[l] = F[4 * ld + s * N + l];
+        }
+        seg_diffs<N>(m, th, dm, dF);
+        contract_eo<N, 0>(P, dm, rows[0]);
+        contract_eo<N, 0>(P, dF, rows[4]);
+      }
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
         double f[N + 1];
 #pragma unroll
         for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
@@ -274,15 +344,17 @@ __global__ void __launch_bounds__(kXThreads) k_line_x(const LineParams P, const 
 // ---------------------------------------------------------------- y lines
 // grid (ceil(n_x / blockDim), nchunk, n_z); each thread marches `chunk`
 // element segments along y at its (x, z).
+// y-fluxes at one node; slot 4 holds theta (the Theta' flux theta (rho v)
+// is taken in difference form with slot 0)
 __device__ __forceinline__ void flux_y(const double* __restrict__ q, const double* __restrict__ W,
-                                       long long np, long long I, double Th0, double (&f)[5]) {
-  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+                                       long long np, long long I, double (&f)[5]) {
+  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
   const double v = W[I], pp = W[2 * np + I];
   f[0] = mv;
   f[1] = mu * v;
   f[2] = fma(mv, v, pp);
   f[3] = mw * v;
-  f[4] = (Th0 + tp) * v;
+  f[4] = W[3 * np + I];
 }
 
 template <int N>
@@ -297,7 +369,6 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
   if (s0 >= s1) return;
   const long long np = P.np;
   const long long col = x + (long long)nx * ny * z;
-  const double Th0 = __ldg(B.base + nz + z);
   const double* __restrict__ q = B.q;
   const double* __restrict__ W = B.W;
   auto nodeI = [&](int gy) -> long long { return col + (long long)nx * (gy == ny ? 0 : gy); };
@@ -310,18 +381,22 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
 #pragma unroll
     for (int l = 0; l <= N; ++l) {
       double f[5];
-      flux_y(q, W, np, nodeI(sp * N + l), Th0, f);
+      flux_y(q, W, np, nodeI(sp * N + l), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
     }
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(fl[0], fl[4], dm, dF);
+    carry[0] = drow_N<N, 1>(P, dm);
+    carry[4] = drow_N<N, 1>(P, dF);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = row_N<N, 1>(P, fl[c]);
+    for (int c = 1; c < 4; ++c) carry[c] = row_N<N, 1>(P, fl[c]);
   }
 
   double fc[5][N + 1];
   {
     double f[5];
-    flux_y(q, W, np, nodeI(s0 * N), Th0, f);
+    flux_y(q, W, np, nodeI(s0 * N), f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
   }
@@ -330,10 +405,18 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
 #pragma unroll
     for (int l = 1; l <= N; ++l) {
       double f[5];
-      flux_y(q, W, np, nodeI(s * N + l), Th0, f);
+      flux_y(q, W, np, nodeI(s * N + l), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
     }
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(fc[0], fc[4], dm, dF);
+    // row a of variable c from start (rho' and Theta' in difference form)
+    auto rowc = [&](int c, int a, double start) -> double {
+      if (c == 0) return drow_from<N, 1>(P, a, dm, start);
+      if (c == 4) return drow_from<N, 1>(P, a, dF, start);
+      return row_from<N, 1>(P, a, fc[c], start);
+    };
     // the segment's running x parts, all loaded before any store
     double tv[5][N];
 #pragma unroll
@@ -346,33 +429,41 @@ __global__ void __launch_bounds__(128) k_line_y(const LineParams P, const StageB
     for (int c = 0; c < 5; ++c) {
       // the running x part is the start of each row's FMA chain
       double t0 = tv[c][0];
-      if (!has_left) t0 = row_from<N, 1>(P, 0, fc[c], t0);   // wall: the row counts twice
-      t0 = row_from<N, 1>(P, 0, fc[c], t0);
+      if (!has_left && !P.open_y[0]) t0 = rowc(c, 0, t0);   // wall: the row counts twice
+      t0 = rowc(c, 0, t0);
       T[c * np + nodeI(s * N)] = has_left ? t0 + carry[c] : t0;
 #pragma unroll
-      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = row_from<N, 1>(P, a, fc[c], tv[c][a]);
-      carry[c] = row_N<N, 1>(P, fc[c]);
-      fc[c][0] = fc[c][N];
+      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = rowc(c, a, tv[c][a]);
+      carry[c] = c == 0 ? drow_N<N, 1>(P, dm) : (c == 4 ? drow_N<N, 1>(P, dF) : row_N<N, 1>(P, fc[c]));
     }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fc[c][0] = fc[c][N];
     has_left = true;
   }
   if (!P.per[1] && s1 == nseg) {
     const long long I = nodeI(nseg * N);
+    if (P.open_y[1]) {   // partition face: the row goes to the neighbour
+      const long long Fo = x + (long long)nx * z;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) T[c * np + I] += carry[c] + carry[c];
+      for (int c = 0; c < 5; ++c) B.face_hi[c * (long long)nx * nz + Fo] = carry[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) T[c * np + I] += carry[c] + carry[c];
+    }
   }
 }
 
 // ---------------------------------------------------------------- z lines + sources + stage
+// z-fluxes at one node; slot 4 holds theta (see flux_y)
 __device__ __forceinline__ void flux_z(const double* __restrict__ q, const double* __restrict__ W,
-                                       long long np, long long I, double Th0, double (&f)[5]) {
-  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+                                       long long np, long long I, double (&f)[5]) {
+  const double mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
   const double w = W[np + I], pp = W[2 * np + I];
   f[0] = mw;
   f[1] = mu * w;
   f[2] = mv * w;
   f[3] = fma(mw, w, pp);
-  f[4] = (Th0 + tp) * w;
+  f[4] = W[3 * np + I];
 }
 
 // Completes node I at level gz given L[5] = T + z part (the assembled flux
@@ -395,7 +486,7 @@ __device__ __forceinline__ void finish_node(const LineParams& P, const StageBufs
   L[3] = fma(-P.g, rp, L[3]);                    // -rho' g
   if (B.S) L[4] = fma(__ldg(B.base + gz) + rp, __ldg(B.S + I), L[4]);  // rho S_theta
   if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = 0.0;
-  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = 0.0;
+  if (!P.per[1] && ((y == 0 && !P.open_y[0]) || (y == P.n[1] - 1 && !P.open_y[1]))) L[2] = 0.0;
   if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0;
   if (B.rhs_only) {
 #pragma unroll
@@ -441,7 +532,6 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
   const double* __restrict__ qn = B.qn;
   double* __restrict__ out = B.out;
   auto lev = [&](int gz) -> int { return gz == nz ? 0 : gz; };
-  auto th0 = [&](int gz) -> double { return __ldg(B.base + nz + gz); };
   bool bad = false;
 
   double carry[5];
@@ -453,19 +543,23 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
     for (int l = 0; l <= N; ++l) {
       const int gz = lev(sp * N + l);
       double f[5];
-      flux_z(q, W, np, col + nxy * gz, th0(gz), f);
+      flux_z(q, W, np, col + nxy * gz, f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
     }
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(fl[0], fl[4], dm, dF);
+    carry[0] = drow_N<N, 2>(P, dm);
+    carry[4] = drow_N<N, 2>(P, dF);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = row_N<N, 2>(P, fl[c]);
+    for (int c = 1; c < 4; ++c) carry[c] = row_N<N, 2>(P, fl[c]);
   }
 
   double fc[5][N + 1];
   {
     const int gz = s0 * N;
     double f[5];
-    flux_z(q, W, np, col + nxy * gz, th0(gz), f);
+    flux_z(q, W, np, col + nxy * gz, f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
   }
@@ -474,10 +568,17 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
     for (int l = 1; l <= N; ++l) {
       const int gz = lev(s * N + l);
       double f[5];
-      flux_z(q, W, np, col + nxy * gz, th0(gz), f);
+      flux_z(q, W, np, col + nxy * gz, f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
     }
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(fc[0], fc[4], dm, dF);
+    auto rowc = [&](int c, int a, double start) -> double {
+      if (c == 0) return drow_from<N, 2>(P, a, dm, start);
+      if (c == 4) return drow_from<N, 2>(P, a, dF, start);
+      return row_from<N, 2>(P, a, fc[c], start);
+    };
     // the segment's x + y parts, all loaded before any store
     double tv[5][N];
 #pragma unroll
@@ -494,17 +595,17 @@ __global__ void __launch_bounds__(128) k_line_z(const LineParams P, const StageB
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double t = tv[c][a];
-        if (a == 0 && !has_left) t = row_from<N, 2>(P, 0, fc[c], t);  // wall: the row counts twice
-        t = row_from<N, 2>(P, a, fc[c], t);
+        if (a == 0 && !has_left) t = rowc(c, 0, t);  // wall: the row counts twice
+        t = rowc(c, a, t);
         L[c] = (a == 0 && has_left) ? t + carry[c] : t;
       }
       finish_node(P, B, q, qn, out, I, x, y, gz, L, bad);
     }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      carry[c] = row_N<N, 2>(P, fc[c]);
-      fc[c][0] = fc[c][N];
-    }
+    for (int c = 0; c < 5; ++c)
+      carry[c] = c == 0 ? drow_N<N, 2>(P, dm) : (c == 4 ? drow_N<N, 2>(P, dF) : row_N<N, 2>(P, fc[c]));
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fc[c][0] = fc[c][N];
     has_left = true;
   }
   if (!P.per[2] && s1 == nseg) {

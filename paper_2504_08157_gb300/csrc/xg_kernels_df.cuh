@@ -23,6 +23,7 @@ struct DfParams {
   int n[3];
   int nseg[3];
   int per[3];
+  int open_y[2];   // partition faces at the y ends (see LineParams)
   long long np;
   df Dm[3][kMaxOrder + 1][kMaxOrder + 1];   // -(2/h_d) D, rows 0 and N halved
   df eos_c[3];                              // C(gamma,1..3)
@@ -36,13 +37,14 @@ struct DfBufs {
   const df* q;
   const df* qn;
   df* out;
-  df* W;          // [3][np] v, w, p'
+  df* W;          // [4][np] v, w, p', theta = Theta / rho
   df* T;          // [5][np]
   const df* S;    // [np] or null
   const df* base; // [4][nz] rho0, Theta0, p0, 1/Theta0
   int* flag;
   df dt, alpha, beta, bdt;   // bdt = beta dt
   int rhs_only;
+  df* face_hi;    // [5][n_z][n_x] one-sided row N at an open y end (see StageBufs)
 };
 
 // (1+x)^gamma - 1 = x (c1 + x (c2 + x (c3 + x g(x)))), g = c4 + ... + c8 x^4
@@ -78,6 +80,52 @@ __device__ __forceinline__ df df_row(const DfParams& P, int a, const df (&f)[N +
   return dacc_value(A);
 }
 
+// ---------------------------------------------------------------- difference form
+// The rho' and Theta' tendencies are small residuals of cancelling flux
+// derivatives wherever the flow is nearly non-divergent (a vortex: the x and
+// y parts nearly cancel), so their absolute error must stay far below the
+// size of each part.  A compensated dot product's error is proportional to
+// the sum of |Dm[a][l] f_l|, which for a smooth flux is many times the
+// derivative itself.  Each row of the LGL derivative matrix sums to zero
+// (D 1 = 0: the derivative of a constant), so
+//     sum_l Dm[a][l] f_l = sum_{l>=1} Dm[a][l] (f_l - f_0),
+// whose terms scale with the flux's variation across the element segment
+// instead of with the flux itself.  The Theta' flux Theta u_d is written as
+// theta (rho u_d) with theta = Theta / rho, and its differences as
+//     F_l - F_0 = theta_l (m_l - m_0) + (theta_l - theta_0) m_0,
+// so that the rounding of the product also scales with the variation (for a
+// level-uniform theta, as in a balanced vortex, the second part vanishes).
+// The exact value is unchanged; only the rounding is.
+
+// differences of one element segment: dm[l-1] = m_l - m_0 (the rho' flux)
+// and dF[l-1] = theta_l m_l - theta_0 m_0 (the Theta' flux), l = 1..N
+template <int N>
+__device__ __forceinline__ void df_seg_diffs(const df (&m)[N + 1], const df (&th)[N + 1],
+                                             df (&dm)[N], df (&dF)[N]) {
+#pragma unroll
+  for (int l = 1; l <= N; ++l) {
+    dm[l - 1] = df_sub(m[l], m[0]);
+    dF[l - 1] = df_add_nc(df_mul(th[l], dm[l - 1]), df_mul(df_sub(th[l], th[0]), m[0]));
+  }
+}
+
+// start + sum_{l>=1} Dm[d][a][l] d[l-1] (Dot2)
+template <int N, int D>
+__device__ __forceinline__ df df_drow_from(const DfParams& P, int a, const df (&d)[N], df start) {
+  dacc A = dacc_from(start);
+#pragma unroll
+  for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[D][a][l], d[l - 1]);
+  return dacc_value(A);
+}
+
+template <int N, int D>
+__device__ __forceinline__ df df_drow(const DfParams& P, int a, const df (&d)[N]) {
+  dacc A = dacc_prod(P.Dm[D][a][1], d[0]);
+#pragma unroll
+  for (int l = 2; l <= N; ++l) dacc_fma(A, P.Dm[D][a][l], d[l - 1]);
+  return dacc_value(A);
+}
+
 // ---------------------------------------------------------------- x lines
 template <int N>
 __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const DfBufs B) {
@@ -104,14 +152,16 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
     const df u = df_mul(mu, ir), v = df_mul(mv, ir), w = df_mul(mw, ir);
     const df pp = df_mul(p0, df_eos_phi(P, df_mul(tp, iTh0)));
     const df Th = df_add(Th0, tp);
+    const df th = df_mul(Th, ir);
     Wo[I] = v;
     Wo[np + I] = w;
     Wo[2 * np + I] = pp;
+    Wo[3 * np + I] = th;
     F[i] = mu;
     F[ld + i] = df_add(df_mul(mu, u), pp);
     F[2 * ld + i] = df_mul(mv, u);
     F[3 * ld + i] = df_mul(mw, u);
-    F[4 * ld + i] = df_mul(Th, u);
+    F[4 * ld + i] = th;               // theta: the Theta' flux is theta (rho u)
     if (P.per[0] && i == 0) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) F[c * ld + nx] = F[c * ld];
@@ -123,8 +173,22 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
     const int s = s0 + threadIdx.x;
     df rows[5][N + 1];
     if (s < nseg) {
+      {
+        df m[N + 1], th[N + 1], dm[N], dF[N];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+        for (int l = 0; l <= N; ++l) {
+          m[l] = F[s * N + l];
+          th[l] = F[4 * ld + s * N + l];
+        }
+        df_seg_diffs<N>(m, th, dm, dF);
+#pragma unroll
+        for (int a = 0; a <= N; ++a) {
+          rows[0][a] = df_drow<N, 0>(P, a, dm);
+          rows[4][a] = df_drow<N, 0>(P, a, dF);
+        }
+      }
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
         df f[N + 1];
 #pragma unroll
         for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
@@ -165,15 +229,17 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
 }
 
 // ---------------------------------------------------------------- y lines
+// y-fluxes at one node; slot 4 holds theta = Theta / rho from W (the Theta'
+// flux is theta (rho v), taken in difference form)
 __device__ __forceinline__ void df_flux_y(const df* __restrict__ q, const df* __restrict__ W,
-                                          long long np, long long I, df Th0, df (&f)[5]) {
-  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I], tp = q[4 * np + I];
+                                          long long np, long long I, df (&f)[5]) {
+  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
   const df v = W[I], pp = W[2 * np + I];
   f[0] = mv;
   f[1] = df_mul(mu, v);
   f[2] = df_add(df_mul(mv, v), pp);
   f[3] = df_mul(mw, v);
-  f[4] = df_mul(df_add(Th0, tp), v);
+  f[4] = W[3 * np + I];
 }
 
 template <int N>
@@ -188,7 +254,6 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
   if (s0 >= s1) return;
   const long long np = P.np;
   const long long col = x + (long long)nx * ny * z;
-  const df Th0 = B.base[nz + z];
   const df* __restrict__ q = B.q;
   const df* __restrict__ W = B.W;
   df* __restrict__ T = B.T;
@@ -202,18 +267,22 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
 #pragma unroll
     for (int l = 0; l <= N; ++l) {
       df f[5];
-      df_flux_y(q, W, np, nodeI(sp * N + l), Th0, f);
+      df_flux_y(q, W, np, nodeI(sp * N + l), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
     }
+    df dm[N], dF[N];
+    df_seg_diffs<N>(fl[0], fl[4], dm, dF);
+    carry[0] = df_drow<N, 1>(P, N, dm);
+    carry[4] = df_drow<N, 1>(P, N, dF);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) carry[c] = df_row<N, 1>(P, N, fl[c]);
+    for (int c = 1; c < 4; ++c) carry[c] = df_row<N, 1>(P, N, fl[c]);
   }
 
   df fc[5][N + 1];
   {
     df f[5];
-    df_flux_y(q, W, np, nodeI(s0 * N), Th0, f);
+    df_flux_y(q, W, np, nodeI(s0 * N), f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
   }
@@ -221,7 +290,7 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
 #pragma unroll
     for (int l = 1; l <= N; ++l) {
       df f[5];
-      df_flux_y(q, W, np, nodeI(s * N + l), Th0, f);
+      df_flux_y(q, W, np, nodeI(s * N + l), f);
 #pragma unroll
       for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
     }
@@ -232,23 +301,39 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
 #pragma unroll
       for (int c = 0; c < 5; ++c) tv[c][a] = T[c * np + I];
     }
+    df dm[N], dF[N];
+    df_seg_diffs<N>(fc[0], fc[4], dm, dF);
+    // row a of variable c seeded with start: rho' and Theta' in difference form
+    auto rowc = [&](int c, int a, df start) -> df {
+      if (c == 0) return df_drow_from<N, 1>(P, a, dm, start);
+      if (c == 4) return df_drow_from<N, 1>(P, a, dF, start);
+      return df_row_from<N, 1>(P, a, fc[c], start);
+    };
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       df t0 = tv[c][0];
-      if (!has_left) t0 = df_row_from<N, 1>(P, 0, fc[c], t0);   // wall: the row counts twice
-      t0 = df_row_from<N, 1>(P, 0, fc[c], t0);
+      if (!has_left && !P.open_y[0]) t0 = rowc(c, 0, t0);   // wall: the row counts twice
+      t0 = rowc(c, 0, t0);
       T[c * np + nodeI(s * N)] = has_left ? df_add(t0, carry[c]) : t0;
 #pragma unroll
-      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = df_row_from<N, 1>(P, a, fc[c], tv[c][a]);
-      carry[c] = df_row<N, 1>(P, N, fc[c]);
-      fc[c][0] = fc[c][N];
+      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = rowc(c, a, tv[c][a]);
+      carry[c] = c == 0 ? df_drow<N, 1>(P, N, dm)
+                        : (c == 4 ? df_drow<N, 1>(P, N, dF) : df_row<N, 1>(P, N, fc[c]));
     }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) fc[c][0] = fc[c][N];
     has_left = true;
   }
   if (!P.per[1] && s1 == nseg) {
     const long long I = nodeI(nseg * N);
+    if (P.open_y[1]) {   // partition face: the row goes to the neighbour
+      const long long Fo = x + (long long)nx * z;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) T[c * np + I] = df_add(T[c * np + I], df_scale2(carry[c], 2.0f));
+      for (int c = 0; c < 5; ++c) B.face_hi[c * (long long)nx * nz + Fo] = carry[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) T[c * np + I] = df_add(T[c * np + I], df_scale2(carry[c], 2.0f));
+    }
   }
 }
 
@@ -278,14 +363,15 @@ namespace xg {
 // also owns the wall node.
 // Fluxes along DIR at one node from loaded values: qv = (rho', rho u,
 // rho v, rho w, Theta'), vel = v (DIR 1) or w (DIR 2), pp = p'.
+// Slot 4 holds theta = Theta / rho: the Theta' flux theta (rho u_DIR) is
+// taken in difference form with slot 0.
 template <int DIR>
-__device__ __forceinline__ void df_flux_vals(const df (&qv)[5], df vel, df pp, df Th0, df (&f)[5]) {
-  const df Th = df_add(Th0, qv[4]);
+__device__ __forceinline__ void df_flux_vals(const df (&qv)[5], df vel, df pp, df th, df (&f)[5]) {
   f[0] = qv[DIR + 1];
   f[1] = DIR == 1 ? df_mul(qv[1], vel) : df_mul(qv[1], vel);
   f[2] = DIR == 1 ? df_add(df_mul(qv[2], vel), pp) : df_mul(qv[2], vel);
   f[3] = DIR == 1 ? df_mul(qv[3], vel) : df_add(df_mul(qv[3], vel), pp);
-  f[4] = df_mul(Th, vel);
+  f[4] = th;
 }
 
 // Sources, walls and the stage store of one node from loaded values.
@@ -310,7 +396,7 @@ __device__ __forceinline__ void df_finish_vals(const DfParams& P, const DfBufs& 
   }
   const df zero = {0.0f, 0.0f};
   if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = zero;
-  if (!P.per[1] && (y == 0 || y == P.n[1] - 1)) L[2] = zero;
+  if (!P.per[1] && ((y == 0 && !P.open_y[0]) || (y == P.n[1] - 1 && !P.open_y[1]))) L[2] = zero;
   if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = zero;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
@@ -345,7 +431,11 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   constexpr int K = df_tile_segments(N);
   constexpr int NS = K * N + N + 1;            // flux slots: N halo planes + K N + 1
   __shared__ df Fs[5][NS][kTileCols];
-  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  // rho' and Theta' flux differences of slot j against its segment's first
+  // slot (difference form); slot j >= 1 lies in the segment that starts at
+  // slot N floor((j - 1) / N), of which it is an interior node or the end
+  __shared__ df Ds[2][NS][kTileCols];
+  const int nx = P.n[0], ny = P.n[1];
   const int nd = P.n[DIR];                      // nodes along the line
   const int nseg = P.nseg[DIR];
   const bool per = P.per[DIR] != 0;
@@ -372,21 +462,22 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const int gh = plane((s0 - 1) * N + ty);
   const long long I = base + sd * (main_plane ? g : 0);
   const long long Ih = base + sd * (halo ? gh : 0);
-
   // every global load of the thread first: one memory round trip
-  df qv[5], vel, pp, hq[5], hvel, hpp, t[5], qnv[5], sv = {0.0f, 0.0f};
+  df qv[5], vel, pp, th, hq[5], hvel, hpp, hth, t[5], qnv[5], sv = {0.0f, 0.0f};
   hq[0] = sv;
   if (main_plane) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) qv[c] = B.q[c * np + I];
     vel = B.W[vslot * np + I];
     pp = B.W[2 * np + I];
+    th = B.W[3 * np + I];
   }
   if (halo) {
 #pragma unroll
     for (int c = 1; c < 5; ++c) hq[c] = B.q[c * np + Ih];
     hvel = B.W[vslot * np + Ih];
     hpp = B.W[2 * np + Ih];
+    hth = B.W[3 * np + Ih];
   }
   if (owns) {
 #pragma unroll
@@ -401,16 +492,29 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   }
   if (main_plane) {
     df f[5];
-    df_flux_vals<DIR>(qv, vel, pp, B.base[nz + (DIR == 2 ? g : other)], f);
+    df_flux_vals<DIR>(qv, vel, pp, th, f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
   }
   if (halo) {
     df f[5];
-    df_flux_vals<DIR>(hq, hvel, hpp, B.base[nz + (DIR == 2 ? gh : other)], f);
+    df_flux_vals<DIR>(hq, hvel, hpp, hth, f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
   }
+  __syncthreads();
+
+  // difference form of the rho' and Theta' fluxes, slot by slot
+  auto diff_slot = [&](int j) {
+    const int b = N * ((j - 1) / N);
+    const df mj = Fs[0][j][tx], mb = Fs[0][b][tx];
+    const df thj = Fs[4][j][tx], thb = Fs[4][b][tx];
+    const df dm = df_sub(mj, mb);
+    Ds[0][j][tx] = dm;
+    Ds[1][j][tx] = df_add_nc(df_mul(thj, dm), df_mul(df_sub(thj, thb), mb));
+  };
+  if (main_plane && (ty > 0 || has_left)) diff_slot(N + ty);   // slot N closes the halo segment
+  if (halo && ty > 0) diff_slot(ty);
   __syncthreads();
   if (!owns) return;
 
@@ -419,6 +523,32 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const int a = ty < kc * N ? ty - k * N : N;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
+    if (c == 0 || c == 4) {
+      const int e = c == 0 ? 0 : 1;
+      df d[N];
+#pragma unroll
+      for (int l = 1; l <= N; ++l) d[l - 1] = Ds[e][N + k * N + l][tx];
+      if (a == N) {                                 // wall node: its one-sided row counts twice
+        const df r = df_drow<N, DIR>(P, N, d);
+        t[c] = df_add(t[c], df_scale2(r, 2.0f));
+      } else if (a > 0) {
+        t[c] = df_drow_from<N, DIR>(P, a, d, t[c]);
+      } else {
+        // a face: both one-sided rows in one compensated sum (the segment
+        // before, or the same row twice at the wall at the line start)
+        df dl[N];
+        const bool left = k > 0 || has_left;
+#pragma unroll
+        for (int l = 1; l <= N; ++l) dl[l - 1] = left ? Ds[e][k * N + l][tx] : d[l - 1];
+        dacc A = dacc_from(t[c]);
+#pragma unroll
+        for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[DIR][0][l], d[l - 1]);
+#pragma unroll
+        for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[DIR][left ? N : 0][l], dl[l - 1]);
+        t[c] = dacc_value(A);
+      }
+      continue;
+    }
     df f[N + 1];
 #pragma unroll
     for (int l = 0; l <= N; ++l) f[l] = Fs[c][N + k * N + l][tx];

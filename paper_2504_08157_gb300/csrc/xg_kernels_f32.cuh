@@ -77,17 +77,52 @@ __device__ __forceinline__ float f_row_from(const FParams& P, int a, const float
   return acc;
 }
 
+// Row a of the rho' and Theta' contractions in difference form, added to r0
+// and r4, from the segment's rho' fluxes m_l = rho u_D and theta_l:
+//   sum_{l>=1} Dm[a][l] (m_l - m_0)  and  sum_{l>=1} Dm[a][l] (F_l - F_0),
+//   F_l - F_0 = theta_l (m_l - m_0) + (theta_l - theta_0) m_0.
+// Equal to the plain rows because each row of the derivative matrix sums to
+// zero; the roundings scale with the fluxes' variation across the segment
+// instead of the fluxes themselves, which matters where the two tendencies
+// are residuals of cancelling x, y and z parts (the difference form is
+// described in full beside df_seg_diffs).
+template <int N, int D>
+__device__ __forceinline__ void f_drows(const FParams& P, int a, const float (&m)[N + 1],
+                                        const float (&th)[N + 1], float& r0, float& r4) {
+#pragma unroll
+  for (int l = 1; l <= N; ++l) {
+    const float dm = m[l] - m[0];
+    const float dF = fmaf(th[l], dm, (th[l] - th[0]) * m[0]);
+    r0 = fmaf(P.Dm[D][a][l], dm, r0);
+    r4 = fmaf(P.Dm[D][a][l], dF, r4);
+  }
+}
+
+// start + sum_{l>=1} Dm[D][a][l] d[l-1] (differences against the segment start)
+template <int N, int D>
+__device__ __forceinline__ float f_drow_from(const FParams& P, int a, const float (&d)[N], float acc) {
+#pragma unroll
+  for (int l = 1; l <= N; ++l) acc = fmaf(P.Dm[D][a][l], d[l - 1], acc);
+  return acc;
+}
+
+// Shared floats of one y/z tile of K segments: the fluxes [5][NS][32] and the
+// rho' and Theta' flux differences [2][NS][32], NS = K N + N + 1.
+__host__ __device__ constexpr int tline_smem_floats(int N, int K) { return 7 * (K * N + N + 1) * kTileCols; }
+
 // ---------------------------------------------------------------- y and z lines, tiled
 // One thread per node over (32 x-columns) x (K segments along DIR) tiles, as
 // k_df_tline; DIR = 1 adds the y part into T, DIR = 2 finishes the node.
+// Slot 4 holds theta = Theta / rho: the Theta' flux theta (rho u_DIR) is taken
+// in difference form with slot 0.
 template <int DIR>
-__device__ __forceinline__ void f_flux_vals(const float (&qv)[5], float vel, float pp, float Th0,
-                                            float (&f)[5]) {
+__device__ __forceinline__ void f_flux_vals(const float (&qv)[5], float vel, float pp, float rho0,
+                                            float Th0, float (&f)[5]) {
   f[0] = qv[DIR + 1];
   f[1] = qv[1] * vel;
   f[2] = DIR == 1 ? fmaf(qv[2], vel, pp) : qv[2] * vel;
   f[3] = DIR == 1 ? qv[3] * vel : fmaf(qv[3], vel, pp);
-  f[4] = (Th0 + qv[4]) * vel;
+  f[4] = (Th0 + qv[4]) * __frcp_rn(rho0 + qv[0]);
 }
 
 __device__ __forceinline__ void f_finish_vals(const FParams& P, const FBufs& B,
@@ -125,8 +160,9 @@ __device__ __forceinline__ void f_finish_vals(const FParams& P, const FBufs& B,
 //
 // f_tline_tile is the body of one tile (bx: 32-column block, by: K-segment
 // block, other: the y index for DIR = 2, the z index for DIR = 1) for the
-// thread (tx, ty), ty < K N + 1 (larger ty own nothing); Fs is the tile's
-// shared flux array [5][K N + N + 1][32].
+// thread (tx, ty), ty < K N + 1 (larger ty own nothing, but every thread of
+// the block calls it: it synchronises the block twice); Fsm holds the tile's
+// tline_smem_floats(N, K) shared floats.
 // CG selects L2-only loads (ld.global.cg) for every array a launch may
 // itself have written, which a persistent launch that runs several passes
 // needs; the per-pass kernels use ordinary loads.
@@ -141,6 +177,9 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
                                              int other, int tx, int ty, float* Fsm) {
   constexpr int NS = K * N + N + 1;
   auto Fs = reinterpret_cast<float(*)[NS][kTileCols]>(Fsm);
+  // rho' and Theta' flux differences of slot j against the first slot of its
+  // segment, N floor((j - 1) / N) (slot j >= 1 is an interior node or the end)
+  auto Ds = reinterpret_cast<float(*)[NS][kTileCols]>(Fsm + 5 * NS * kTileCols);
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
   const int nd = P.n[DIR];
   const int nseg = P.nseg[DIR];
@@ -156,6 +195,10 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
   auto th0 = [&](int g) -> float {
     const df t = B.base[nz + (DIR == 2 ? g : other)];
+    return t.h + t.l;
+  };
+  auto rh0 = [&](int g) -> float {
+    const df t = B.base[DIR == 2 ? g : other];
     return t.h + t.l;
   };
   const int vslot = DIR == 1 ? 0 : 1;
@@ -179,7 +222,7 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   }
   if (halo) {
 #pragma unroll
-    for (int c = 1; c < 5; ++c) hq[c] = ldf<CG>(B.q + c * np + Ih);
+    for (int c = 0; c < 5; ++c) hq[c] = ldf<CG>(B.q + c * np + Ih);
     hvel = ldf<CG>(B.W + vslot * np + Ih);
     hpp = ldf<CG>(B.W + 2 * np + Ih);
   }
@@ -200,23 +243,56 @@ __device__ __forceinline__ void f_tline_tile(const FParams& P, const FBufs& B, i
   }
   if (main_plane) {
     float f[5];
-    f_flux_vals<DIR>(qv, vel, pp, th0(g), f);
+    f_flux_vals<DIR>(qv, vel, pp, rh0(g), th0(g), f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
   }
   if (halo) {
     float f[5];
-    f_flux_vals<DIR>(hq, hvel, hpp, th0(gh), f);
+    f_flux_vals<DIR>(hq, hvel, hpp, rh0(gh), th0(gh), f);
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
   }
+  __syncthreads();
+  // difference form of the rho' and Theta' fluxes, slot by slot (every
+  // thread of the block reaches both barriers)
+  auto diff_slot = [&](int j) {
+    const int b = N * ((j - 1) / N);
+    const float mb = Fs[0][b][tx], thb = Fs[4][b][tx], thj = Fs[4][j][tx];
+    const float dm = Fs[0][j][tx] - mb;
+    Ds[0][j][tx] = dm;
+    Ds[1][j][tx] = fmaf(thj, dm, (thj - thb) * mb);
+  };
+  if (main_plane && (ty > 0 || has_left)) diff_slot(N + ty);   // slot N closes the halo segment
+  if (halo && ty > 0) diff_slot(ty);
   __syncthreads();
   if (!owns) return;   // no barrier follows: the caller synchronises before reusing Fs
 
   const int k = ty < kc * N ? ty / N : kc - 1;
   const int a = ty < kc * N ? ty - k * N : N;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
+  for (int e = 0; e < 2; ++e) {
+    const int c = e == 0 ? 0 : 4;
+    float d[N];
+#pragma unroll
+    for (int l = 1; l <= N; ++l) d[l - 1] = Ds[e][N + k * N + l][tx];
+    if (a == N) {
+      t[c] = fmaf(2.0f, f_drow_from<N, DIR>(P, N, d, 0.0f), t[c]);
+    } else if (a > 0) {
+      t[c] = f_drow_from<N, DIR>(P, a, d, t[c]);
+    } else if (k > 0 || has_left) {
+      float dl[N];
+#pragma unroll
+      for (int l = 1; l <= N; ++l) dl[l - 1] = Ds[e][k * N + l][tx];
+      t[c] = f_drow_from<N, DIR>(P, 0, d, t[c]);
+      t[c] = f_drow_from<N, DIR>(P, N, dl, t[c]);
+    } else {
+      t[c] = f_drow_from<N, DIR>(P, 0, d, t[c]);
+      t[c] = f_drow_from<N, DIR>(P, 0, d, t[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
     float f[N + 1];
 #pragma unroll
     for (int l = 0; l <= N; ++l) f[l] = Fs[c][N + k * N + l][tx];
@@ -254,7 +330,7 @@ __host__ __device__ constexpr int f32_tile_segments(int N) { return N >= 8 ? 1 :
 template <int N, int DIR>
 __global__ void __launch_bounds__(kTileCols * (8 + 1), 4) k_f_tline(const FParams P, const FBufs B) {
   constexpr int K = f32_tile_segments(N);
-  __shared__ float Fs[5 * (K * N + N + 1) * kTileCols];
+  __shared__ float Fs[tline_smem_floats(N, K)];
   f_tline_tile<N, DIR, false, K>(P, B, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, Fs);
 }
 

@@ -1,14 +1,15 @@
 // xg_noalloc.cu -- the right-hand side for callers that must not allocate
 // device memory (see xg_rhs_noalloc in include/xg.h).
 //
-// The line kernels need scratch beyond their inputs and outputs: W (v, w, p'
-// per node), T (x + y parts of the tendency), the per-level reference table
+// The line kernels need scratch beyond their inputs and outputs: W (v, w, p',
+// theta per node), T (x + y parts of the tendency), the per-level reference table
 // and the non-finite flag.  A context allocates those with cudaMalloc.  Here
 // they live in one file-scope __device__ array of fixed size instead, so a
 // call allocates nothing: no cudaMalloc, no cudaFree, no allocating library
 // routine.  The array exists once per device that loads this library and
 // stays until the process exits.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -33,6 +34,9 @@ double* g_scratch_addr[kMaxDevices] = {};
 // Device address of g_scratch on the current device.  In host code the name
 // g_scratch is only a host-side stand-in, so the address is looked up once
 // per device with cudaGetSymbolAddress (with that device current) and kept.
+// The kept address belongs to the device's primary context, the one the CUDA
+// runtime uses; it stays valid for the life of the process as long as that
+// context is not destroyed (no cudaDeviceReset of the device between calls).
 xg_status scratch_address(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -92,15 +96,24 @@ extern "C" xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, cons
   if (st != XG_OK) return st;
   if (d->precision != XG_FP64) return XG_ERR_UNSUPPORTED;
   const long long np = geo.np;
+  // the kernels read q (and S_theta) in other CTAs while dqdt is written:
+  // the output must not overlap them (a host-side address comparison)
+  auto overlaps = [](const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+  };
+  const size_t bytes5 = sizeof(double) * 5 * (size_t)np;
+  if (overlaps(q, bytes5, dqdt, bytes5)) return XG_ERR_ARG;
+  if (S_theta && overlaps(S_theta, sizeof(double) * (size_t)np, dqdt, bytes5)) return XG_ERR_ARG;
   const int nz = geo.n[2];
-  const unsigned long long need = 8ull * (unsigned long long)np + 4ull * (unsigned long long)nz +
+  const unsigned long long need = 9ull * (unsigned long long)np + 4ull * (unsigned long long)nz +
                                   kFlagSlots;
   if (need > kScratchDoubles) {
     fprintf(stderr,
             "xg_rhs_noalloc: a mesh of %lld nodes needs %llu bytes of scratch; the static "
             "scratch holds %llu bytes (at most about %llu nodes)\n",
             np, need * 8ull, (unsigned long long)XG_NOALLOC_SCRATCH_BYTES,
-            (unsigned long long)((kScratchDoubles - kFlagSlots) / 8));
+            (unsigned long long)((kScratchDoubles - kFlagSlots) / 9));
     return XG_ERR_UNSUPPORTED;
   }
   double* scratch = nullptr;
@@ -120,9 +133,9 @@ extern "C" xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, cons
   B.q = q;
   B.qn = nullptr;
   B.out = dqdt;
-  B.W = scratch;                       // [3][np]
-  B.T = scratch + 3 * np;              // [5][np]
-  double* base = scratch + 8 * np;     // [4][nz]
+  B.W = scratch;                       // [4][np]
+  B.T = scratch + 4 * np;              // [5][np]
+  double* base = scratch + 9 * np;     // [4][nz]
   B.base = base;
   B.flag = reinterpret_cast<int*>(base + 4 * nz);
   B.S = S_theta;

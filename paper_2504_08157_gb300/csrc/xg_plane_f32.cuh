@@ -78,8 +78,10 @@ struct PlaneTile {
 // The pointwise phase of tile T of level z: the primitives of every node of
 // the cross-shaped region, W = (v, w, p') of the owned nodes, and the fluxes
 // handed to fxs(j, ii, F[5]) (x-fluxes of owned row j at ii = i + N) and
-// fys(jj, i, F[5]) (y-fluxes of owned column i at jj = j + N).
-template <int N, int BATCH, bool CG, typename StoreX, typename StoreY>
+// fys(jj, i, F[5]) (y-fluxes of owned column i at jj = j + N).  With THETA,
+// slot 4 holds theta = Theta / rho instead of the Theta' flux, for the
+// difference form of the contraction (f_drows).
+template <int N, int BATCH, bool CG, bool THETA, typename StoreX, typename StoreY>
 __device__ __forceinline__ void f_plane_pointwise(const FParams& P, const FBufs& B, const PlaneTile& T, int z,
                                                   int tid, int nthr, StoreX fxs, StoreY fys) {
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
@@ -153,12 +155,13 @@ __device__ __forceinline__ void f_plane_pointwise(const FParams& P, const FBufs&
         Wo[np + I] = w;
         Wo[2 * np + I] = pp;
       }
+      const float th = Th * ir;
       if (iny) {                                  // x-fluxes on owned rows
-        const float F[5] = {mu, fmaf(mu, u_, pp), mv * u_, mw * u_, Th * u_};
+        const float F[5] = {mu, fmaf(mu, u_, pp), mv * u_, mw * u_, THETA ? th : Th * u_};
         fxs(j, i + N, F);
       }
       if (inx) {                                  // y-fluxes on owned columns
-        const float F[5] = {mv, mu * v, fmaf(mv, v, pp), mw * v, Th * v};
+        const float F[5] = {mv, mu * v, fmaf(mv, v, pp), mw * v, THETA ? th : Th * v};
         fys(j + N, i, F);
       }
     }
@@ -181,7 +184,7 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
 
   PlaneTile T;
   T.init<N, E>(P, bx, by);
-  f_plane_pointwise<N, BATCH, CG>(
+  f_plane_pointwise<N, BATCH, CG, true>(
       P, B, T, z, tid, nthr,
       [&](int j, int ii, const float (&F)[5]) {
 #pragma unroll
@@ -207,8 +210,51 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
     const long long I = zoff + (x0 + i) + (long long)nx * (y0 + j);
     const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
     const int sy = min(j / N, eky - 1), ay = j - sy * N;
+    {   // rho' and Theta' in difference form (slot 0: rho u_d, slot 4: theta)
+      float m[N + 1], th[N + 1], v0 = 0.0f, v4 = 0.0f, w0 = 0.0f, w4 = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+      for (int l = 0; l <= N; ++l) {
+        m[l] = fx(0, j, N + sx * N + l);
+        th[l] = fx(4, j, N + sx * N + l);
+      }
+      f_drows<N, 0>(P, ax, m, th, v0, v4);
+      if (ax == 0 || ax == N) {
+        if (ax == 0 && (sx > 0 || hxl)) {
+#pragma unroll
+          for (int l = 0; l <= N; ++l) {
+            m[l] = fx(0, j, sx * N + l);
+            th[l] = fx(4, j, sx * N + l);
+          }
+          f_drows<N, 0>(P, N, m, th, v0, v4);
+        } else {
+          v0 = v0 + v0;
+          v4 = v4 + v4;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l <= N; ++l) {
+        m[l] = fy(0, N + sy * N + l, i);
+        th[l] = fy(4, N + sy * N + l, i);
+      }
+      f_drows<N, 1>(P, ay, m, th, w0, w4);
+      if (ay == 0 || ay == N) {
+        if (ay == 0 && (sy > 0 || hyl)) {
+#pragma unroll
+          for (int l = 0; l <= N; ++l) {
+            m[l] = fy(0, sy * N + l, i);
+            th[l] = fy(4, sy * N + l, i);
+          }
+          f_drows<N, 1>(P, N, m, th, w0, w4);
+        } else {
+          w0 = w0 + w0;
+          w4 = w4 + w4;
+        }
+      }
+      To[I] = v0 + w0;
+      To[4 * np + I] = v4 + w4;
+    }
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
       float f[N + 1], v = 0.0f;
 #pragma unroll
       for (int l = 0; l <= N; ++l) f[l] = fx(c, j, N + sx * N + l);

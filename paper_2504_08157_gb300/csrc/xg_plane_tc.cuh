@@ -167,7 +167,7 @@ __device__ __forceinline__ void f_plane_tile_tc(const FParams& P, const FBufs& B
     YH[ln * PT + jj] = 0.0f;
     YL[ln * PT + jj] = 0.0f;
   }
-  f_plane_pointwise<N, kPlaneBatch, CG>(
+  f_plane_pointwise<N, kPlaneBatch, CG, false>(
       P, B, T, z, tid, nthr,
       [&](int j, int ii, const float (&F)[5]) {
 #pragma unroll

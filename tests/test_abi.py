@@ -100,6 +100,20 @@ def test_null_arguments(lib):
     lib.xg_destroy(None)  # no-op
 
 
+def test_noalloc_rejects_an_output_that_overlaps_its_input(lib):
+    """xg_rhs_noalloc compares the addresses of q, S_theta and dqdt on the host
+    and rejects overlapping ranges before any device work (the addresses
+    below are never dereferenced)."""
+    from paper_2504_08157_gb300 import xg
+    d = _desc()
+    nx, ny, nz = [4 * d.nel[k] + (0 if d.periodic[k] else 1) for k in range(3)]
+    vec = 8 * nx * ny * nz
+    q, r0, t0 = 1 << 32, 1 << 33, (1 << 33) + 4096
+    for out, S in ((q, None), (q + 8, None), (q - 4 * vec, None), (q + 5 * vec, q + 5 * vec)):
+        assert lib.xg_rhs_noalloc(ctypes.byref(d), q, r0, t0, S, out, None) == xg.XG_ERR_ARG
+    assert lib.xg_rhs_noalloc(ctypes.byref(d), q, None, t0, None, q + 5 * vec, None) == xg.XG_ERR_ARG
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2504_08157_gb300 import xg
     monkeypatch.setattr(xg, "_lib", None)

@@ -85,6 +85,56 @@ def test_fp32_bubble_rhs_and_200_steps(cuda_device):
     assert np.all(e_inc <= 1e-2), (e_state, e_inc)
 
 
+def _rounded(q):
+    """The FP64 state the FP32 form actually holds."""
+    return q.astype(np.float32).astype(np.float64)
+
+
+def test_fp32_tc_vortex_rhs(cuda_device):
+    """The bench's CPU sample (cyclone box, 16 x 16 x 16 elements) at the
+    pure-vortex state, where the rho' and Theta' tendencies are residuals of
+    cancelling x and y parts.  Rounding the FP64 vortex momentum to FP32
+    alone moves the oracle's own RHS of those two by about 1.2e-5 relative
+    L2 (test_precision_floor), so the bar there is against the oracle of the
+    state the form holds: every variable within 3e-6 of it.  Against the
+    oracle of the FP64 state the momentum tendencies are within 1e-5 and rho'
+    and Theta' within 1.1x that rounding floor."""
+    wl = W.tc(nel=(16, 16, 16))
+    with GpuContext(wl, precision=FP32) as g:
+        got = g.rhs()
+    ref = oracle_rhs(wl)
+    ref32 = oracle_rhs(wl, q=_rounded(wl["q"]))
+    arith = rel_l2_per_var(got, ref32)
+    assert np.all(arith <= 3e-6), arith
+    err = rel_l2_per_var(got, ref)
+    floor = rel_l2_per_var(ref32, ref)
+    assert np.all(err[1:4] <= RHS_TOL32), err
+    assert np.all(err[[0, 4]] <= 1.1 * floor[[0, 4]]), (err, floor)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("contraction", [0, 1], ids=["fma", "tf32x3"])
+def test_fp32_full_size_tc_vortex_rhs_sampled(cuda_device, contraction):
+    """The full cyclone box at the bench's own initial state (pure vortex),
+    sampled nodes, against the oracle of the FP32-rounded state.  At full
+    size the rho' and Theta' residuals are smaller still relative to their
+    cancelling parts than on the 16^3 sample: rounding the state to FP32
+    alone moves them by ~3e-4 and ~1e-4 (test_precision_floor), so the 1e-5
+    bar of the form cannot hold there against the FP64 state.  Against the
+    state the form holds: the momentum tendencies within 1e-5 and rho' and
+    Theta' within 3e-5 for the CUDA-core contraction (difference form), 2e-3
+    for the tensor-core mode, which keeps the plain form of those two
+    contractions (its products read the raw fluxes in place)."""
+    import test_gpu_parity as P
+    wl = W.tc()
+    got, _, (m, phys, base, nodes) = P._full_size_sampled(wl, FP32, contraction)
+    ref32 = E.rhs_at_nodes(m, _rounded(wl["q"]), base, wl["S_theta"], phys, nodes)
+    err = rel_l2_per_var(got, ref32)
+    print("fp32 vortex, contraction", contraction, err)
+    assert np.all(err[1:4] <= RHS_TOL32), err
+    assert np.all(err[[0, 4]] <= (3e-5 if contraction == 0 else 2e-3)), err
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("contraction", [0, 1], ids=["fma", "tf32x3"])
 def test_fp32_full_size_tc_rhs_sampled(cuda_device, contraction):

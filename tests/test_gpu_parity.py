@@ -16,7 +16,8 @@ import pytest
 from inputs import workloads as W
 from oracle import euler as E, lgl, mesh as M
 
-from helpers import GpuContext, oracle_of, oracle_rhs, oracle_steps, rel_l2_per_var
+from helpers import (GpuContext, oracle_of, oracle_rhs, oracle_rhs_at_nodes_extended,
+                     oracle_steps, rel_l2_per_var)
 
 pytestmark = pytest.mark.gpu
 
@@ -176,32 +177,84 @@ def test_full_size_tc_rhs_sampled(cuda_device, prec):
     assert np.all(err <= RHS_TOL), err
 
 
+def df_rounded(q):
+    """The FP64 state as the double-float form holds it (48 significand bits)."""
+    h = q.astype(np.float32).astype(np.float64)
+    return h + (q - h).astype(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def full_tc_vortex_extended(full_tc):
+    """The extended-precision oracle at the full-size sampled nodes, of the
+    FP64 state and of the state rounded to double-float (computed once)."""
+    nodes = _sample_nodes((512, 512, 65), np.random.default_rng(2504), 600)
+    return (oracle_rhs_at_nodes_extended(full_tc, nodes),
+            oracle_rhs_at_nodes_extended(full_tc, nodes, q=df_rounded(full_tc["q"])))
+
+
 @PREC
 @pytest.mark.slow
-def test_full_size_tc_vortex_rhs_sampled(cuda_device, full_tc, prec):
-    """The bench's own initial state (pure vortex).  The momentum tendencies
-    are held to 1e-12.  The vortex is horizontally non-divergent, so the rho'
-    and Theta' tendencies are small residuals of cancelling x and y flux
-    derivatives (residual / terms ~ 1/144 and 1/59 here): for those two the
-    bar is 1e-13 of the magnitude of the cancelling terms, i.e. agreement to
-    FP64 rounding of the terms themselves (relative to the residual it is
-    ~1e-12, the same as two FP64 evaluations in different orders).  Double-
-    float carries 48 significand bits instead of 53 (unit roundoff 32x
-    FP64's), so its bar on those two residuals is 5e-13 of the terms."""
+def test_full_size_tc_vortex_rhs_sampled(cuda_device, full_tc, full_tc_vortex_extended, prec):
+    """The bench's own initial state (pure vortex) at full size, ~600 sampled
+    nodes.  The vortex is horizontally non-divergent, so the rho' and Theta'
+    tendencies are small residuals of cancelling x and y flux derivatives
+    (checked here: the parts are more than 10x the residual).  The kernels
+    take those two contractions in difference form so that their rounding
+    scales with the fluxes' variation, not with the parts; the FP64 oracle's
+    own rounding there is close to 1e-12 (test_oracle_extended), so the
+    reference is the oracle evaluated in extended precision.
+    FP64: every variable within 1e-12 of it.  Double-float: rounding the
+    state to its 48 significand bits alone moves the exact rho' and Theta'
+    tendencies by ~5e-12 here (a property of the stored format, computed
+    below), so it is held to 1e-12 of the exact RHS of the state it holds,
+    and to 1.2x that floor against the FP64 state's."""
     wl = full_tc
+    refx, refx_df = full_tc_vortex_extended
     got, ref, (m, phys, base, nodes) = _full_size_sampled(wl, prec)
-    err = rel_l2_per_var(got, ref)
-    assert np.all(err[1:4] <= RHS_TOL), err
-    qx, qy = wl["q"].copy(), wl["q"].copy()
+    err = rel_l2_per_var(got, refx)
+    if prec == 0:
+        assert np.all(err <= RHS_TOL), err
+    else:
+        arith = rel_l2_per_var(got, refx_df)
+        floor = rel_l2_per_var(refx_df, refx)
+        print("df64 full-size vortex: vs exact", err, "vs its state", arith, "floor", floor)
+        assert np.all(arith <= RHS_TOL), arith
+        assert np.all(err <= np.maximum(1.2 * floor, RHS_TOL)), (err, floor)
+    qx = wl["q"].copy()
     qx[2] = 0.0   # x fluxes of rho' and Theta' only
-    qy[1] = 0.0   # y fluxes only
     rx = E.rhs_at_nodes(m, qx, base, wl["S_theta"], phys, nodes)
-    ry = E.rhs_at_nodes(m, qy, base, wl["S_theta"], phys, nodes)
     for v in (0, 4):
-        terms = np.linalg.norm(rx[v]) + np.linalg.norm(ry[v])
-        assert terms > 10 * np.linalg.norm(ref[v])          # it is a cancellation
-        bar = 1e-13 if prec == 0 else 5e-13
-        assert np.linalg.norm(got[v] - ref[v]) <= bar * terms, (v, err[v])
+        assert np.linalg.norm(rx[v]) > 10 * np.linalg.norm(ref[v])   # it is a cancellation
+
+
+@pytest.fixture(scope="module")
+def tc16_vortex():
+    """The bench's CPU sample at the pure-vortex state: the FP64 oracle over
+    every node and the extended-precision oracle at ~800 sampled nodes."""
+    wl = W.tc(nel=(16, 16, 16))
+    nodes = _sample_nodes((64, 64, 65), np.random.default_rng(16), 800)
+    return wl, oracle_rhs(wl), nodes, oracle_rhs_at_nodes_extended(wl, nodes)
+
+
+@PREC
+def test_rhs_tc_vortex_sample(cuda_device, tc16_vortex, prec):
+    """The cyclone box at 16 x 16 x 16 elements (the bench's CPU sample, the
+    same spacing, order and boundaries) at the pure-vortex state: one RHS
+    within 1e-12 of the whole FP64 oracle, and within 1e-12 of the oracle in
+    extended precision at the sampled nodes."""
+    wl, ref, nodes, refx = tc16_vortex
+    with GpuContext(wl, precision=prec) as g:
+        got = g.rhs()
+    err64 = rel_l2_per_var(got, ref)
+    assert np.all(err64 <= RHS_TOL), err64
+    err = rel_l2_per_var(got[:, nodes], refx)
+    assert np.all(err <= RHS_TOL), err
+
+
+@PREC
+def test_rhs_tc_vortex_sample_random(cuda_device, prec):
+    """The same sample at the vortex plus a seeded smooth perturbation."""
+    _check_rhs(W.tc(nel=(16, 16, 16), state="random"), prec)
 
 
 @PREC
