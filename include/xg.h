@@ -188,6 +188,64 @@ xg_status xg_kernel_times(xg_ctx* ctx, double ms[3], long long launches[3], int 
  * tests can hold it against IEEE division.  Errors: XG_ERR_ARG, XG_ERR_CUDA. */
 xg_status xg_reciprocal(const double* x, double* out, long long n, void* stream);
 
+/* Element partition (Sec. 3.1: non-overlapping element partitions that keep
+ * columns whole; Alg. 3: the partition-face contributions are exchanged once
+ * per right-hand side).  A domain of nel_y elements along y is split into
+ * slabs of consecutive element rows; each slab is an ordinary context whose
+ * mesh description covers its own elements (nel[1] = its rows, lo[1]/hi[1]
+ * its extent, periodic[1] = 0, so its y nodes run from one partition face to
+ * the other, both included).  xg_partition_set marks which of the
+ * context's y ends are partition faces (open_lo: y = lo[1], open_hi: y =
+ * hi[1]; 0 = a no-flux wall as usual, 1 = a partition face) and gives the
+ * caller-owned device buffers of the exchange, each 5 n_x n_z values of 8
+ * bytes in the context's representation ([5][n_z][n_x]; FP64 doubles, or
+ * double-float pairs for XG_DF64).  At a partition face the face node's y
+ * part is the sum of two one-sided rows, one from each slab: the slab above
+ * the face sends (send_lo) its partial value (x part plus its own row), the
+ * slab below sends (send_hi) its row; after each side has received the
+ * other's array (recv_lo from the lower neighbour's send_hi, recv_hi from
+ * the upper neighbour's send_lo) both complete the face node in the same
+ * order as a single domain does, so a partitioned run equals the
+ * single-domain run bit for bit.  A periodic domain is a ring (the first
+ * slab's lower neighbour is the last slab).  Precisions XG_FP64 and XG_DF64
+ * only; not with hyper-diffusion/sponge (xg_set_dynamics) or IMEX
+ * (XG_ERR_UNSUPPORTED).  While any end is open, xg_rhs and xg_step return
+ * XG_ERR_UNSUPPORTED: use xg_partition_stage.  Setting both flags to 0
+ * restores the walled context.  XG_ERR_ARG: a periodic y direction, a NULL
+ * buffer for an open side, flags other than 0/1. */
+xg_status xg_partition_set(xg_ctx* ctx, int open_lo, int open_hi, double* send_lo,
+                           double* recv_lo, double* send_hi, double* recv_hi);
+
+/* One half of a partitioned pass: stage 0, 1, 2 of an SSP-RK3 step of size
+ * dt (as xg_step), or stage -1 for dq/dt into dqdt [5][Np] (as xg_rhs, `where`
+ * says where dqdt lives).  half 0 runs the x and y passes and fills the send
+ * buffers; the caller then exchanges them with the neighbours (recv_lo <-
+ * lower neighbour's send_hi, recv_hi <- upper neighbour's send_lo) on or
+ * after `stream`; half 1 combines the received arrays into the face nodes
+ * and runs the z pass (sources, walls, the stage store).  Half 1 of stage 2
+ * ends the step (the new state becomes current) and, like xg_step,
+ * synchronises once to report XG_ERR_NONFINITE.  The send buffers must stay
+ * unchanged until half 1 of the same stage has been enqueued.  Errors:
+ * XG_ERR_ARG (no open end, half or stage out of range, NULL dqdt for stage
+ * -1), XG_ERR_UNSUPPORTED (dynamics set), XG_ERR_CUDA. */
+xg_status xg_partition_stage(xg_ctx* ctx, int half, int stage, double dt, double* dqdt, int where,
+                             void* stream);
+
+/* Test hook for the equation of state (Sec. 2.1, Eq. 3): p[I] = p' =
+ * p(Theta_0 + Theta') - p(Theta_0) at every node I of the mesh, from
+ * theta_p[I] = Theta' and the reference Theta_0 of node I's level, evaluated
+ * by the same device code and in the same arithmetic as the context's
+ * kernels (theta_p is first converted to the context's precision, as
+ * xg_set_state converts the state).  Those kernels use a binomial series of
+ * (1 + x)^gamma - 1, x = Theta'/Theta_0, for |x| < x_max and
+ * expm1(gamma log1p(x)) beyond; *x_max (if x_max is not NULL) receives the
+ * switch point (in the FP32 and double-float forms the test is applied to
+ * x rounded to float).  theta_p and p are caller-owned device arrays of Np
+ * FP64 values; the call is asynchronous on the stream.  XG_ERR_ARG for NULL
+ * arrays or a context without a reference state. */
+xg_status xg_pressure_perturbation(const xg_ctx* ctx, const double* theta_p, double* p,
+                                   double* x_max, void* stream);
+
 /* Free every buffer of the context (synchronises the device first).  NULL
  * is a no-op. */
 void xg_destroy(xg_ctx* ctx);
@@ -205,19 +263,24 @@ void xg_destroy(xg_ctx* ctx);
  *
  * The caller passes every input and output as device memory of the current
  * device: q [5][Np], rho0 and rhotheta0 [n_z], S_theta [Np] (NULL = no
- * heating), dqdt [5][Np] (layouts as above).  The intermediate arrays the
+ * heating), dqdt [5][Np] (layouts as above); dqdt must not overlap q or
+ * S_theta (XG_ERR_ARG: other thread blocks still read them while it is
+ * written).  The intermediate arrays the
  * kernels need live in one fixed array of XG_NOALLOC_SCRATCH_BYTES per
  * device, which every device that loads this library keeps until the
- * process exits; meshes whose 8 Np + 4 n_z + 32 doubles do not fit (about
- * 262,000 nodes) are rejected with XG_ERR_UNSUPPORTED and a message on
+ * process exits; meshes whose 9 Np + 4 n_z + 32 doubles do not fit (about
+ * 233,000 nodes) are rejected with XG_ERR_UNSUPPORTED and a message on
  * stderr.  The first call on a device looks up that array's device address
  * (once per device, with the device current); make that first call before
- * any stream capture.  All calls share the array and it keeps the last
+ * any stream capture.  The address found belongs to the device's primary
+ * context (the CUDA runtime's) and is kept for the life of the process: do
+ * not call this entry point on a device after a cudaDeviceReset of it.  All calls share the array and it keeps the last
  * call's contents, so calls that overlap on the GPU (different streams or
  * threads) race: serialise them.  Work is enqueued on `stream` and the call
  * returns without waiting; the reference values must be positive (this
  * entry point cannot check device data without waiting for it).
- * Errors: XG_ERR_ARG (NULL pointer, invalid description), XG_ERR_UNSUPPORTED
+ * Errors: XG_ERR_ARG (NULL pointer, invalid description, dqdt overlapping
+ * q or S_theta), XG_ERR_UNSUPPORTED
  * (mesh too large for the scratch, a precision other than XG_FP64, or a
  * description this build cannot run), XG_ERR_CUDA. */
 xg_status xg_rhs_noalloc(const xg_mesh_desc* d, const double* q, const double* rho0,

@@ -42,6 +42,78 @@ __global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ o
     out[i] = xg::rcp_newton(x[i]);
 }
 
+// Equation-of-state self-check: p' of Eq. 3 at every node from Theta' (FP64
+// values, converted as the state is) and the node level's reference values,
+// through the device function each precision's kernels call.
+__global__ void k_eos_check_fp64(const xg::LineParams P, const double* __restrict__ base,
+                                 const double* __restrict__ tp, double* __restrict__ out,
+                                 long long np, long long nxy, int nz) {
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < np;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(I / nxy);
+    out[I] = base[2 * nz + z] * xg::eos_phi(P, tp[I] * base[3 * nz + z]);
+  }
+}
+
+__global__ void k_eos_check_df(const xg::DfParams P, const xg::df* __restrict__ base,
+                               const double* __restrict__ tp, double* __restrict__ out,
+                               long long np, long long nxy, int nz) {
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < np;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(I / nxy);
+    const xg::df x = xg::df_mul(xg::df_from_double(tp[I]), base[3 * nz + z]);
+    out[I] = xg::df_to_double(xg::df_mul(base[2 * nz + z], xg::df_eos_phi(P, x)));
+  }
+}
+
+__global__ void k_eos_check_f32(const xg::FParams P, const xg::df* __restrict__ base,
+                                const double* __restrict__ tp, double* __restrict__ out,
+                                long long np, long long nxy, int nz) {
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < np;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int z = (int)(I / nxy);
+    out[I] = (double)xg::f_pressure_pert(P, __double2float_rn(tp[I]), base[2 * nz + z], base[3 * nz + z]);
+  }
+}
+
+// Partition faces (values of 8 bytes: FP64 or double-float pairs).  Face
+// arrays are [5][n_z][n_x].  pack: the slab's first y plane of T (x part
+// plus row 0 of the first y segment) into out.  combine: the first plane
+// gets the left neighbour's row N (t0 + carry, the order of k_line_y at a
+// shared face), the last plane the right neighbour's t0 plus this slab's own
+// row N -- so both slabs hold bit for bit the value a single domain has.
+template <typename V>
+__global__ void k_face_pack(const V* __restrict__ T, V* __restrict__ out, int nx, int ny, int nz,
+                            long long np) {
+  const long long nf = (long long)nx * nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 5 * nf;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k / nf);
+    const long long r = k - c * nf;
+    const int z = (int)(r / nx), x = (int)(r - (long long)z * nx);
+    out[k] = T[c * np + x + (long long)nx * ny * z];
+  }
+}
+
+__device__ __forceinline__ double face_add(double a, double b) { return a + b; }
+__device__ __forceinline__ xg::df face_add(xg::df a, xg::df b) { return xg::df_add(a, b); }
+
+template <typename V>
+__global__ void k_face_combine(V* __restrict__ T, const V* __restrict__ recv_lo,
+                               const V* __restrict__ recv_hi, const V* __restrict__ own_hi,
+                               int nx, int ny, int nz, long long np) {
+  const long long nf = (long long)nx * nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 5 * nf;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k / nf);
+    const long long r = k - c * nf;
+    const int z = (int)(r / nx), x = (int)(r - (long long)z * nx);
+    const long long I0 = c * np + x + (long long)nx * ny * z;
+    if (recv_lo) T[I0] = face_add(T[I0], recv_lo[k]);
+    if (recv_hi) T[I0 + (long long)nx * (ny - 1)] = face_add(recv_hi[k], own_hi[k]);
+  }
+}
+
 }  // namespace
 
 namespace xg {
@@ -156,20 +228,26 @@ void prof_fold(xg_ctx* c) {
   c->ev_used = 0;
 }
 
+// parts: bit 0 the x and y passes, bit 1 the z pass (a partitioned stage
+// exchanges the partition faces' rows in between)
 template <int N>
-void launch_stage_n(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
-  dim3 gx(c->n[1], c->n[2]);
-  prof_mark(c, 0, false, st);
-  xg::k_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->P, B);
-  prof_mark(c, 0, true, st);
-  dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
-  prof_mark(c, 1, false, st);
-  xg::k_line_y<N><<<gy, 128, 0, st>>>(c->P, B, c->chunk_y);
-  prof_mark(c, 1, true, st);
-  dim3 gz((c->n[0] + 127) / 128, c->nchunk_z, c->n[1]);
-  prof_mark(c, 2, false, st);
-  xg::k_line_z<N><<<gz, 128, 0, st>>>(c->P, B, c->chunk_z);
-  prof_mark(c, 2, true, st);
+void launch_stage_n(xg_ctx* c, const StageBufs& B, cudaStream_t st, int parts) {
+  if (parts & 1) {
+    dim3 gx(c->n[1], c->n[2]);
+    prof_mark(c, 0, false, st);
+    xg::k_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->P, B);
+    prof_mark(c, 0, true, st);
+    dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
+    prof_mark(c, 1, false, st);
+    xg::k_line_y<N><<<gy, 128, 0, st>>>(c->P, B, c->chunk_y);
+    prof_mark(c, 1, true, st);
+  }
+  if (parts & 2) {
+    dim3 gz((c->n[0] + 127) / 128, c->nchunk_z, c->n[1]);
+    prof_mark(c, 2, false, st);
+    xg::k_line_z<N><<<gz, 128, 0, st>>>(c->P, B, c->chunk_z);
+    prof_mark(c, 2, true, st);
+  }
 }
 
 template <int N>
@@ -183,22 +261,26 @@ cudaError_t configure_n(xg_ctx* c) {
 }
 
 template <int N>
-void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
-  dim3 gx(c->n[1], c->n[2]);
-  prof_mark(c, 0, false, st);
-  xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
-  prof_mark(c, 0, true, st);
-  constexpr int K = xg::df_tile_segments(N);
-  const dim3 blk(xg::kTileCols, K * N + 1);
-  const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
-  dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
-  prof_mark(c, 1, false, st);
-  xg::k_df_line_y<N><<<gy, 128, 0, st>>>(c->Pdf, B, c->chunk_y);
-  prof_mark(c, 1, true, st);
-  dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);
-  prof_mark(c, 2, false, st);
-  xg::k_df_tline<N, 2><<<gz, blk, 0, st>>>(c->Pdf, B);
-  prof_mark(c, 2, true, st);
+void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
+  if (parts & 1) {
+    dim3 gx(c->n[1], c->n[2]);
+    prof_mark(c, 0, false, st);
+    xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
+    prof_mark(c, 0, true, st);
+    dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
+    prof_mark(c, 1, false, st);
+    xg::k_df_line_y<N><<<gy, 128, 0, st>>>(c->Pdf, B, c->chunk_y);
+    prof_mark(c, 1, true, st);
+  }
+  if (parts & 2) {
+    constexpr int K = xg::df_tile_segments(N);
+    const dim3 blk(xg::kTileCols, K * N + 1);
+    const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
+    dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);
+    prof_mark(c, 2, false, st);
+    xg::k_df_tline<N, 2><<<gz, blk, 0, st>>>(c->Pdf, B);
+    prof_mark(c, 2, true, st);
+  }
 }
 
 template <int N>
@@ -238,31 +320,31 @@ cudaError_t launch_f32_stage(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_df_stage(xg_ctx* c, const DfBufs& B, cudaStream_t st) {
+cudaError_t launch_df_stage(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
   switch (c->d.order) {
-    case 1: launch_df_stage_n<1>(c, B, st); break;
-    case 2: launch_df_stage_n<2>(c, B, st); break;
-    case 3: launch_df_stage_n<3>(c, B, st); break;
-    case 4: launch_df_stage_n<4>(c, B, st); break;
-    case 5: launch_df_stage_n<5>(c, B, st); break;
-    case 6: launch_df_stage_n<6>(c, B, st); break;
-    case 7: launch_df_stage_n<7>(c, B, st); break;
-    case 8: launch_df_stage_n<8>(c, B, st); break;
+    case 1: launch_df_stage_n<1>(c, B, st, parts); break;
+    case 2: launch_df_stage_n<2>(c, B, st, parts); break;
+    case 3: launch_df_stage_n<3>(c, B, st, parts); break;
+    case 4: launch_df_stage_n<4>(c, B, st, parts); break;
+    case 5: launch_df_stage_n<5>(c, B, st, parts); break;
+    case 6: launch_df_stage_n<6>(c, B, st, parts); break;
+    case 7: launch_df_stage_n<7>(c, B, st, parts); break;
+    case 8: launch_df_stage_n<8>(c, B, st, parts); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(xg_ctx* c, const StageBufs& B, cudaStream_t st) {
+cudaError_t launch_stage(xg_ctx* c, const StageBufs& B, cudaStream_t st, int parts) {
   switch (c->d.order) {
-    case 1: launch_stage_n<1>(c, B, st); break;
-    case 2: launch_stage_n<2>(c, B, st); break;
-    case 3: launch_stage_n<3>(c, B, st); break;
-    case 4: launch_stage_n<4>(c, B, st); break;
-    case 5: launch_stage_n<5>(c, B, st); break;
-    case 6: launch_stage_n<6>(c, B, st); break;
-    case 7: launch_stage_n<7>(c, B, st); break;
-    case 8: launch_stage_n<8>(c, B, st); break;
+    case 1: launch_stage_n<1>(c, B, st, parts); break;
+    case 2: launch_stage_n<2>(c, B, st, parts); break;
+    case 3: launch_stage_n<3>(c, B, st, parts); break;
+    case 4: launch_stage_n<4>(c, B, st, parts); break;
+    case 5: launch_stage_n<5>(c, B, st, parts); break;
+    case 6: launch_stage_n<6>(c, B, st, parts); break;
+    case 7: launch_stage_n<7>(c, B, st, parts); break;
+    case 8: launch_stage_n<8>(c, B, st, parts); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -297,6 +379,7 @@ StageBufs make_bufs(xg_ctx* c, const double* q, const double* qn, double* out, d
   B.alpha = alpha;
   B.beta = beta;
   B.rhs_only = rhs_only;
+  B.face_hi = c->part_send[1];
   return B;
 }
 
@@ -304,7 +387,7 @@ StageBufs make_bufs(xg_ctx* c, const double* q, const double* qn, double* out, d
 // or combined as out = alpha qn + beta (q + dt L(q)).  Buffers are device
 // arrays of the context's precision.
 cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, double dt,
-                      double alpha, double beta, int rhs_only, cudaStream_t st) {
+                      double alpha, double beta, int rhs_only, cudaStream_t st, int parts = 3) {
   if (c->f32) {
     xg::FBufs F;
     F.C = nullptr;
@@ -335,7 +418,7 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
       if (e != cudaSuccess) return e;
       B.E = c->dyn_E;
     }
-    return launch_stage(c, B, st);
+    return launch_stage(c, B, st, parts);
   }
   DfBufs B;
   B.q = (const df*)q;
@@ -351,7 +434,8 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
   B.beta = xg::split_df(beta);
   B.bdt = xg::split_df((double)((long double)beta * (long double)dt));
   B.rhs_only = rhs_only;
-  return launch_df_stage(c, B, st);
+  B.face_hi = (df*)c->part_send[1];
+  return launch_df_stage(c, B, st, parts);
 }
 
 // Device FP64 array -> the context's device representation (n values).
@@ -429,7 +513,7 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
 
   const size_t vec = sizeof(double) * (size_t)np;
   struct { double** p; size_t bytes; } allocs[] = {
-      {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->Dq, 5 * vec}, {&c->W, 3 * vec},
+      {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->Dq, 5 * vec}, {&c->W, 4 * vec},
       {&c->T, 5 * vec}, {&c->S, vec}, {&c->base, sizeof(double) * 4 * (size_t)n[2]}};
   for (auto& a : allocs) {
     e = cudaMalloc((void**)a.p, a.bytes);
@@ -569,6 +653,7 @@ xg_status xg_set_forcing(xg_ctx* c, const double* S, int where, void* stream) {
 xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c || !dqdt) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
+  if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // xg_partition_stage
   if (where != XG_HOST && where != XG_DEVICE) return XG_ERR_ARG;
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -601,6 +686,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
 xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   if (!c) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
+  if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // xg_partition_stage
   if (!std::isfinite(dt) || nsteps < 0) return XG_ERR_ARG;
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -674,6 +760,111 @@ xg_status xg_reciprocal(const double* x, double* out, long long n, void* stream)
   k_rcp_check<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, out, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(nullptr, e, "xg_reciprocal");
+  return XG_OK;
+}
+
+xg_status xg_partition_set(xg_ctx* c, int open_lo, int open_hi, double* send_lo, double* recv_lo,
+                           double* send_hi, double* recv_hi) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if ((open_lo != 0 && open_lo != 1) || (open_hi != 0 && open_hi != 1)) return XG_ERR_ARG;
+  if ((open_lo || open_hi) && c->d.periodic[1]) return XG_ERR_ARG;
+  if (open_lo && (!send_lo || !recv_lo)) return XG_ERR_ARG;
+  if (open_hi && (!send_hi || !recv_hi)) return XG_ERR_ARG;
+  if ((open_lo || open_hi) && (c->f32 || c->dyn || c->closure)) return XG_ERR_UNSUPPORTED;
+  c->part_open[0] = open_lo;
+  c->part_open[1] = open_hi;
+  c->part_send[0] = open_lo ? send_lo : nullptr;
+  c->part_recv[0] = open_lo ? recv_lo : nullptr;
+  c->part_send[1] = open_hi ? send_hi : nullptr;
+  c->part_recv[1] = open_hi ? recv_hi : nullptr;
+  c->P.open_y[0] = c->Pdf.open_y[0] = open_lo;
+  c->P.open_y[1] = c->Pdf.open_y[1] = open_hi;
+  return XG_OK;
+}
+
+xg_status xg_partition_stage(xg_ctx* c, int half, int stage, double dt, double* dqdt, int where,
+                             void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!c->part_open[0] && !c->part_open[1]) return XG_ERR_ARG;
+  if ((half != 0 && half != 1) || stage < -1 || stage > 2 || !std::isfinite(dt)) return XG_ERR_ARG;
+  if (stage < 0 && half == 1 && (!dqdt || (where != XG_HOST && where != XG_DEVICE))) return XG_ERR_ARG;
+  if (!c->has_state) return XG_ERR_ARG;
+  if (c->dyn) return XG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the stage's buffers, as in xg_step / xg_rhs
+  const void* q = c->A;
+  const void* qn = nullptr;
+  void* out = c->Bq;
+  double alpha = 0.0, beta = 1.0;
+  if (stage == 1) { q = c->Bq; qn = c->A; out = c->Cq; alpha = 0.75; beta = 0.25; }
+  if (stage == 2) { q = c->Cq; qn = c->A; out = c->Dq; alpha = 1.0 / 3.0; beta = 2.0 / 3.0; }
+  if (stage < 0) out = c->dfm ? (void*)c->Cq : (where == XG_DEVICE ? (void*)dqdt : (void*)c->Bq);
+  const int rhs = stage < 0 ? 1 : 0;
+  const long long nf5 = 5ll * c->n[0] * c->n[2];
+  const unsigned g = conv_blocks(nf5);
+  if (half == 0) {
+    if (stage <= 0) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    XG_CUDA(c, run_stage(c, q, qn, out, rhs ? 0.0 : dt, alpha, beta, rhs, st, 1));
+    if (c->part_open[0]) {
+      if (c->dfm)
+        k_face_pack<df><<<g, 256, 0, st>>>((const df*)c->T, (df*)c->part_send[0], c->n[0], c->n[1],
+                                           c->n[2], c->np);
+      else
+        k_face_pack<double><<<g, 256, 0, st>>>(c->T, c->part_send[0], c->n[0], c->n[1], c->n[2], c->np);
+      XG_CUDA(c, cudaGetLastError());
+    }
+    return XG_OK;
+  }
+  if (c->dfm)
+    k_face_combine<df><<<g, 256, 0, st>>>((df*)c->T, (const df*)c->part_recv[0],
+                                          (const df*)c->part_recv[1], (const df*)c->part_send[1],
+                                          c->n[0], c->n[1], c->n[2], c->np);
+  else
+    k_face_combine<double><<<g, 256, 0, st>>>(c->T, c->part_recv[0], c->part_recv[1], c->part_send[1],
+                                              c->n[0], c->n[1], c->n[2], c->np);
+  XG_CUDA(c, cudaGetLastError());
+  XG_CUDA(c, run_stage(c, q, qn, out, rhs ? 0.0 : dt, alpha, beta, rhs, st, 2));
+  if (stage < 0) {
+    double* dst = where == XG_DEVICE ? dqdt : c->Bq;
+    if (c->dfm) XG_CUDA(c, export_values(c, c->Cq, dst, 5 * c->np, st));
+    if (where == XG_HOST) {
+      XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
+                                 cudaMemcpyDeviceToHost, st));
+      XG_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return XG_OK;
+  }
+  if (stage == 2) {
+    double* t = c->A;
+    c->A = c->Dq;
+    c->Dq = t;
+    XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XG_CUDA(c, cudaStreamSynchronize(st));
+    prof_fold(c);
+    return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
+  }
+  return XG_OK;
+}
+
+xg_status xg_pressure_perturbation(const xg_ctx* c, const double* theta_p, double* p,
+                                   double* x_max, void* stream) {
+  if (!c || !theta_p || !p) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!c->has_base) return XG_ERR_ARG;
+  if (x_max) *x_max = c->P.eos_xmax;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nxy = (long long)c->n[0] * c->n[1];
+  const unsigned g = conv_blocks(c->np);
+  if (c->f32)
+    k_eos_check_f32<<<g, 256, 0, st>>>(c->Pf, (const df*)c->base, theta_p, p, c->np, nxy, c->n[2]);
+  else if (c->dfm)
+    k_eos_check_df<<<g, 256, 0, st>>>(c->Pdf, (const df*)c->base, theta_p, p, c->np, nxy, c->n[2]);
+  else
+    k_eos_check_fp64<<<g, 256, 0, st>>>(c->P, c->base, theta_p, p, c->np, nxy, c->n[2]);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(const_cast<xg_ctx*>(c), e, "xg_pressure_perturbation");
   return XG_OK;
 }
 

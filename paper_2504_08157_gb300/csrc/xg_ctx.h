@@ -28,7 +28,7 @@ struct xg_ctx {
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer
   double* Dq = nullptr;  // q^{n+1}; swapped with A after every step
-  double* W = nullptr;   // [3][np] primitives v, w, p'
+  double* W = nullptr;   // [4][np] primitives v, w, p', theta (FP32: [3][np])
   double* T = nullptr;   // [5][np] partial tendency
   double* S = nullptr;   // [np] heating
   double* base = nullptr;  // [4][nz]
@@ -65,6 +65,12 @@ struct xg_ctx {
   double* dyn_gamma = nullptr;   // [n_z] sponge rate per level
   // IMEX work arrays (xg_imex.cu), allocated on first use
   void* imex = nullptr;
+  // element partition along y (xg_partition_set): which y ends are
+  // partition faces, and the caller's face buffers [5][n_z][n_x] (8-byte
+  // values) sent to / received from the neighbours on those sides
+  int part_open[2] = {0, 0};
+  double* part_send[2] = {nullptr, nullptr};
+  double* part_recv[2] = {nullptr, nullptr};
 };
 
 void imex_free(xg_ctx* c);

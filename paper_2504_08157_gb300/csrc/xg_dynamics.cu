@@ -278,6 +278,7 @@ xg_status xg_set_dynamics(xg_ctx* c, const xg_dynamics* dyn) {
     return XG_OK;
   }
   if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // partitioned contexts
   const double H = c->d.hi[2] - c->d.lo[2];
   bool hyper = false;
   for (int k = 0; k < 3; ++k) {

@@ -533,6 +533,7 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
   if (!c) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
   if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // partitioned: explicit only
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !c->has_state) return XG_ERR_ARG;
   double tol = 1e-10;
   int m = 20, maxrs = 50;

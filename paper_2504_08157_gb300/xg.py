@@ -29,7 +29,8 @@ XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5,
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_set_contraction", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_diagnostics", "xg_destroy", "library",
+           "xg_step", "xg_get_state", "xg_set_contraction", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_pressure_perturbation", "xg_partition_set",
+           "xg_partition_stage", "xg_diagnostics", "xg_destroy", "library",
            "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
            "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
            "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
@@ -128,6 +129,12 @@ def library():
     lib.xg_rhs_noalloc.argtypes = [ctypes.POINTER(xg_mesh_desc), P, P, P, P, P, P]
     lib.xg_reciprocal.restype = I
     lib.xg_reciprocal.argtypes = [P, P, LL, P]
+    lib.xg_partition_set.restype = I
+    lib.xg_partition_set.argtypes = [P, I, I, P, P, P, P]
+    lib.xg_partition_stage.restype = I
+    lib.xg_partition_stage.argtypes = [P, I, I, D, P, I, P]
+    lib.xg_pressure_perturbation.restype = I
+    lib.xg_pressure_perturbation.argtypes = [P, P, P, ctypes.POINTER(D), P]
     lib.xg_diagnostics.restype = I
     lib.xg_diagnostics.argtypes = [P, ctypes.POINTER(D), P]
     lib.xg_destroy.restype = None
@@ -339,6 +346,46 @@ def xg_reciprocal(x, out, stream=None):
         raise ValueError("xg_reciprocal takes device arrays")
     n = x.numel() if hasattr(x, "numel") else len(x)
     _check(library().xg_reciprocal(px, po, int(n), _stream(stream, sx)), "xg_reciprocal")
+
+
+def xg_partition_set(ctx, open_lo, open_hi, send_lo=None, recv_lo=None, send_hi=None, recv_hi=None):
+    """Mark the context's y ends as partition faces and give the exchange
+    buffers (device arrays of 5 n_x n_z values of 8 bytes each, owned by the
+    caller and kept alive while the partition is set)."""
+    ptrs = []
+    for a in (send_lo, recv_lo, send_hi, recv_hi):
+        if a is None:
+            ptrs.append(None)
+            continue
+        p, w, _ = _ptr(a, writable=True)
+        if w != XG_DEVICE:
+            raise ValueError("partition face buffers must be device arrays")
+        ptrs.append(p)
+    _check(library().xg_partition_set(ctx, int(open_lo), int(open_hi), *ptrs), "xg_partition_set")
+
+
+def xg_partition_stage(ctx, half, stage, dt=0.0, dqdt=None, stream=None):
+    """One half of a partitioned stage (stage 0..2 of an SSP-RK3 step, or -1
+    for dq/dt into dqdt)."""
+    pd, wd, sd = _ptr(dqdt, writable=True)
+    st = _stream(stream, sd) if (stream is not None or sd is not None) else _default_stream(None)
+    _check(library().xg_partition_stage(ctx, int(half), int(stage), float(dt), pd,
+                                        XG_DEVICE if wd is None else wd, st),
+           "xg_partition_stage")
+
+
+def xg_pressure_perturbation(ctx, theta_p, out, stream=None):
+    """p' of Eq. 3 at every node from Theta' (device arrays of Np values),
+    through the context's own equation-of-state code (test hook); returns the
+    series/fallback switch point x_max."""
+    pt, wt, st = _ptr(theta_p)
+    po, wo, _ = _ptr(out, writable=True)
+    if wt != XG_DEVICE or wo != XG_DEVICE:
+        raise ValueError("xg_pressure_perturbation takes device arrays")
+    xm = ctypes.c_double(0.0)
+    _check(library().xg_pressure_perturbation(ctx, pt, po, ctypes.byref(xm), _stream(stream, st)),
+           "xg_pressure_perturbation")
+    return xm.value
 
 
 def xg_diagnostics(ctx, stream=None):
