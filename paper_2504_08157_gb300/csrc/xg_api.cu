@@ -61,7 +61,7 @@ __global__ void k_eos_check_df(const xg::DfParams P, const xg::df* __restrict__ 
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < np;
        I += (long long)gridDim.x * blockDim.x) {
     const int z = (int)(I / nxy);
-    const xg::df x = xg::df_mul(xg::df_from_double(tp[I]), base[3 * nz + z]);
+    const xg::df x = xg::df_mul(xg::df_of_double(tp[I]), base[3 * nz + z]);
     out[I] = xg::df_to_double(xg::df_mul(base[2 * nz + z], xg::df_eos_phi(P, x)));
   }
 }
@@ -95,12 +95,10 @@ __global__ void k_face_pack(const V* __restrict__ T, V* __restrict__ out, int nx
   }
 }
 
-__device__ __forceinline__ double face_add(double a, double b) { return a + b; }
-__device__ __forceinline__ xg::df face_add(xg::df a, xg::df b) { return xg::df_add(a, b); }
-
-template <typename V>
-__global__ void k_face_combine(V* __restrict__ T, const V* __restrict__ recv_lo,
-                               const V* __restrict__ recv_hi, const V* __restrict__ own_hi,
+// MIXED: slots 0 and 4 hold doubles and 1..3 double-float pairs (XG_DF64)
+template <bool MIXED>
+__global__ void k_face_combine(double* __restrict__ T, const double* __restrict__ recv_lo,
+                               const double* __restrict__ recv_hi, const double* __restrict__ own_hi,
                                int nx, int ny, int nz, long long np) {
   const long long nf = (long long)nx * nz;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 5 * nf;
@@ -109,24 +107,22 @@ __global__ void k_face_combine(V* __restrict__ T, const V* __restrict__ recv_lo,
     const long long r = k - c * nf;
     const int z = (int)(r / nx), x = (int)(r - (long long)z * nx);
     const long long I0 = c * np + x + (long long)nx * ny * z;
-    if (recv_lo) T[I0] = face_add(T[I0], recv_lo[k]);
-    if (recv_hi) T[I0 + (long long)nx * (ny - 1)] = face_add(recv_hi[k], own_hi[k]);
+    const long long I1 = I0 + (long long)nx * (ny - 1);
+    if (MIXED && c != 0 && c != 4) {
+      xg::df* Tm = reinterpret_cast<xg::df*>(T);
+      if (recv_lo) Tm[I0] = xg::df_add(Tm[I0], reinterpret_cast<const xg::df*>(recv_lo)[k]);
+      if (recv_hi)
+        Tm[I1] = xg::df_add(reinterpret_cast<const xg::df*>(recv_hi)[k], reinterpret_cast<const xg::df*>(own_hi)[k]);
+    } else {
+      if (recv_lo) T[I0] = T[I0] + recv_lo[k];
+      if (recv_hi) T[I1] = recv_hi[k] + own_hi[k];
+    }
   }
 }
 
 }  // namespace
 
 namespace xg {
-__global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = df_from_double(in[i]);
-}
-__global__ void k_from_df(const df* __restrict__ in, double* __restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = df_to_double(in[i]);
-}
 __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -421,32 +417,37 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
     return launch_stage(c, B, st, parts);
   }
   DfBufs B;
-  B.q = (const df*)q;
-  B.qn = (const df*)qn;
-  B.out = (df*)out;
+  B.q = (const double*)q;
+  B.qn = (const double*)qn;
+  B.out = (double*)out;
   B.W = (df*)c->W;
-  B.T = (df*)c->T;
-  B.S = c->has_forcing ? (const df*)c->S : nullptr;
+  B.W64 = c->W + 3 * c->np;
+  B.T = c->T;
+  B.Tm = (df*)c->T;
+  B.S = c->has_forcing ? c->S : nullptr;
   B.base = (const df*)c->base;
+  B.base64 = c->base64;
   B.flag = c->flag;
   B.dt = xg::split_df(dt);
   B.alpha = xg::split_df(alpha);
   B.beta = xg::split_df(beta);
   B.bdt = xg::split_df((double)((long double)beta * (long double)dt));
+  B.dt64 = dt;
+  B.alpha64 = alpha;
+  B.beta64 = beta;
   B.rhs_only = rhs_only;
-  B.face_hi = (df*)c->part_send[1];
+  B.face_hi = c->part_send[1];
   return launch_df_stage(c, B, st, parts);
 }
 
-// Device FP64 array -> the context's device representation (n values).
+// Device FP64 array -> the context's device representation (n values; FP64
+// and XG_DF64 contexts hold FP64 arrays).
 cudaError_t import_values(xg_ctx* c, const double* src, void* dst, long long n, cudaStream_t st) {
   if (c->f32) {
     xg::k_to_f32<<<conv_blocks(n), 256, 0, st>>>(src, (float*)dst, n);
     return cudaGetLastError();
   }
-  if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-  xg::k_to_df<<<conv_blocks(n), 256, 0, st>>>(src, (df*)dst, n);
-  return cudaGetLastError();
+  return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
 }
 
 // The context's device representation -> device FP64 array.
@@ -455,9 +456,7 @@ cudaError_t export_values(xg_ctx* c, const void* src, double* dst, long long n, 
     xg::k_from_f32<<<conv_blocks(n), 256, 0, st>>>((const float*)src, dst, n);
     return cudaGetLastError();
   }
-  if (!c->dfm) return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-  xg::k_from_df<<<conv_blocks(n), 256, 0, st>>>((const df*)src, dst, n);
-  return cudaGetLastError();
+  return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace
@@ -514,7 +513,8 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
   const size_t vec = sizeof(double) * (size_t)np;
   struct { double** p; size_t bytes; } allocs[] = {
       {&c->A, 5 * vec}, {&c->Bq, 5 * vec}, {&c->Cq, 5 * vec}, {&c->Dq, 5 * vec}, {&c->W, 4 * vec},
-      {&c->T, 5 * vec}, {&c->S, vec}, {&c->base, sizeof(double) * 4 * (size_t)n[2]}};
+      {&c->T, 5 * vec}, {&c->S, vec}, {&c->base, sizeof(double) * 4 * (size_t)n[2]},
+      {&c->base64, sizeof(double) * 4 * (size_t)n[2]}};
   for (auto& a : allocs) {
     e = cudaMalloc((void**)a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -602,20 +602,24 @@ xg_status xg_set_state(xg_ctx* c, const double* q, const double* rho0, const dou
       hb[2 * nz + k] = c->d.p_a * pow(c->d.R * t0[k] / c->d.p_a, gamma);  // Eq. 3
       hb[3 * nz + k] = 1.0 / t0[k];
     }
-    if (c->dfm || c->f32) {  // the table as double-float pairs (8 bytes each, in place)
+    // the FP64 table (the rho' and Theta' path of XG_DF64), then for the
+    // double-float and FP32 kernels the table as pairs (8 bytes each, in place)
+    cudaError_t e = cudaMemcpyAsync(c->base64, hb, sizeof(double) * 4 * nz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (c->dfm || c->f32) {
       for (int k = 0; k < 4 * nz; ++k) {
         const df v = xg::split_df(hb[k]);
         memcpy(hb + k, &v, sizeof(df));
       }
     }
-    cudaError_t e = cudaMemcpyAsync(c->base, hb, sizeof(double) * 4 * nz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->base, hb, sizeof(double) * 4 * nz, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     free(hb);
     if (e != cudaSuccess) return fail_cuda(c, e, "xg_set_state reference upload");
     c->has_base = true;
   }
   const long long n5 = 5 * c->np;
-  if (!c->dfm && !c->f32) {
+  if (!c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(c->A, q, sizeof(double) * (size_t)n5,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else if (where == XG_DEVICE) {
@@ -637,7 +641,7 @@ xg_status xg_set_forcing(xg_ctx* c, const double* S, int where, void* stream) {
     c->has_forcing = false;
     return XG_OK;
   }
-  if (!c->dfm && !c->f32) {
+  if (!c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(c->S, S, sizeof(double) * (size_t)c->np,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else if (where == XG_DEVICE) {
@@ -660,7 +664,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
   const bool tc_waits = c->closure || c->contract != XG_CONTRACT_FMA;   // kernels with bounded waits
   if (tc_waits) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
-  if (!c->dfm && !c->f32) {
+  if (!c->f32) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
   } else {
     XG_CUDA(c, run_stage(c, c->A, nullptr, c->Cq, 0.0, 0.0, 1.0, 1, st));
@@ -713,7 +717,7 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const long long n5 = 5 * c->np;
-  if (!c->dfm && !c->f32) {
+  if (!c->f32) {
     XG_CUDA(c, cudaMemcpyAsync(q, c->A, sizeof(double) * (size_t)n5,
                                where == XG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   } else if (where == XG_DEVICE) {
@@ -778,8 +782,8 @@ xg_status xg_partition_set(xg_ctx* c, int open_lo, int open_hi, double* send_lo,
   c->part_recv[0] = open_lo ? recv_lo : nullptr;
   c->part_send[1] = open_hi ? send_hi : nullptr;
   c->part_recv[1] = open_hi ? recv_hi : nullptr;
-  c->P.open_y[0] = c->Pdf.open_y[0] = open_lo;
-  c->P.open_y[1] = c->Pdf.open_y[1] = open_hi;
+  c->P.open_y[0] = c->Pdf.open_y[0] = c->Pdf.P64.open_y[0] = open_lo;
+  c->P.open_y[1] = c->Pdf.open_y[1] = c->Pdf.P64.open_y[1] = open_hi;
   return XG_OK;
 }
 
@@ -800,7 +804,7 @@ xg_status xg_partition_stage(xg_ctx* c, int half, int stage, double dt, double* 
   double alpha = 0.0, beta = 1.0;
   if (stage == 1) { q = c->Bq; qn = c->A; out = c->Cq; alpha = 0.75; beta = 0.25; }
   if (stage == 2) { q = c->Cq; qn = c->A; out = c->Dq; alpha = 1.0 / 3.0; beta = 2.0 / 3.0; }
-  if (stage < 0) out = c->dfm ? (void*)c->Cq : (where == XG_DEVICE ? (void*)dqdt : (void*)c->Bq);
+  if (stage < 0) out = where == XG_DEVICE ? (void*)dqdt : (void*)c->Bq;
   const int rhs = stage < 0 ? 1 : 0;
   const long long nf5 = 5ll * c->n[0] * c->n[2];
   const unsigned g = conv_blocks(nf5);
@@ -808,27 +812,20 @@ xg_status xg_partition_stage(xg_ctx* c, int half, int stage, double dt, double* 
     if (stage <= 0) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
     XG_CUDA(c, run_stage(c, q, qn, out, rhs ? 0.0 : dt, alpha, beta, rhs, st, 1));
     if (c->part_open[0]) {
-      if (c->dfm)
-        k_face_pack<df><<<g, 256, 0, st>>>((const df*)c->T, (df*)c->part_send[0], c->n[0], c->n[1],
-                                           c->n[2], c->np);
-      else
-        k_face_pack<double><<<g, 256, 0, st>>>(c->T, c->part_send[0], c->n[0], c->n[1], c->n[2], c->np);
+      k_face_pack<double><<<g, 256, 0, st>>>(c->T, c->part_send[0], c->n[0], c->n[1], c->n[2], c->np);
       XG_CUDA(c, cudaGetLastError());
     }
     return XG_OK;
   }
   if (c->dfm)
-    k_face_combine<df><<<g, 256, 0, st>>>((df*)c->T, (const df*)c->part_recv[0],
-                                          (const df*)c->part_recv[1], (const df*)c->part_send[1],
-                                          c->n[0], c->n[1], c->n[2], c->np);
+    k_face_combine<true><<<g, 256, 0, st>>>(c->T, c->part_recv[0], c->part_recv[1], c->part_send[1],
+                                            c->n[0], c->n[1], c->n[2], c->np);
   else
-    k_face_combine<double><<<g, 256, 0, st>>>(c->T, c->part_recv[0], c->part_recv[1], c->part_send[1],
-                                              c->n[0], c->n[1], c->n[2], c->np);
+    k_face_combine<false><<<g, 256, 0, st>>>(c->T, c->part_recv[0], c->part_recv[1], c->part_send[1],
+                                             c->n[0], c->n[1], c->n[2], c->np);
   XG_CUDA(c, cudaGetLastError());
   XG_CUDA(c, run_stage(c, q, qn, out, rhs ? 0.0 : dt, alpha, beta, rhs, st, 2));
   if (stage < 0) {
-    double* dst = where == XG_DEVICE ? dqdt : c->Bq;
-    if (c->dfm) XG_CUDA(c, export_values(c, c->Cq, dst, 5 * c->np, st));
     if (where == XG_HOST) {
       XG_CUDA(c, cudaMemcpyAsync(dqdt, c->Bq, sizeof(double) * 5 * (size_t)c->np,
                                  cudaMemcpyDeviceToHost, st));
@@ -876,9 +873,6 @@ xg_status xg_diagnostics(xg_ctx* c, double out[5], void* stream) {
   if (c->f32)
     k_diag_partial<float><<<kDiagBlocks, kDiagThreads, 0, st>>>((const float*)c->A, c->wasm, c->n[0],
                                                                 c->n[1], c->n[2], c->np, c->partial);
-  else if (c->dfm)
-    k_diag_partial<df><<<kDiagBlocks, kDiagThreads, 0, st>>>((const df*)c->A, c->wasm, c->n[0],
-                                                             c->n[1], c->n[2], c->np, c->partial);
   else
     k_diag_partial<double><<<kDiagBlocks, kDiagThreads, 0, st>>>(c->A, c->wasm, c->n[0], c->n[1],
                                                                  c->n[2], c->np, c->partial);
@@ -906,6 +900,7 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->T);
   cudaFree(c->S);
   cudaFree(c->base);
+  cudaFree(c->base64);
   cudaFree(c->flag);
   if (c->hflag) cudaFreeHost(c->hflag);
   closure_free(c);

@@ -21,7 +21,7 @@ struct xg_ctx {
   xg::LineParams P;
   xg::DfParams Pdf;      // launch constants of the double-float kernels
   xg::FParams Pf;        // launch constants of the FP32 kernels
-  bool dfm = false;      // precision XG_DF64: device arrays hold double-float pairs
+  bool dfm = false;      // precision XG_DF64: FP64 arrays, mixed FP64 / double-float kernels
   bool f32 = false;      // precision XG_FP32: device arrays hold floats
   int contract = 0;      // XG_FP32: arithmetic of the x and y contractions (XG_CONTRACT_*)
   double* A = nullptr;   // q^n (the state)
@@ -31,7 +31,8 @@ struct xg_ctx {
   double* W = nullptr;   // [4][np] primitives v, w, p', theta (FP32: [3][np])
   double* T = nullptr;   // [5][np] partial tendency
   double* S = nullptr;   // [np] heating
-  double* base = nullptr;  // [4][nz]
+  double* base = nullptr;  // [4][nz] (double-float pairs for XG_DF64 and XG_FP32)
+  double* base64 = nullptr;  // [4][nz] the same table in FP64
   double* wasm = nullptr;  // assembled 1-D mass weights: [n_x + n_y + n_z], J folded into x
   double* partial = nullptr;  // [kDiagBlocks][5] per-block conservation sums
   double* hdiag = nullptr;    // pinned [5]

@@ -1,15 +1,27 @@
-// xg_kernels_df.cuh -- the line kernels of xg_kernels.cuh in double-float
-// arithmetic (xg_df.cuh) on the FP32 pipes.
+// xg_kernels_df.cuh -- the FP64-accurate fast path (XG_DF64): the line
+// kernels of xg_kernels.cuh with the work split between the FP64 and the
+// FP32 pipes.
 //
-// Same method, same three-kernel stage (x lines with primitives, y lines,
-// z lines with sources, walls and the SSP-RK stage; the z kernel is tiled
-// instead of marching, see k_df_tline), same data layout: every
-// [5][Np] array holds double-float pairs (8 bytes per value, like FP64).
-// The contractions are compensated dot products (Dot2) seeded with the
-// running tendency; additions that can cancel use the accurate double-word
-// sum; the equation of state keeps the binomial series, its tail in float
-// and its first three terms in double-float.  The FP64 pipe is used only by
-// the rare equation-of-state fallback (|Theta'/Theta_0| >= x_max).
+// GB300 runs 2 FP64 FMAs per clock per SM against 128 FP32 FMAs.  The state
+// stays in FP64 (every [5][Np] array holds doubles, the ABI's own format), and
+// each equation is computed in the arithmetic its conditioning needs:
+//   * rho' and Theta' (Eq. 1a, 1c) -- their tendencies are residuals of
+//     cancelling flux derivatives where the flow is nearly non-divergent, so
+//     their whole path is native FP64: theta = Theta/rho, the fluxes' segment
+//     differences (difference form, xg_kernels.cuh), the contractions, the
+//     face sums, the partial tendency T, the heating source and the stage
+//     update.  These are the only FP64 instructions of the stage (~60 per
+//     node), which bound it.
+//   * the momentum (Eq. 1b) -- its tendency does not cancel; primitives,
+//     the equation of state, fluxes, contractions (compensated Dot2), face
+//     sums, Coriolis and gravity and the stage update run in double-float
+//     arithmetic (xg_df.cuh, unit roundoff 2^-48) on the FP32 pipes, from the
+//     FP64 state split into float pairs with integer operations only (FP64
+//     conversions run at the FP64 rate), and the results are widened back
+//     to FP64 for storage.
+// The partial tendency T holds doubles for rho' and Theta' and double-float
+// pairs for the momentum (8 bytes each); W holds v, w, p' as pairs and theta
+// as a double.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,21 +43,64 @@ struct DfParams {
   float eos_xmax;
   double gamma;
   df f, g;
+  LineParams P64;  // the FP64 constants of the rho' and Theta' path
 };
 
 struct DfBufs {
-  const df* q;
-  const df* qn;
-  df* out;
-  df* W;          // [4][np] v, w, p', theta = Theta / rho
-  df* T;          // [5][np]
-  const df* S;    // [np] or null
-  const df* base; // [4][nz] rho0, Theta0, p0, 1/Theta0
+  const double* q;
+  const double* qn;
+  double* out;
+  df* W;            // [3][np] v, w, p' (pairs); theta follows as doubles (W64)
+  double* W64;      // [np] theta = Theta / rho
+  double* T;        // [5][np]: slots 0 and 4 doubles, slots 1..3 pairs (Tm)
+  df* Tm;           // the same array seen as pairs
+  const double* S;  // [np] heating or null
+  const df* base;   // [4][nz] rho0, Theta0, p0, 1/Theta0 as pairs
+  const double* base64;  // the same table in FP64
   int* flag;
-  df dt, alpha, beta, bdt;   // bdt = beta dt
+  df dt, alpha, beta, bdt;      // momentum stage coefficients (bdt = beta dt)
+  double dt64, alpha64, beta64; // rho' and Theta' stage coefficients
   int rhs_only;
-  df* face_hi;    // [5][n_z][n_x] one-sided row N at an open y end (see StageBufs)
+  double* face_hi;  // [5][n_z][n_x] row N at an open y end (slot types as T)
 };
+
+// ---------------------------------------------------------------- FP64 <-> pairs
+// x = h + l with h the leading 24 significand bits of x (truncated) and l the
+// next ones rounded to a float, then renormalised (|l| <= ulp(h)/2): unit
+// roundoff 2^-48, integer and FP32 operations only.  |x| < 2^-100 gives 0 (far
+// below any state value's significance); |x| >= 2^128 gives +-inf, so a
+// non-finite value stays non-finite.
+__device__ __forceinline__ df df_of_double(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned sign = hi & 0x80000000u;
+  if (e < 1023 - 100) return {__uint_as_float(sign), 0.0f};
+  if (e > 1023 + 127) return {__uint_as_float(sign | 0x7f800000u), 0.0f};
+  const unsigned top = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | top);
+  float l = 0.0f;
+  if (e >= 949) {   // the remainder's scale 2^(e - 1075) is a normal float
+    l = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((unsigned)(e - 948) << 23));
+    if (sign) l = -l;
+  }
+  float s, t;
+  fast_two_sum(h, l, s, t);
+  return {s, t};
+}
+
+// A float widened to a double exactly, with integer operations (subnormal
+// floats, below 2^-126, give 0; inf/nan stay non-finite).
+__device__ __forceinline__ double dbl_of_float(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ef == 255) return __hiloint2double((int)((u & 0x80000000u) | 0x7ff00000u | ((u >> 3) & 0xfffffu)), 0);
+  const unsigned hi = (u & 0x80000000u) | ((ef + 896u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// h + l rounded to FP64 (one FP64 add of two exact widenings).
+__device__ __forceinline__ double dbl_of_df(df a) { return __dadd_rn(dbl_of_float(a.h), dbl_of_float(a.l)); }
 
 // (1+x)^gamma - 1 = x (c1 + x (c2 + x (c3 + x g(x)))), g = c4 + ... + c8 x^4
 // in float (its rounding enters at relative size x^3 2^-24).
@@ -80,52 +135,6 @@ __device__ __forceinline__ df df_row(const DfParams& P, int a, const df (&f)[N +
   return dacc_value(A);
 }
 
-// ---------------------------------------------------------------- difference form
-// The rho' and Theta' tendencies are small residuals of cancelling flux
-// derivatives wherever the flow is nearly non-divergent (a vortex: the x and
-// y parts nearly cancel), so their absolute error must stay far below the
-// size of each part.  A compensated dot product's error is proportional to
-// the sum of |Dm[a][l] f_l|, which for a smooth flux is many times the
-// derivative itself.  Each row of the LGL derivative matrix sums to zero
-// (D 1 = 0: the derivative of a constant), so
-//     sum_l Dm[a][l] f_l = sum_{l>=1} Dm[a][l] (f_l - f_0),
-// whose terms scale with the flux's variation across the element segment
-// instead of with the flux itself.  The Theta' flux Theta u_d is written as
-// theta (rho u_d) with theta = Theta / rho, and its differences as
-//     F_l - F_0 = theta_l (m_l - m_0) + (theta_l - theta_0) m_0,
-// so that the rounding of the product also scales with the variation (for a
-// level-uniform theta, as in a balanced vortex, the second part vanishes).
-// The exact value is unchanged; only the rounding is.
-
-// differences of one element segment: dm[l-1] = m_l - m_0 (the rho' flux)
-// and dF[l-1] = theta_l m_l - theta_0 m_0 (the Theta' flux), l = 1..N
-template <int N>
-__device__ __forceinline__ void df_seg_diffs(const df (&m)[N + 1], const df (&th)[N + 1],
-                                             df (&dm)[N], df (&dF)[N]) {
-#pragma unroll
-  for (int l = 1; l <= N; ++l) {
-    dm[l - 1] = df_sub(m[l], m[0]);
-    dF[l - 1] = df_add_nc(df_mul(th[l], dm[l - 1]), df_mul(df_sub(th[l], th[0]), m[0]));
-  }
-}
-
-// start + sum_{l>=1} Dm[d][a][l] d[l-1] (Dot2)
-template <int N, int D>
-__device__ __forceinline__ df df_drow_from(const DfParams& P, int a, const df (&d)[N], df start) {
-  dacc A = dacc_from(start);
-#pragma unroll
-  for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[D][a][l], d[l - 1]);
-  return dacc_value(A);
-}
-
-template <int N, int D>
-__device__ __forceinline__ df df_drow(const DfParams& P, int a, const df (&d)[N]) {
-  dacc A = dacc_prod(P.Dm[D][a][1], d[0]);
-#pragma unroll
-  for (int l = 2; l <= N; ++l) dacc_fma(A, P.Dm[D][a][l], d[l - 1]);
-  return dacc_value(A);
-}
-
 // ---------------------------------------------------------------- x lines
 template <int N>
 __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const DfBufs B) {
@@ -136,56 +145,59 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
   const long long np = P.np;
   const long long row = (long long)nx * (y + (long long)ny * z);
   const int ld = nx + 1;
-  df* F = smd;             // [5][ld], later rows 0..N-1 of every segment in place
-  df* RN = smd + 5 * ld;   // [5][nseg] row N
-  const df rho0 = B.base[z], Th0 = B.base[nz + z], p0 = B.base[2 * nz + z];
-  const df iTh0 = B.base[3 * nz + z];
-  const df* __restrict__ q = B.q;
-  df* __restrict__ Wo = B.W;
-  df* __restrict__ To = B.T;
+  // [5][ld] fluxes (slots 0 and 4 doubles: rho u and theta; 1..3 pairs), later
+  // rows 0..N-1 of every segment in place; RN [5][nseg] row N (same types)
+  df* F = smd;
+  double* F64 = reinterpret_cast<double*>(smd);
+  df* RN = smd + 5 * ld;
+  double* RN64 = reinterpret_cast<double*>(RN);
+  const df p0 = B.base[2 * nz + z], iTh0 = B.base[3 * nz + z];
+  const double rho0 = B.base64[z], Th0 = B.base64[nz + z];
+  const double* __restrict__ q = B.q;
 
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const long long I = row + i;
-    const df rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
-    const df tp = q[4 * np + I];
-    const df ir = df_rcp(df_add(rho0, rp));
-    const df u = df_mul(mu, ir), v = df_mul(mv, ir), w = df_mul(mw, ir);
-    const df pp = df_mul(p0, df_eos_phi(P, df_mul(tp, iTh0)));
-    const df Th = df_add(Th0, tp);
-    const df th = df_mul(Th, ir);
-    Wo[I] = v;
-    Wo[np + I] = w;
-    Wo[2 * np + I] = pp;
-    Wo[3 * np + I] = th;
-    F[i] = mu;
-    F[ld + i] = df_add(df_mul(mu, u), pp);
-    F[2 * ld + i] = df_mul(mv, u);
-    F[3 * ld + i] = df_mul(mw, u);
-    F[4 * ld + i] = th;               // theta: the Theta' flux is theta (rho u)
+    const double rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
+    const double tp = q[4 * np + I];
+    const double ir64 = rcp_newton(rho0 + rp);
+    const double th = (Th0 + tp) * ir64;
+    const df ir = df_of_double(ir64);
+    const df muD = df_of_double(mu), mvD = df_of_double(mv), mwD = df_of_double(mw);
+    const df u = df_mul(muD, ir), v = df_mul(mvD, ir), w = df_mul(mwD, ir);
+    const df pp = df_mul(p0, df_eos_phi(P, df_mul(df_of_double(tp), iTh0)));
+    B.W[I] = v;
+    B.W[np + I] = w;
+    B.W[2 * np + I] = pp;
+    B.W64[I] = th;
+    F64[i] = mu;
+    F[ld + i] = df_add(df_mul(muD, u), pp);
+    F[2 * ld + i] = df_mul(mvD, u);
+    F[3 * ld + i] = df_mul(mwD, u);
+    F64[4 * ld + i] = th;                 // the Theta' flux is theta (rho u)
     if (P.per[0] && i == 0) {
+      F64[nx] = mu;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) F[c * ld + nx] = F[c * ld];
+      for (int c = 1; c < 4; ++c) F[c * ld + nx] = F[c * ld];
+      F64[4 * ld + nx] = th;
     }
   }
   __syncthreads();
 
   for (int s0 = 0; s0 < nseg; s0 += blockDim.x) {
     const int s = s0 + threadIdx.x;
-    df rows[5][N + 1];
+    double r64[2][N + 1];
+    df rows[3][N + 1];
     if (s < nseg) {
-      {
-        df m[N + 1], th[N + 1], dm[N], dF[N];
+      {   // rho' and Theta': FP64, difference form
+        double m[N + 1], th[N + 1], dm[N + 1], dF[N + 1];
 #pragma unroll
         for (int l = 0; l <= N; ++l) {
-          m[l] = F[s * N + l];
-          th[l] = F[4 * ld + s * N + l];
+          m[l] = F64[s * N + l];
+          th[l] = F64[4 * ld + s * N + l];
         }
-        df_seg_diffs<N>(m, th, dm, dF);
-#pragma unroll
-        for (int a = 0; a <= N; ++a) {
-          rows[0][a] = df_drow<N, 0>(P, a, dm);
-          rows[4][a] = df_drow<N, 0>(P, a, dF);
-        }
+        seg_diffs<N>(m, th, dm, dF);
+        contract_eo<N, 0>(P.P64, dm, r64[0]);
+        contract_eo<N, 0>(P.P64, dF, r64[1]);
       }
 #pragma unroll
       for (int c = 1; c < 4; ++c) {
@@ -193,16 +205,23 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
 #pragma unroll
         for (int l = 0; l <= N; ++l) f[l] = F[c * ld + s * N + l];
 #pragma unroll
-        for (int a = 0; a <= N; ++a) rows[c][a] = df_row<N, 0>(P, a, f);
+        for (int a = 0; a <= N; ++a) rows[c - 1][a] = df_row<N, 0>(P, a, f);
       }
     }
     __syncthreads();
     if (s < nseg) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+      for (int a = 0; a < N; ++a) {
+        F64[s * N + a] = r64[0][a];
+        F64[4 * ld + s * N + a] = r64[1][a];
+      }
+      RN64[s] = r64[0][N];
+      RN64[4 * nseg + s] = r64[1][N];
 #pragma unroll
-        for (int a = 0; a < N; ++a) F[c * ld + s * N + a] = rows[c][a];
-        RN[c * nseg + s] = rows[c][N];
+      for (int c = 1; c < 4; ++c) {
+#pragma unroll
+        for (int a = 0; a < N; ++a) F[c * ld + s * N + a] = rows[c - 1][a];
+        RN[c * nseg + s] = rows[c - 1][N];
       }
     }
     __syncthreads();
@@ -211,8 +230,23 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const int s = i / N, a = i - s * N;
     const long long I = row + i;
+    const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < 5; c += 4) {
+      double v;
+      if (s == nseg) {
+        v = RN64[c * nseg + nseg - 1];
+        v = v + v;
+      } else if (a != 0) {
+        v = F64[c * ld + i];
+      } else {
+        const double r0 = F64[c * ld + i];
+        v = r0 + (left >= 0 ? RN64[c * nseg + left] : r0);
+      }
+      B.T[c * np + I] = v;
+    }
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
       df v;
       if (s == nseg) {
         v = df_scale2(RN[c * nseg + nseg - 1], 2.0f);
@@ -220,30 +254,29 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
         v = F[c * ld + i];
       } else {
         const df r0 = F[c * ld + i];
-        const int left = s > 0 ? s - 1 : (P.per[0] ? nseg - 1 : -1);
         v = left >= 0 ? df_add(r0, RN[c * nseg + left]) : df_scale2(r0, 2.0f);
       }
-      To[c * np + I] = v;
+      B.Tm[c * np + I] = v;
     }
   }
 }
 
 // ---------------------------------------------------------------- y lines
-// y-fluxes at one node; slot 4 holds theta = Theta / rho from W (the Theta'
-// flux is theta (rho v), taken in difference form)
-__device__ __forceinline__ void df_flux_y(const df* __restrict__ q, const df* __restrict__ W,
-                                          long long np, long long I, df (&f)[5]) {
-  const df mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
-  const df v = W[I], pp = W[2 * np + I];
-  f[0] = mv;
-  f[1] = df_mul(mu, v);
-  f[2] = df_add(df_mul(mv, v), pp);
-  f[3] = df_mul(mw, v);
-  f[4] = W[3 * np + I];
+// y-fluxes at one node: rho v and theta (FP64) for the difference form of
+// rho' and Theta', the momentum fluxes as pairs
+__device__ __forceinline__ void df_flux_y(const DfBufs& B, long long np, long long I, double& m,
+                                          double& th, df (&f)[3]) {
+  const double mu = B.q[np + I], mv = B.q[2 * np + I], mw = B.q[3 * np + I];
+  const df v = B.W[I], pp = B.W[2 * np + I];
+  m = mv;
+  th = B.W64[I];
+  f[0] = df_mul(df_of_double(mu), v);
+  f[1] = df_add(df_mul(df_of_double(mv), v), pp);
+  f[2] = df_mul(df_of_double(mw), v);
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const DfBufs B, int chunk) {
+__global__ void __launch_bounds__(128, N <= 3 ? 4 : 3) k_df_line_y(const DfParams P, const DfBufs B, int chunk) {
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
   const int nseg = P.nseg[1];
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,187 +287,199 @@ __global__ void __launch_bounds__(128, 4) k_df_line_y(const DfParams P, const Df
   if (s0 >= s1) return;
   const long long np = P.np;
   const long long col = x + (long long)nx * ny * z;
-  const df* __restrict__ q = B.q;
-  const df* __restrict__ W = B.W;
-  df* __restrict__ T = B.T;
+  const LineParams& P64 = P.P64;
+  double* __restrict__ T = B.T;
+  df* __restrict__ Tm = B.Tm;
   auto nodeI = [&](int gy) -> long long { return col + (long long)nx * (gy == ny ? 0 : gy); };
 
-  df carry[5];
+  double carry64[2];
+  df carry[3];
   bool has_left = (s0 > 0) || P.per[1];
   if (has_left) {
     const int sp = s0 > 0 ? s0 - 1 : nseg - 1;
-    df fl[5][N + 1];
+    double m[N + 1], th[N + 1];
+    df fl[3][N + 1];
 #pragma unroll
     for (int l = 0; l <= N; ++l) {
-      df f[5];
-      df_flux_y(q, W, np, nodeI(sp * N + l), f);
+      df f[3];
+      df_flux_y(B, np, nodeI(sp * N + l), m[l], th[l], f);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) fl[c][l] = f[c];
+      for (int c = 0; c < 3; ++c) fl[c][l] = f[c];
     }
-    df dm[N], dF[N];
-    df_seg_diffs<N>(fl[0], fl[4], dm, dF);
-    carry[0] = df_drow<N, 1>(P, N, dm);
-    carry[4] = df_drow<N, 1>(P, N, dF);
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(m, th, dm, dF);
+    carry64[0] = drow_N<N, 1>(P64, dm);
+    carry64[1] = drow_N<N, 1>(P64, dF);
 #pragma unroll
-    for (int c = 1; c < 4; ++c) carry[c] = df_row<N, 1>(P, N, fl[c]);
+    for (int c = 0; c < 3; ++c) carry[c] = df_row<N, 1>(P, N, fl[c]);
   }
 
-  df fc[5][N + 1];
+  double fm[N + 1], fth[N + 1];
+  df fc[3][N + 1];
   {
-    df f[5];
-    df_flux_y(q, W, np, nodeI(s0 * N), f);
+    df f[3];
+    df_flux_y(B, np, nodeI(s0 * N), fm[0], fth[0], f);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) fc[c][0] = f[c];
+    for (int c = 0; c < 3; ++c) fc[c][0] = f[c];
   }
   for (int s = s0; s < s1; ++s) {
 #pragma unroll
     for (int l = 1; l <= N; ++l) {
-      df f[5];
-      df_flux_y(q, W, np, nodeI(s * N + l), f);
+      df f[3];
+      df_flux_y(B, np, nodeI(s * N + l), fm[l], fth[l], f);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) fc[c][l] = f[c];
+      for (int c = 0; c < 3; ++c) fc[c][l] = f[c];
     }
-    df tv[5][N];
+    double tv64[2][N];
+    df tv[3][N];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const long long I = nodeI(s * N + a);
+      tv64[0][a] = T[I];
+      tv64[1][a] = T[4 * np + I];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) tv[c][a] = T[c * np + I];
+      for (int c = 0; c < 3; ++c) tv[c][a] = Tm[(c + 1) * np + I];
     }
-    df dm[N], dF[N];
-    df_seg_diffs<N>(fc[0], fc[4], dm, dF);
-    // row a of variable c seeded with start: rho' and Theta' in difference form
-    auto rowc = [&](int c, int a, df start) -> df {
-      if (c == 0) return df_drow_from<N, 1>(P, a, dm, start);
-      if (c == 4) return df_drow_from<N, 1>(P, a, dF, start);
-      return df_row_from<N, 1>(P, a, fc[c], start);
-    };
+    double dm[N + 1], dF[N + 1];
+    seg_diffs<N>(fm, fth, dm, dF);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (int e = 0; e < 2; ++e) {   // rho' (e = 0) and Theta' (e = 1), FP64
+      const double (&d)[N + 1] = e == 0 ? dm : dF;
+      double* Tv = T + (e == 0 ? 0 : 4) * np;
+      double t0 = tv64[e][0];
+      if (!has_left && !P.open_y[0]) t0 = drow_from<N, 1>(P64, 0, d, t0);   // wall: twice
+      t0 = drow_from<N, 1>(P64, 0, d, t0);
+      Tv[nodeI(s * N)] = has_left ? t0 + carry64[e] : t0;
+#pragma unroll
+      for (int a = 1; a < N; ++a) Tv[nodeI(s * N + a)] = drow_from<N, 1>(P64, a, d, tv64[e][a]);
+      carry64[e] = drow_N<N, 1>(P64, d);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
       df t0 = tv[c][0];
-      if (!has_left && !P.open_y[0]) t0 = rowc(c, 0, t0);   // wall: the row counts twice
-      t0 = rowc(c, 0, t0);
-      T[c * np + nodeI(s * N)] = has_left ? df_add(t0, carry[c]) : t0;
+      if (!has_left && !P.open_y[0]) t0 = df_row_from<N, 1>(P, 0, fc[c], t0);
+      t0 = df_row_from<N, 1>(P, 0, fc[c], t0);
+      Tm[(c + 1) * np + nodeI(s * N)] = has_left ? df_add(t0, carry[c]) : t0;
 #pragma unroll
-      for (int a = 1; a < N; ++a) T[c * np + nodeI(s * N + a)] = rowc(c, a, tv[c][a]);
-      carry[c] = c == 0 ? df_drow<N, 1>(P, N, dm)
-                        : (c == 4 ? df_drow<N, 1>(P, N, dF) : df_row<N, 1>(P, N, fc[c]));
+      for (int a = 1; a < N; ++a)
+        Tm[(c + 1) * np + nodeI(s * N + a)] = df_row_from<N, 1>(P, a, fc[c], tv[c][a]);
+      carry[c] = df_row<N, 1>(P, N, fc[c]);
+      fc[c][0] = fc[c][N];
     }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) fc[c][0] = fc[c][N];
+    fm[0] = fm[N];
+    fth[0] = fth[N];
     has_left = true;
   }
   if (!P.per[1] && s1 == nseg) {
     const long long I = nodeI(nseg * N);
-    if (P.open_y[1]) {   // partition face: the row goes to the neighbour
-      const long long Fo = x + (long long)nx * z;
+    if (P.open_y[1]) {   // partition face: the rows go to the neighbour
+      const long long Fo = x + (long long)nx * z, nf = (long long)nx * nz;
+      B.face_hi[Fo] = carry64[0];
+      B.face_hi[4 * nf + Fo] = carry64[1];
+      df* fh = reinterpret_cast<df*>(B.face_hi);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) B.face_hi[c * (long long)nx * nz + Fo] = carry[c];
+      for (int c = 0; c < 3; ++c) fh[(c + 1) * nf + Fo] = carry[c];
     } else {
+      T[I] += carry64[0] + carry64[0];
+      T[4 * np + I] += carry64[1] + carry64[1];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) T[c * np + I] = df_add(T[c * np + I], df_scale2(carry[c], 2.0f));
+      for (int c = 0; c < 3; ++c)
+        Tm[(c + 1) * np + I] = df_add(Tm[(c + 1) * np + I], df_scale2(carry[c], 2.0f));
     }
   }
 }
 
 // ---------------------------------------------------------------- z lines + sources + stage
 
-// FP64 <-> double-float conversion of n values (data entering or leaving).
-__global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, long long n);
-__global__ void k_from_df(const df* __restrict__ in, double* __restrict__ out, long long n);
-
-}  // namespace xg
-
-namespace xg {
-
-// ---------------------------------------------------------------- z lines, tiled
-// (The template also covers y lines; the marching k_df_line_y measured faster
-// there, so only DIR = 2 is launched.)
-// One CTA per (32 x-columns) x (a chunk of K element segments along the line
-// direction DIR: 1 = y, 2 = z) x (the remaining coordinate), one thread per
-// node: block (32, K N + 1), warp = one plane of 32 columns, so every warp
-// does the same kind of work.  All loads of the chunk are issued up front
-// (high memory-level parallelism), the fluxes along DIR go to shared memory
-// -- the chunk's K N + 1 planes plus the N planes of the segment before it
-// (whose last row completes the chunk's first face node) -- and each thread
-// then assembles its own node: y adds its part into T, z adds its part,
-// the sources, walls and the stage store.  Thread row K N handles the
-// chunk's end face: its fluxes close the last segment, and at a wall it
-// also owns the wall node.
-// Fluxes along DIR at one node from loaded values: qv = (rho', rho u,
-// rho v, rho w, Theta'), vel = v (DIR 1) or w (DIR 2), pp = p'.
-// Slot 4 holds theta = Theta / rho: the Theta' flux theta (rho u_DIR) is
-// taken in difference form with slot 0.
+// Momentum fluxes along DIR (1 = y, 2 = z) at one node from its momentum as
+// pairs, vel = v or w and pp = p'.
 template <int DIR>
-__device__ __forceinline__ void df_flux_vals(const df (&qv)[5], df vel, df pp, df th, df (&f)[5]) {
-  f[0] = qv[DIR + 1];
-  f[1] = DIR == 1 ? df_mul(qv[1], vel) : df_mul(qv[1], vel);
-  f[2] = DIR == 1 ? df_add(df_mul(qv[2], vel), pp) : df_mul(qv[2], vel);
-  f[3] = DIR == 1 ? df_mul(qv[3], vel) : df_add(df_mul(qv[3], vel), pp);
-  f[4] = th;
+__device__ __forceinline__ void df_flux_mom(const df (&m)[3], df vel, df pp, df (&f)[3]) {
+  f[0] = df_mul(m[0], vel);
+  f[1] = DIR == 1 ? df_add(df_mul(m[1], vel), pp) : df_mul(m[1], vel);
+  f[2] = DIR == 1 ? df_mul(m[2], vel) : df_add(df_mul(m[2], vel), pp);
 }
 
-// Sources, walls and the stage store of one node from loaded values.
-__device__ __forceinline__ void df_finish_vals(const DfParams& P, const DfBufs& B,
-                                               const df (&qv)[5], const df (&qnv)[5], df sv,
-                                               df rho0, df* __restrict__ out, long long I, int x,
-                                               int y, int gz, df (&L)[5], bool& bad) {
+// Sources, walls and the stage store of one node: L64 = the rho' and Theta'
+// tendencies (FP64), Lm = the momentum tendencies (pairs); qv the node's
+// FP64 state, qm its momentum as pairs, qnv the FP64 q^n (stages 2-3).
+__device__ __forceinline__ void df_finish(const DfParams& P, const DfBufs& B, const double (&qv)[5],
+                                          const df (&qm)[3], const double (&qnv)[5], double sv,
+                                          double rho0, double* __restrict__ out, long long I, int x,
+                                          int y, int gz, double (&L64)[2], df (&Lm)[3], bool& bad) {
   const long long np = P.np;
-  dacc A = dacc_from(L[1]);
-  dacc_fma(A, P.f, qv[2]);                       // +f rho v
-  L[1] = dacc_value(A);
-  A = dacc_from(L[2]);
-  dacc_fma(A, df_neg(P.f), qv[1]);               // -f rho u
-  L[2] = dacc_value(A);
-  A = dacc_from(L[3]);
-  dacc_fma(A, df_neg(P.g), qv[0]);               // -rho' g
-  L[3] = dacc_value(A);
-  if (B.S) {
-    A = dacc_from(L[4]);
-    dacc_fma(A, df_add(rho0, qv[0]), sv);        // rho S_theta
-    L[4] = dacc_value(A);
-  }
+  dacc A = dacc_from(Lm[0]);
+  dacc_fma(A, P.f, qm[1]);                       // +f rho v
+  Lm[0] = dacc_value(A);
+  A = dacc_from(Lm[1]);
+  dacc_fma(A, df_neg(P.f), qm[0]);               // -f rho u
+  Lm[1] = dacc_value(A);
+  A = dacc_from(Lm[2]);
+  dacc_fma(A, df_neg(P.g), df_of_double(qv[0])); // -rho' g
+  Lm[2] = dacc_value(A);
+  if (B.S) L64[1] = fma(rho0 + qv[0], sv, L64[1]);   // rho S_theta
   const df zero = {0.0f, 0.0f};
-  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) L[1] = zero;
-  if (!P.per[1] && ((y == 0 && !P.open_y[0]) || (y == P.n[1] - 1 && !P.open_y[1]))) L[2] = zero;
-  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = zero;
+  if (!P.per[0] && (x == 0 || x == P.n[0] - 1)) Lm[0] = zero;
+  if (!P.per[1] && ((y == 0 && !P.open_y[0]) || (y == P.n[1] - 1 && !P.open_y[1]))) Lm[1] = zero;
+  if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) Lm[2] = zero;
+  const bool stage1 = B.alpha64 == 0.0;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
+  for (int e = 0; e < 2; ++e) {
+    const int c = e == 0 ? 0 : 4;
+    double o;
+    if (B.rhs_only) o = L64[e];
+    else if (stage1) o = fma(B.dt64, L64[e], qv[c]);
+    else o = fma(B.alpha64, qnv[c], B.beta64 * fma(B.dt64, L64[e], qv[c]));
+    out[c * np + I] = o;
+    bad |= is_nonfinite(o);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
     df o;
     if (B.rhs_only) {
-      o = L[c];
-    } else if (B.alpha.h == 0.0f) {
-      dacc R = dacc_from(qv[c]);
-      dacc_fma(R, B.dt, L[c]);
+      o = Lm[c];
+    } else if (stage1) {
+      dacc R = dacc_from(qm[c]);
+      dacc_fma(R, B.dt, Lm[c]);
       o = dacc_value(R);
     } else {
-      dacc R = dacc_prod(B.alpha, qnv[c]);
-      dacc_fma(R, B.beta, qv[c]);
-      dacc_fma(R, B.bdt, L[c]);
+      dacc R = dacc_prod(B.alpha, df_of_double(qnv[c + 1]));
+      dacc_fma(R, B.beta, qm[c]);
+      dacc_fma(R, B.bdt, Lm[c]);
       o = dacc_value(R);
     }
-    out[c * np + I] = o;
     bad |= df_nonfinite(o);
+    out[(c + 1) * np + I] = dbl_of_df(o);
   }
 }
 
 constexpr int kTileCols = 32;
 
 __host__ __device__ constexpr int tile_segments(int N) { return N >= 16 ? 1 : 16 / N; }
-// The double-float z tiles hold half as many segments (at most 9 planes):
-// 3 CTAs of 288 threads fit an SM without spills (measured: 0.76 vs 0.84 ms
-// per launch on the 128x128x16 order-4 box against 16-plane tiles).
+// The z tiles hold at most 9 planes: 3 CTAs of 288 threads fit an SM
+// without spills.
 __host__ __device__ constexpr int df_tile_segments(int N) { return N >= 8 ? 1 : 8 / N; }
 
+// ---------------------------------------------------------------- z lines, tiled
+// One CTA per (32 x-columns) x (a chunk of K element segments along z) x y,
+// one thread per node: block (32, K N + 1), warp = one plane of 32 columns.
+// All loads of the chunk are issued up front, the fluxes go to shared memory
+// -- the chunk's K N + 1 planes plus the N planes of the segment before it
+// (whose last row completes the chunk's first face node) -- and each thread
+// then assembles its own node: the z part, the sources, walls and the stage
+// store.  Thread row K N handles the chunk's end face: its fluxes close the
+// last segment, and at a wall it also owns the wall node.  (DIR = 1, y
+// lines, is the same scheme; only z is launched.)
 template <int N, int DIR>
 __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfParams P, const DfBufs B) {
   constexpr int K = df_tile_segments(N);
   constexpr int NS = K * N + N + 1;            // flux slots: N halo planes + K N + 1
-  __shared__ df Fs[5][NS][kTileCols];
+  __shared__ df Fm[3][NS][kTileCols];          // momentum fluxes (pairs)
+  __shared__ double Fs[2][NS][kTileCols];      // rho u_DIR and theta
   // rho' and Theta' flux differences of slot j against its segment's first
   // slot (difference form); slot j >= 1 lies in the segment that starts at
   // slot N floor((j - 1) / N), of which it is an interior node or the end
-  __shared__ df Ds[2][NS][kTileCols];
+  __shared__ double Ds[2][NS][kTileCols];
   const int nx = P.n[0], ny = P.n[1];
   const int nd = P.n[DIR];                      // nodes along the line
   const int nseg = P.nseg[DIR];
@@ -451,9 +496,8 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const bool has_left = s0 > 0 || per;
   auto plane = [&](int g) -> int { return g >= nd ? g - nd : (g < 0 ? g + nd : g); };
   const int vslot = DIR == 1 ? 0 : 1;            // v or w in W
+  const LineParams& P64 = P.P64;
 
-  // the node this thread owns: planes s0 N + ty for ty < kc N, and the end
-  // wall plane for the extra row of the last chunk of a walled line
   const int own = s0 * N + ty;
   const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
   const bool main_plane = xin && ty <= kc * N;   // the extra row fills the end face
@@ -462,56 +506,68 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const int gh = plane((s0 - 1) * N + ty);
   const long long I = base + sd * (main_plane ? g : 0);
   const long long Ih = base + sd * (halo ? gh : 0);
+
   // every global load of the thread first: one memory round trip
-  df qv[5], vel, pp, th, hq[5], hvel, hpp, hth, t[5], qnv[5], sv = {0.0f, 0.0f};
-  hq[0] = sv;
+  double qv[5], hq[3], th = 0.0, hth = 0.0, t64[2], qnv[5], sv = 0.0;
+  df vel, pp, hvel, hpp, tm[3];
   if (main_plane) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) qv[c] = B.q[c * np + I];
     vel = B.W[vslot * np + I];
     pp = B.W[2 * np + I];
-    th = B.W[3 * np + I];
+    th = B.W64[I];
   }
   if (halo) {
 #pragma unroll
-    for (int c = 1; c < 5; ++c) hq[c] = B.q[c * np + Ih];
+    for (int c = 0; c < 3; ++c) hq[c] = B.q[(c + 1) * np + Ih];
     hvel = B.W[vslot * np + Ih];
     hpp = B.W[2 * np + Ih];
-    hth = B.W[3 * np + Ih];
+    hth = B.W64[Ih];
   }
   if (owns) {
+    t64[0] = B.T[I];
+    t64[1] = B.T[4 * np + I];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) t[c] = B.T[c * np + I];
+    for (int c = 0; c < 3; ++c) tm[c] = B.Tm[(c + 1) * np + I];
     if (DIR == 2) {
-      if (!B.rhs_only && B.alpha.h != 0.0f) {
+      if (!B.rhs_only && B.alpha64 != 0.0) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) qnv[c] = B.qn[c * np + I];
       }
       if (B.S) sv = B.S[I];
     }
   }
+  df qm[3];
   if (main_plane) {
-    df f[5];
-    df_flux_vals<DIR>(qv, vel, pp, th, f);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][N + ty][tx] = f[c];
+    for (int c = 0; c < 3; ++c) qm[c] = df_of_double(qv[c + 1]);
+    df f[3];
+    df_flux_mom<DIR>(qm, vel, pp, f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Fm[c][N + ty][tx] = f[c];
+    Fs[0][N + ty][tx] = qv[DIR + 1];
+    Fs[1][N + ty][tx] = th;
   }
   if (halo) {
-    df f[5];
-    df_flux_vals<DIR>(hq, hvel, hpp, hth, f);
+    df hm[3];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Fs[c][ty][tx] = f[c];
+    for (int c = 0; c < 3; ++c) hm[c] = df_of_double(hq[c]);
+    df f[3];
+    df_flux_mom<DIR>(hm, hvel, hpp, f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Fm[c][ty][tx] = f[c];
+    Fs[0][ty][tx] = hq[DIR];
+    Fs[1][ty][tx] = hth;
   }
   __syncthreads();
 
-  // difference form of the rho' and Theta' fluxes, slot by slot
+  // difference form of the rho' and Theta' fluxes, slot by slot (FP64)
   auto diff_slot = [&](int j) {
     const int b = N * ((j - 1) / N);
-    const df mj = Fs[0][j][tx], mb = Fs[0][b][tx];
-    const df thj = Fs[4][j][tx], thb = Fs[4][b][tx];
-    const df dm = df_sub(mj, mb);
+    const double mb = Fs[0][b][tx], thb = Fs[1][b][tx], thj = Fs[1][j][tx];
+    const double dm = Fs[0][j][tx] - mb;
     Ds[0][j][tx] = dm;
-    Ds[1][j][tx] = df_add_nc(df_mul(thj, dm), df_mul(df_sub(thj, thb), mb));
+    Ds[1][j][tx] = fma(thj, dm, (thj - thb) * mb);
   };
   if (main_plane && (ty > 0 || has_left)) diff_slot(N + ty);   // slot N closes the halo segment
   if (halo && ty > 0) diff_slot(ty);
@@ -522,58 +578,59 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const int k = ty < kc * N ? ty / N : kc - 1;
   const int a = ty < kc * N ? ty - k * N : N;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    if (c == 0 || c == 4) {
-      const int e = c == 0 ? 0 : 1;
-      df d[N];
+  for (int e = 0; e < 2; ++e) {
+    double d[N + 1];
+    d[0] = 0.0;
 #pragma unroll
-      for (int l = 1; l <= N; ++l) d[l - 1] = Ds[e][N + k * N + l][tx];
-      if (a == N) {                                 // wall node: its one-sided row counts twice
-        const df r = df_drow<N, DIR>(P, N, d);
-        t[c] = df_add(t[c], df_scale2(r, 2.0f));
-      } else if (a > 0) {
-        t[c] = df_drow_from<N, DIR>(P, a, d, t[c]);
-      } else {
-        // a face: both one-sided rows in one compensated sum (the segment
-        // before, or the same row twice at the wall at the line start)
-        df dl[N];
-        const bool left = k > 0 || has_left;
+    for (int l = 1; l <= N; ++l) d[l] = Ds[e][N + k * N + l][tx];
+    double t = t64[e];
+    if (a == N) {                                 // wall node: its one-sided row counts twice
+      const double r = drow_N<N, DIR>(P64, d);
+      t = t + (r + r);
+    } else if (a > 0) {
+      t = drow_from<N, DIR>(P64, a, d, t);
+    } else if (k > 0 || has_left) {               // shared face: both one-sided halves
+      double dl[N + 1];
+      dl[0] = 0.0;
 #pragma unroll
-        for (int l = 1; l <= N; ++l) dl[l - 1] = left ? Ds[e][k * N + l][tx] : d[l - 1];
-        dacc A = dacc_from(t[c]);
-#pragma unroll
-        for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[DIR][0][l], d[l - 1]);
-#pragma unroll
-        for (int l = 1; l <= N; ++l) dacc_fma(A, P.Dm[DIR][left ? N : 0][l], dl[l - 1]);
-        t[c] = dacc_value(A);
-      }
-      continue;
+      for (int l = 1; l <= N; ++l) dl[l] = Ds[e][k * N + l][tx];
+      t = drow_from<N, DIR>(P64, 0, d, t);
+      t = drow_from<N, DIR>(P64, N, dl, t);
+    } else {                                      // wall at the line start
+      t = drow_from<N, DIR>(P64, 0, d, t);
+      t = drow_from<N, DIR>(P64, 0, d, t);
     }
+    t64[e] = t;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
     df f[N + 1];
 #pragma unroll
-    for (int l = 0; l <= N; ++l) f[l] = Fs[c][N + k * N + l][tx];
-    if (a == N) {                                   // wall node: its one-sided row counts twice
+    for (int l = 0; l <= N; ++l) f[l] = Fm[c][N + k * N + l][tx];
+    if (a == N) {
       const df r = df_row<N, DIR>(P, N, f);
-      t[c] = df_add(t[c], df_scale2(r, 2.0f));
+      tm[c] = df_add(tm[c], df_scale2(r, 2.0f));
     } else if (a > 0) {
-      t[c] = df_row_from<N, DIR>(P, a, f, t[c]);
-    } else if (k > 0 || has_left) {                 // shared face: both one-sided halves
+      tm[c] = df_row_from<N, DIR>(P, a, f, tm[c]);
+    } else if (k > 0 || has_left) {
       df fl[N + 1];
 #pragma unroll
-      for (int l = 0; l <= N; ++l) fl[l] = Fs[c][k * N + l][tx];
-      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
-      t[c] = df_add(t[c], df_row<N, DIR>(P, N, fl));
-    } else {                                        // wall at the line start
-      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
-      t[c] = df_row_from<N, DIR>(P, 0, f, t[c]);
+      for (int l = 0; l <= N; ++l) fl[l] = Fm[c][k * N + l][tx];
+      tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
+      tm[c] = df_add(tm[c], df_row<N, DIR>(P, N, fl));
+    } else {
+      tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
+      tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
     }
   }
   if (DIR == 1) {
+    B.T[I] = t64[0];
+    B.T[4 * np + I] = t64[1];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) B.T[c * np + I] = t[c];
+    for (int c = 0; c < 3; ++c) B.Tm[(c + 1) * np + I] = tm[c];
   } else {
     bool bad = false;
-    df_finish_vals(P, B, qv, qnv, sv, B.base[g], B.out, I, x, other, g, t, bad);
+    df_finish(P, B, qv, qm, qnv, sv, B.base64[g], B.out, I, x, other, g, t64, tm, bad);
     if (bad) *B.flag = 1;
   }
 }

@@ -205,6 +205,7 @@ inline void fill_df_params(const LineParams& P, DfParams* Q) {
   Q->gamma = P.gamma;
   Q->f = split_df(P.f);
   Q->g = split_df(P.g);
+  Q->P64 = P;
 }
 
 // Launch constants of the FP32 line kernels, from the FP64 ones.
