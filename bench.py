@@ -52,7 +52,7 @@ KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 # the kernels behind the three timing slots in each precision (the FP32 form
 # fuses the x and y passes into one plane kernel; slot 1 stays empty)
 KERNEL_NAMES = {0: ("k_line_x", "k_line_y", "k_line_z"),
-                2: ("k_df_line_x", "k_df_line_y", "k_df_tline"),
+                2: ("k_df_line_x", "k_df_tline_y", "k_df_tline_z"),
                 1: ("k_f_plane_xy", "-", "k_f_tline")}
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
@@ -468,7 +468,7 @@ def make_ctx(xg, torch, wl, dev, precision=0):
 # W (3) and T; its z pass reads w and p' (no theta).
 _Z_VALUES = 5 + 3 + 5 + 1 + 5 * 2 / 3 + 5
 KERNEL_VALUES_PER_NODE = {"k_line_x": 14, "k_line_y": 16, "k_line_z": _Z_VALUES,
-                          "k_df_line_x": 14, "k_df_line_y": 16, "k_df_tline": _Z_VALUES,
+                          "k_df_line_x": 14, "k_df_tline_y": 16, "k_df_tline_z": _Z_VALUES,
                           "k_f_plane_xy": 13, "k_f_plane_xy_tc": 13, "k_f_tline": _Z_VALUES - 1}
 # The method's own traffic per node and stage: q and S in,
 # q out, plus q^n in stages 2 and 3.

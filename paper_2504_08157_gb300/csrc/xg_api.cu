@@ -263,9 +263,12 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
     prof_mark(c, 0, false, st);
     xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
     prof_mark(c, 0, true, st);
-    dim3 gy((c->n[0] + 127) / 128, c->nchunk_y, c->n[2]);
+    constexpr int K = xg::df_tile_segments(N);
+    const dim3 blk(xg::kTileCols, K * N + 1);
+    const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
+    dim3 gy(xb, (c->d.nel[1] + K - 1) / K, c->n[2]);
     prof_mark(c, 1, false, st);
-    xg::k_df_line_y<N><<<gy, 128, 0, st>>>(c->Pdf, B, c->chunk_y);
+    xg::k_df_tline<N, 1><<<gy, blk, 0, st>>>(c->Pdf, B);
     prof_mark(c, 1, true, st);
   }
   if (parts & 2) {

@@ -194,12 +194,13 @@ __device__ __forceinline__ double row_N(const LineParams& P, const double (&f)[N
 // value is unchanged.
 //
 // diffs(m, th, dm, dF): dm[l] = m_l - m_0 and dF[l] = theta_l m_l - theta_0
-// m_0 in that form, l = 0..N (dm[0] = dF[0] = 0).
+// m_0 in that form, l = 0..N (dm[0] = dF[0] = -0, the additive identity, so
+// the even/odd contraction's sums with them need no instruction).
 template <int N>
 __device__ __forceinline__ void seg_diffs(const double (&m)[N + 1], const double (&th)[N + 1],
                                           double (&dm)[N + 1], double (&dF)[N + 1]) {
-  dm[0] = 0.0;
-  dF[0] = 0.0;
+  dm[0] = -0.0;
+  dF[0] = -0.0;
 #pragma unroll
   for (int l = 1; l <= N; ++l) {
     dm[l] = m[l] - m[0];

@@ -99,8 +99,32 @@ __device__ __forceinline__ double dbl_of_float(float f) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// h + l rounded to FP64 (one FP64 add of two exact widenings).
-__device__ __forceinline__ double dbl_of_df(df a) { return __dadd_rn(dbl_of_float(a.h), dbl_of_float(a.l)); }
+// h + l as an FP64 value, with integer operations only (no FP64 add): h's
+// 24-bit significand becomes the top of a 53-bit one and l's is added or
+// subtracted at its place, truncated below the last bit (an error below one
+// unit in the last place of the double, far below the pair's own 2^-48).
+// Expects a normalised pair (|l| <= ulp(h)/2, as every double-float
+// operation returns).
+__device__ __forceinline__ double dbl_of_df(df a) {
+  const unsigned uh = __float_as_uint(a.h), ul = __float_as_uint(a.l);
+  const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
+  if (eh == 0 || eh == 255 || el == 0) return dbl_of_float(a.h);
+  unsigned long long M = (unsigned long long)((uh & 0x7fffffu) | 0x800000u) << 29;
+  const unsigned long long ml = (unsigned long long)((ul & 0x7fffffu) | 0x800000u);
+  const int d = eh - el;                      // >= 24 for a normalised pair
+  const unsigned long long L = d >= 29 ? (d - 29 < 64 ? ml >> (d - 29) : 0ull) : ml << (29 - d);
+  int e = eh;
+  if ((uh ^ ul) & 0x80000000u) {
+    M -= L;
+    if (M < (1ull << 52)) { M <<= 1; --e; }
+  } else {
+    M += L;
+    if (M >= (1ull << 53)) { M >>= 1; ++e; }
+  }
+  const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                                  ((unsigned long long)(e + 896) << 52) | (M & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
 
 // (1+x)^gamma - 1 = x (c1 + x (c2 + x (c3 + x g(x)))), g = c4 + ... + c8 x^4
 // in float (its rounding enters at relative size x^3 2^-24).
@@ -159,9 +183,13 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
     const long long I = row + i;
     const double rp = q[I], mu = q[np + I], mv = q[2 * np + I], mw = q[3 * np + I];
     const double tp = q[4 * np + I];
-    const double ir64 = rcp_newton(rho0 + rp);
-    const double th = (Th0 + tp) * ir64;
-    const df ir = df_of_double(ir64);
+    // theta = Theta / rho in FP64 from a double-float estimate and one Newton
+    // correction (t1 = t0 + (Theta - t0 rho) / rho: the estimate's 2^-47
+    // error squares away, leaving FP64 rounding), 2 FP64 adds and 2 FMAs
+    const double rho = rho0 + rp, Th = Th0 + tp;
+    const df ir = df_rcp(df_of_double(rho));
+    const double t0 = dbl_of_df(df_mul(df_of_double(Th), ir));
+    const double th = fma(fma(-t0, rho, Th), dbl_of_df(ir), t0);
     const df muD = df_of_double(mu), mvD = df_of_double(mv), mwD = df_of_double(mw);
     const df u = df_mul(muD, ir), v = df_mul(mvD, ir), w = df_mul(mwD, ir);
     const df pp = df_mul(p0, df_eos_phi(P, df_mul(df_of_double(tp), iTh0)));
@@ -261,134 +289,6 @@ __global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const
   }
 }
 
-// ---------------------------------------------------------------- y lines
-// y-fluxes at one node: rho v and theta (FP64) for the difference form of
-// rho' and Theta', the momentum fluxes as pairs
-__device__ __forceinline__ void df_flux_y(const DfBufs& B, long long np, long long I, double& m,
-                                          double& th, df (&f)[3]) {
-  const double mu = B.q[np + I], mv = B.q[2 * np + I], mw = B.q[3 * np + I];
-  const df v = B.W[I], pp = B.W[2 * np + I];
-  m = mv;
-  th = B.W64[I];
-  f[0] = df_mul(df_of_double(mu), v);
-  f[1] = df_add(df_mul(df_of_double(mv), v), pp);
-  f[2] = df_mul(df_of_double(mw), v);
-}
-
-template <int N>
-__global__ void __launch_bounds__(128, N <= 3 ? 4 : 3) k_df_line_y(const DfParams P, const DfBufs B, int chunk) {
-  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const int nseg = P.nseg[1];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= nx) return;
-  const int z = blockIdx.z;
-  const int s0 = blockIdx.y * chunk;
-  const int s1 = min(nseg, s0 + chunk);
-  if (s0 >= s1) return;
-  const long long np = P.np;
-  const long long col = x + (long long)nx * ny * z;
-  const LineParams& P64 = P.P64;
-  double* __restrict__ T = B.T;
-  df* __restrict__ Tm = B.Tm;
-  auto nodeI = [&](int gy) -> long long { return col + (long long)nx * (gy == ny ? 0 : gy); };
-
-  double carry64[2];
-  df carry[3];
-  bool has_left = (s0 > 0) || P.per[1];
-  if (has_left) {
-    const int sp = s0 > 0 ? s0 - 1 : nseg - 1;
-    double m[N + 1], th[N + 1];
-    df fl[3][N + 1];
-#pragma unroll
-    for (int l = 0; l <= N; ++l) {
-      df f[3];
-      df_flux_y(B, np, nodeI(sp * N + l), m[l], th[l], f);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) fl[c][l] = f[c];
-    }
-    double dm[N + 1], dF[N + 1];
-    seg_diffs<N>(m, th, dm, dF);
-    carry64[0] = drow_N<N, 1>(P64, dm);
-    carry64[1] = drow_N<N, 1>(P64, dF);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) carry[c] = df_row<N, 1>(P, N, fl[c]);
-  }
-
-  double fm[N + 1], fth[N + 1];
-  df fc[3][N + 1];
-  {
-    df f[3];
-    df_flux_y(B, np, nodeI(s0 * N), fm[0], fth[0], f);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) fc[c][0] = f[c];
-  }
-  for (int s = s0; s < s1; ++s) {
-#pragma unroll
-    for (int l = 1; l <= N; ++l) {
-      df f[3];
-      df_flux_y(B, np, nodeI(s * N + l), fm[l], fth[l], f);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) fc[c][l] = f[c];
-    }
-    double tv64[2][N];
-    df tv[3][N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const long long I = nodeI(s * N + a);
-      tv64[0][a] = T[I];
-      tv64[1][a] = T[4 * np + I];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) tv[c][a] = Tm[(c + 1) * np + I];
-    }
-    double dm[N + 1], dF[N + 1];
-    seg_diffs<N>(fm, fth, dm, dF);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {   // rho' (e = 0) and Theta' (e = 1), FP64
-      const double (&d)[N + 1] = e == 0 ? dm : dF;
-      double* Tv = T + (e == 0 ? 0 : 4) * np;
-      double t0 = tv64[e][0];
-      if (!has_left && !P.open_y[0]) t0 = drow_from<N, 1>(P64, 0, d, t0);   // wall: twice
-      t0 = drow_from<N, 1>(P64, 0, d, t0);
-      Tv[nodeI(s * N)] = has_left ? t0 + carry64[e] : t0;
-#pragma unroll
-      for (int a = 1; a < N; ++a) Tv[nodeI(s * N + a)] = drow_from<N, 1>(P64, a, d, tv64[e][a]);
-      carry64[e] = drow_N<N, 1>(P64, d);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      df t0 = tv[c][0];
-      if (!has_left && !P.open_y[0]) t0 = df_row_from<N, 1>(P, 0, fc[c], t0);
-      t0 = df_row_from<N, 1>(P, 0, fc[c], t0);
-      Tm[(c + 1) * np + nodeI(s * N)] = has_left ? df_add(t0, carry[c]) : t0;
-#pragma unroll
-      for (int a = 1; a < N; ++a)
-        Tm[(c + 1) * np + nodeI(s * N + a)] = df_row_from<N, 1>(P, a, fc[c], tv[c][a]);
-      carry[c] = df_row<N, 1>(P, N, fc[c]);
-      fc[c][0] = fc[c][N];
-    }
-    fm[0] = fm[N];
-    fth[0] = fth[N];
-    has_left = true;
-  }
-  if (!P.per[1] && s1 == nseg) {
-    const long long I = nodeI(nseg * N);
-    if (P.open_y[1]) {   // partition face: the rows go to the neighbour
-      const long long Fo = x + (long long)nx * z, nf = (long long)nx * nz;
-      B.face_hi[Fo] = carry64[0];
-      B.face_hi[4 * nf + Fo] = carry64[1];
-      df* fh = reinterpret_cast<df*>(B.face_hi);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) fh[(c + 1) * nf + Fo] = carry[c];
-    } else {
-      T[I] += carry64[0] + carry64[0];
-      T[4 * np + I] += carry64[1] + carry64[1];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        Tm[(c + 1) * np + I] = df_add(Tm[(c + 1) * np + I], df_scale2(carry[c], 2.0f));
-    }
-  }
-}
-
 // ---------------------------------------------------------------- z lines + sources + stage
 
 // Momentum fluxes along DIR (1 = y, 2 = z) at one node from its momentum as
@@ -460,16 +360,21 @@ __host__ __device__ constexpr int tile_segments(int N) { return N >= 16 ? 1 : 16
 // without spills.
 __host__ __device__ constexpr int df_tile_segments(int N) { return N >= 8 ? 1 : 8 / N; }
 
-// ---------------------------------------------------------------- z lines, tiled
-// One CTA per (32 x-columns) x (a chunk of K element segments along z) x y,
-// one thread per node: block (32, K N + 1), warp = one plane of 32 columns.
-// All loads of the chunk are issued up front, the fluxes go to shared memory
-// -- the chunk's K N + 1 planes plus the N planes of the segment before it
-// (whose last row completes the chunk's first face node) -- and each thread
-// then assembles its own node: the z part, the sources, walls and the stage
-// store.  Thread row K N handles the chunk's end face: its fluxes close the
-// last segment, and at a wall it also owns the wall node.  (DIR = 1, y
-// lines, is the same scheme; only z is launched.)
+// ---------------------------------------------------------------- y and z lines, tiled
+// One CTA per (32 x-columns) x (a chunk of K element segments along DIR) x
+// the remaining coordinate, one thread per node: block (32, K N + 1), warp =
+// one plane of 32 columns.  All loads of the chunk are issued up front, the
+// fluxes go to shared memory -- the chunk's K N + 1 planes plus the N planes
+// of the segment before it (whose last row completes the chunk's first face
+// node) -- and each thread then assembles its own node: DIR = 1 adds the y
+// part into T, DIR = 2 the z part, the sources, walls and the stage store.
+// Thread row K N handles the chunk's end face: its fluxes close the last
+// segment, and at a wall it also owns the wall node.  A shared face node
+// takes its two one-sided rows as t0 + row N (t0: the running tendency plus
+// row 0), the order a partition face is completed in (xg_partition_stage),
+// so partitioned runs match single domains bit for bit.  At a partition face
+// (open_y, DIR = 1) the slab's first node takes row 0 once, and the end node
+// hands its one-sided row N to face_hi instead of doubling it.
 template <int N, int DIR>
 __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfParams P, const DfBufs B) {
   constexpr int K = df_tile_segments(N);
@@ -498,6 +403,7 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   const int vslot = DIR == 1 ? 0 : 1;            // v or w in W
   const LineParams& P64 = P.P64;
 
+  const bool open_lo = DIR == 1 && P.open_y[0], open_hi = DIR == 1 && P.open_y[1];
   const int own = s0 * N + ty;
   const bool owns = xin && (ty < kc * N || (ty == kc * N && s0 + kc == nseg && !per));
   const bool main_plane = xin && ty <= kc * N;   // the extra row fills the end face
@@ -577,27 +483,30 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
   // the node's segment k and local index a; the wall node is row N of the last
   const int k = ty < kc * N ? ty / N : kc - 1;
   const int a = ty < kc * N ? ty - k * N : N;
+  // the end node of an open slab end: its rows go to the neighbour
+  const bool hand = open_hi && a == N;
+  const long long Fo = x + (long long)P.n[0] * other, nf = (long long)P.n[0] * P.n[2];
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     double d[N + 1];
-    d[0] = 0.0;
+    d[0] = -0.0;
 #pragma unroll
     for (int l = 1; l <= N; ++l) d[l] = Ds[e][N + k * N + l][tx];
     double t = t64[e];
     if (a == N) {                                 // wall node: its one-sided row counts twice
       const double r = drow_N<N, DIR>(P64, d);
+      if (hand) B.face_hi[(e == 0 ? 0 : 4) * nf + Fo] = r;
       t = t + (r + r);
     } else if (a > 0) {
       t = drow_from<N, DIR>(P64, a, d, t);
-    } else if (k > 0 || has_left) {               // shared face: both one-sided halves
+    } else if (k > 0 || has_left) {               // shared face: t0 + row N of the left
       double dl[N + 1];
-      dl[0] = 0.0;
+      dl[0] = -0.0;
 #pragma unroll
       for (int l = 1; l <= N; ++l) dl[l] = Ds[e][k * N + l][tx];
-      t = drow_from<N, DIR>(P64, 0, d, t);
-      t = drow_from<N, DIR>(P64, N, dl, t);
-    } else {                                      // wall at the line start
-      t = drow_from<N, DIR>(P64, 0, d, t);
+      t = drow_from<N, DIR>(P64, 0, d, t) + drow_N<N, DIR>(P64, dl);
+    } else {                                      // line start: a wall (twice) or open (once)
+      if (!open_lo) t = drow_from<N, DIR>(P64, 0, d, t);
       t = drow_from<N, DIR>(P64, 0, d, t);
     }
     t64[e] = t;
@@ -609,6 +518,7 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
     for (int l = 0; l <= N; ++l) f[l] = Fm[c][N + k * N + l][tx];
     if (a == N) {
       const df r = df_row<N, DIR>(P, N, f);
+      if (hand) reinterpret_cast<df*>(B.face_hi)[(c + 1) * nf + Fo] = r;
       tm[c] = df_add(tm[c], df_scale2(r, 2.0f));
     } else if (a > 0) {
       tm[c] = df_row_from<N, DIR>(P, a, f, tm[c]);
@@ -619,11 +529,12 @@ __global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfPar
       tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
       tm[c] = df_add(tm[c], df_row<N, DIR>(P, N, fl));
     } else {
-      tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
+      if (!open_lo) tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
       tm[c] = df_row_from<N, DIR>(P, 0, f, tm[c]);
     }
   }
   if (DIR == 1) {
+    if (hand) return;                             // completed after the exchange
     B.T[I] = t64[0];
     B.T[4 * np + I] = t64[1];
 #pragma unroll
