@@ -4,9 +4,12 @@ Default workload (the cyclone box): 1024 x 1024 x 20 km, 128 x 128 x 16
 order-4 elements, doubly periodic sides, no-flux bottom and top
 (512 x 512 x 65 = 17,039,360 nodes), stable sounding, f-plane, vortex and
 ring-plus-cells heating, dt = 0.1 s.  The timed arm is the FP64-accurate
-double-float path (--precision df64, the default); the same line reports
-plain native FP64 on the same workload and GPU, and the relative L2 error
-of both against the FP64 oracle.  One bench step is one SSP-RK3
+mixed path (--precision df64, the default: FP64 state, rho' and Theta' on
+the FP64 pipe, the momentum in double-float arithmetic on the FP32 pipes);
+the same line reports plain native FP64 on the same workload and GPU, the
+FP32, batched and closure forms, and the relative L2 errors against the
+oracle (at the timed full-size state against its extended-precision
+evaluation).  One bench step is one SSP-RK3
 step = three passes of the whole hot path (each pass: primitives, fluxes,
 sum-factorised derivatives, DSS, inverse mass, sources, walls, stage
 update), so
@@ -1195,7 +1198,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
-                    help="df64: FP64-accurate double-float on the FP32 pipes (default); "
+                    help="df64: the FP64-accurate mixed FP64 / double-float path (default); "
                          "fp64: native FP64; fp32: the FP32 precision form")
     ap.add_argument("--contraction", choices=["fma", "tf32x3"], default="fma",
                     help="with --precision fp32: x and y contractions on the CUDA cores (fma) or "
