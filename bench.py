@@ -57,6 +57,11 @@ KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 KERNEL_NAMES = {0: ("k_line_x", "k_line_y", "k_line_z"),
                 2: ("k_df_line_x", "k_df_tline_y", "k_df_tline_z"),
                 1: ("k_f_plane_xy", "-", "k_f_tline")}
+# the FP32 plane kernel of each tensor-core contraction mode (by --contraction
+# name: the mode's constant, the kernel; by mode constant: the kernel)
+CONTRACTIONS = {"tf32x3": (lambda xg: xg.XG_CONTRACT_TF32X3, "k_f_plane_xy_tc"),
+                "f16x3": (lambda xg: xg.XG_CONTRACT_F16X3, "k_f_plane_xy_h16")}
+PLANE_KERNEL_OF = {1: "k_f_plane_xy_tc", 2: "k_f_plane_xy_h16"}
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -271,6 +276,7 @@ def random_state_errors(name, xg, torch, dev):
     out = {p: oracle_error_of_gpu(sw, xg, torch, dev, v)
            for p, v in (("df64", xg.XG_DF64), ("fp64", xg.XG_FP64), ("fp32", xg.XG_FP32))}
     out["fp32_tf32x3_contraction"] = oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32, xg.XG_CONTRACT_TF32X3)
+    out["fp32_f16x3_contraction"] = oracle_error_of_gpu(sw, xg, torch, dev, xg.XG_FP32, xg.XG_CONTRACT_F16X3)
     return out
 
 
@@ -472,7 +478,8 @@ def make_ctx(xg, torch, wl, dev, precision=0):
 _Z_VALUES = 5 + 3 + 5 + 1 + 5 * 2 / 3 + 5
 KERNEL_VALUES_PER_NODE = {"k_line_x": 14, "k_line_y": 16, "k_line_z": _Z_VALUES,
                           "k_df_line_x": 14, "k_df_tline_y": 16, "k_df_tline_z": _Z_VALUES,
-                          "k_f_plane_xy": 13, "k_f_plane_xy_tc": 13, "k_f_tline": _Z_VALUES - 1}
+                          "k_f_plane_xy": 13, "k_f_plane_xy_tc": 13, "k_f_plane_xy_h16": 13,
+                          "k_f_tline": _Z_VALUES - 1}
 # The method's own traffic per node and stage: q and S in,
 # q out, plus q^n in stages 2 and 3.
 STAGE_BYTES_PER_NODE = (88 + 128 + 128) / 3.0
@@ -524,9 +531,9 @@ def run_xg(args, world, rank, local):
 
     ctx = make_ctx(xg, torch, wl, dev, prec)
     knames = KERNEL_NAMES[prec]
-    if prec == xg.XG_FP32 and args.contraction == "tf32x3":
-        xg.xg_set_contraction(ctx, xg.XG_CONTRACT_TF32X3)
-        knames = ("k_f_plane_xy_tc",) + knames[1:]
+    if prec == xg.XG_FP32 and args.contraction != "fma":
+        xg.xg_set_contraction(ctx, CONTRACTIONS[args.contraction][0](xg))
+        knames = (CONTRACTIONS[args.contraction][1],) + knames[1:]
     ms_max, kms, klaunch, clk = timed_steps(xg, torch, ctx, dt, K, Wm, stream, world, local, True)
     value = gdof(ms_max, K)
 
@@ -603,7 +610,7 @@ def run_xg(args, world, rank, local):
         xg.xg_destroy(c2)
         return {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": dtype,
                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
-                "kernel_ms_per_launch": {(("k_f_plane_xy_tc",) + KERNEL_NAMES[p][1:] if contract
+                "kernel_ms_per_launch": {((PLANE_KERNEL_OF[contract],) + KERNEL_NAMES[p][1:] if contract
                                           else KERNEL_NAMES[p])[i]: round(kmsp[i] / max(klp[i], 1), 4)
                                          for i in range(3) if klp[i]}}
     plain = side_run(xg.XG_FP64, "f64") if prec != xg.XG_FP64 and not args.no_plain else None
@@ -611,6 +618,7 @@ def run_xg(args, world, rank, local):
     if fp32 is not None and wl["N"] == 4:
         # the same form with the x and y contractions on the tensor cores
         fp32["tf32x3_contraction"] = side_run(xg.XG_FP32, "f32", xg.XG_CONTRACT_TF32X3)
+        fp32["f16x3_contraction"] = side_run(xg.XG_FP32, "f32", xg.XG_CONTRACT_F16X3)
     batched = None
     if not args.no_plain and not args.no_batch:
         batched = batch_measure(xg, torch, dev, stream, world, local, max(1, min(K, 10)), 3,
@@ -632,6 +640,8 @@ def run_xg(args, world, rank, local):
         if sw["N"] == 4:
             got["fp32_tf32x3_contraction"] = gpu_rhs(sw, xg, torch, dev, xg.XG_FP32,
                                                      xg.XG_CONTRACT_TF32X3)
+            got["fp32_f16x3_contraction"] = gpu_rhs(sw, xg, torch, dev, xg.XG_FP32,
+                                                    xg.XG_CONTRACT_F16X3)
         # the extended-precision oracle at sampled nodes of the sample
         n_all = got["fp64"].shape[1]
         nodes = np.unique(np.concatenate([np.arange(0, n_all, 331),
@@ -644,7 +654,8 @@ def run_xg(args, world, rank, local):
         l2["meets_1e-12"] = {p: bool(max(l2["vs_extended_oracle"][p]) <= 1e-12 and max(l2[p]) <= 1e-12)
                              for p in ("fp64", "df64")}
         l2["fp32_vs_oracle_of_fp32_rounded_state"] = {
-            p: rel_err(got[p], ref32) for p in ("fp32", "fp32_tf32x3_contraction") if p in got}
+            p: rel_err(got[p], ref32) for p in ("fp32", "fp32_tf32x3_contraction", "fp32_f16x3_contraction")
+            if p in got}
         l2["fp32_state_rounding_floor"] = rel_err(ref32, ref)
         # the same sample at a seeded smooth random state plus the vortex, where no
         # tendency is a cancellation residual
@@ -1200,9 +1211,10 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
                     help="df64: the FP64-accurate mixed FP64 / double-float path (default); "
                          "fp64: native FP64; fp32: the FP32 precision form")
-    ap.add_argument("--contraction", choices=["fma", "tf32x3"], default="fma",
+    ap.add_argument("--contraction", choices=["fma", "tf32x3", "f16x3"], default="fma",
                     help="with --precision fp32: x and y contractions on the CUDA cores (fma) or "
-                         "on the tensor cores (tf32x3, order 4)")
+                         "on the tensor cores (tf32x3: TF32 head/tail split; f16x3: half-precision "
+                         "head/tail split with a scale per segment; order 4)")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain-FP64 and FP32-form comparison runs")
     ap.add_argument("--instances", type=int, default=96,

@@ -161,10 +161,17 @@ xg_status xg_diagnostics(xg_ctx* ctx, double out[5], void* stream);
  *                       entry split into a TF32 head and tail and three
  *                       products summed (head*head + tail*head + head*tail);
  *                       order 4 only
+ *   XG_CONTRACT_F16X3   the tensor cores with IEEE half-precision operands
+ *                       (tcgen05.mma kind f16, FP32 accumulation): the
+ *                       differences of each segment's fluxes against its first
+ *                       value, scaled by a power of two per segment into half
+ *                       range and split into three halves (exact for FP32
+ *                       values), against Dm split likewise; six partial
+ *                       products in two instructions of K = 16; order 4 only
  * The z contraction stays on the CUDA cores.  Errors: XG_ERR_ARG (NULL, an
- * unknown mode), XG_ERR_UNSUPPORTED (XG_CONTRACT_TF32X3 on a context that
+ * unknown mode), XG_ERR_UNSUPPORTED (a tensor-core mode on a context that
  * is not XG_FP32 or not of order 4). */
-enum { XG_CONTRACT_FMA = 0, XG_CONTRACT_TF32X3 = 1 };
+enum { XG_CONTRACT_FMA = 0, XG_CONTRACT_TF32X3 = 1, XG_CONTRACT_F16X3 = 2 };
 xg_status xg_set_contraction(xg_ctx* ctx, int mode);
 
 /* Kernel timing (Sec. 5.4 measures its kernels against a roofline; this is

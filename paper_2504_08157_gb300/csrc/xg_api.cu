@@ -16,6 +16,7 @@
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
 #include "xg_kernels_df.cuh"
+#include "xg_plane_h16.cuh"
 #include "xg_plane_tc.cuh"
 #include "xg_setup.h"
 #include "xg_ctx.h"
@@ -253,6 +254,13 @@ cudaError_t configure_n(xg_ctx* c) {
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_plane_xy<N>, xg::PlaneLayoutF<N>::bytes);
   if (N == xg::PlaneTcLayout::N && e == cudaSuccess)
     e = xg::raise_dynamic_smem(xg::k_f_plane_xy_tc, xg::PlaneTcLayout::bytes);
+  if (N == xg::PlaneH16Layout::N && e == cudaSuccess) {
+    e = xg::raise_dynamic_smem(xg::k_f_plane_xy_h16, xg::PlaneH16Layout::bytes);
+    // two CTAs of 111 KB per SM need the whole shared-memory carveout
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)xg::k_f_plane_xy_h16, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               100);
+  }
   return e;
 }
 
@@ -291,6 +299,9 @@ void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
   if (N == xg::PlaneTcLayout::N && c->contract == XG_CONTRACT_TF32X3) {
     static_assert(xg::plane_elems_f32(4) == xg::PlaneTcLayout::E, "same tiles");
     xg::k_f_plane_xy_tc<<<gp, xg::kPlaneTcThreads, xg::PlaneTcLayout::bytes, st>>>(c->Pf, B);
+  } else if (N == xg::PlaneH16Layout::N && c->contract == XG_CONTRACT_F16X3) {
+    static_assert(xg::plane_elems_f32(4) == xg::PlaneH16Layout::E, "same tiles");
+    xg::k_f_plane_xy_h16<<<gp, xg::kPlaneH16Threads, xg::PlaneH16Layout::bytes, st>>>(c->Pf, B);
   } else {
     xg::k_f_plane_xy<N><<<gp, xg::kPlaneThreads, xg::PlaneLayoutF<N>::bytes, st>>>(c->Pf, B);
   }
@@ -735,8 +746,9 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
 
 xg_status xg_set_contraction(xg_ctx* c, int mode) {
   if (!c) return XG_ERR_ARG;
-  if (mode != XG_CONTRACT_FMA && mode != XG_CONTRACT_TF32X3) return XG_ERR_ARG;
-  if (mode == XG_CONTRACT_TF32X3 && (!c->f32 || c->d.order != xg::PlaneTcLayout::N))
+  if (mode != XG_CONTRACT_FMA && mode != XG_CONTRACT_TF32X3 && mode != XG_CONTRACT_F16X3) return XG_ERR_ARG;
+  static_assert(xg::PlaneTcLayout::N == xg::PlaneH16Layout::N, "both tensor-core forms are of one order");
+  if (mode != XG_CONTRACT_FMA && (!c->f32 || c->d.order != xg::PlaneTcLayout::N))
     return XG_ERR_UNSUPPORTED;
   c->contract = mode;
   return XG_OK;

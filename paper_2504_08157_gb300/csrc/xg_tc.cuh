@@ -50,6 +50,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);          // M / 16
 }
 
+// Instruction descriptor of kind::f16 with IEEE half-precision A and B (both
+// K-major; A and B always of the same type), FP32 accumulator, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4)                              // D format: F32
+         | (0u << 7)                            // A format: F16
+         | (0u << 10)                           // B format: F16
+         | ((uint32_t)(N >> 3) << 17)           // N / 8
+         | ((uint32_t)(M >> 4) << 24);          // M / 16
+}
+
 // The same for 32-bit elements (TF32 operands): a core matrix row holds 4.
 __host__ __device__ constexpr int kmajor32(int R, int r, int k) {
   return (k >> 2) * (R * 4) + (r >> 3) * 32 + (r & 7) * 4 + (k & 3);
@@ -84,7 +94,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
-// D[tmem] (+)= A[adesc] * B[bdesc]^T, issued by one thread
+// D[tmem] (+)= A[adesc] * B[bdesc]^T with 16-bit operands (bfloat16 or half,
+// as the instruction descriptor says), issued by one thread
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          bool accumulate) {
   asm volatile(

@@ -24,7 +24,7 @@ XG_HOST, XG_DEVICE = 0, 1
 XG_FP64, XG_FP32, XG_DF64 = 0, 1, 2
 XG_SCHED_ROUND_ROBIN, XG_SCHED_LPT, XG_SCHED_DYNAMIC = 0, 1, 2
 XG_MLP_FP32, XG_MLP_BF16 = 0, 1
-XG_CONTRACT_FMA, XG_CONTRACT_TF32X3 = 0, 1
+XG_CONTRACT_FMA, XG_CONTRACT_TF32X3, XG_CONTRACT_F16X3 = 0, 1, 2
 XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5, 5893
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",

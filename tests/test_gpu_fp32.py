@@ -113,7 +113,7 @@ def test_fp32_tc_vortex_rhs(cuda_device):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("contraction", [0, 1], ids=["fma", "tf32x3"])
+@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fma", "tf32x3", "f16x3"])
 def test_fp32_full_size_tc_vortex_rhs_sampled(cuda_device, contraction):
     """The full cyclone box at the bench's own initial state (pure vortex),
     sampled nodes, against the oracle of the FP32-rounded state.  At full
@@ -122,9 +122,10 @@ def test_fp32_full_size_tc_vortex_rhs_sampled(cuda_device, contraction):
     alone moves them by ~3e-4 and ~1e-4 (test_precision_floor), so the 1e-5
     bar of the form cannot hold there against the FP64 state.  Against the
     state the form holds: the momentum tendencies within 1e-5 and rho' and
-    Theta' within 3e-5 for the CUDA-core contraction (difference form), 2e-3
-    for the tensor-core mode, which keeps the plain form of those two
-    contractions (its products read the raw fluxes in place)."""
+    Theta' within 3e-5 for the CUDA-core contraction and the half-precision
+    tensor-core mode (both in difference form), 2e-3 for the TF32 mode, which
+    keeps the plain form of those two contractions (its products read the raw
+    fluxes in place)."""
     import test_gpu_parity as P
     wl = W.tc()
     got, _, (m, phys, base, nodes) = P._full_size_sampled(wl, FP32, contraction)
@@ -132,14 +133,14 @@ def test_fp32_full_size_tc_vortex_rhs_sampled(cuda_device, contraction):
     err = rel_l2_per_var(got, ref32)
     print("fp32 vortex, contraction", contraction, err)
     assert np.all(err[1:4] <= RHS_TOL32), err
-    assert np.all(err[[0, 4]] <= (3e-5 if contraction == 0 else 2e-3)), err
+    assert np.all(err[[0, 4]] <= (2e-3 if contraction == TF32X3 else 3e-5)), err
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("contraction", [0, 1], ids=["fma", "tf32x3"])
+@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fma", "tf32x3", "f16x3"])
 def test_fp32_full_size_tc_rhs_sampled(cuda_device, contraction):
     """The full cyclone box in the bench's launch configuration, sampled
-    nodes, both contraction modes."""
+    nodes, every contraction mode."""
     import test_gpu_parity as P
     got, ref, _ = P._full_size_sampled(W.tc(state="random"), FP32, contraction)
     err = rel_l2_per_var(got, ref)
@@ -181,8 +182,11 @@ def test_mass_conserved_on_gpu(cuda_device, prec, tol):
 # ------------------------------------------------------------------ tensor-core contractions
 
 TF32X3 = 1   # XG_CONTRACT_TF32X3
+F16X3 = 2    # XG_CONTRACT_F16X3
+TC_MODES = pytest.mark.parametrize("mode", [TF32X3, F16X3], ids=["tf32x3", "f16x3"])
 
 
+@TC_MODES
 @pytest.mark.parametrize("nel,periodic", [
     ((1, 1, 1), (False, False, False)),
     ((2, 2, 2), (True, True, True)),
@@ -190,25 +194,44 @@ TF32X3 = 1   # XG_CONTRACT_TF32X3
     ((9, 10, 2), (True, False, False)),     # one full 8 x 8 element tile and ragged ones
     ((17, 9, 2), (False, True, True)),
 ])
-def test_fp32_tf32x3_contraction_rhs(cuda_device, nel, periodic):
-    """The x and y contractions on the tensor cores (TF32 head/tail split,
-    three products): within the FP32 form's bar of the oracle, on tiles that
-    are full, ragged, walled and periodic."""
+def test_fp32_tensor_core_contraction_rhs(cuda_device, mode, nel, periodic):
+    """The x and y contractions on the tensor cores (TF32 head/tail split, or
+    half-precision head/tail split with a scale per segment): within the
+    FP32 form's bar of the oracle, on tiles that are full, ragged, walled and
+    periodic."""
     L = tuple(1000.0 * n for n in nel)
     wl = W.box(nel, 4, (0.0, 0.0, 0.0), L, periodic, seed=7 * sum(nel) + 1)
     with GpuContext(wl, precision=FP32) as g:
-        g.xg.xg_set_contraction(g.ctx, TF32X3)
+        g.xg.xg_set_contraction(g.ctx, mode)
         got = g.rhs()
     err = rel_l2_per_var(got, oracle_rhs(wl))
     assert np.all(err <= RHS_TOL32), err
 
 
-def test_fp32_tf32x3_contraction_tc_scaled_and_steps(cuda_device):
+@pytest.mark.parametrize("h", [2.0, 1.0e5], ids=["2m", "100km"])
+def test_fp32_f16x3_contraction_element_sizes(cuda_device, h):
+    """Half precision covers 2^-24 .. 65504 only: x and y element sizes of
+    2 m and of 100 km put the derivative matrix and the flux differences far
+    outside it, and the per-segment and per-direction powers of two bring
+    them back
+    (without them a 100 km element's Dm entries, ~1e-5, would be subnormal
+    halves)."""
+    nel, periodic = (9, 10, 2), (True, False, False)
+    wl = W.box(nel, 4, (0.0, 0.0, 0.0), (h * nel[0], h * nel[1], 1000.0 * nel[2]), periodic, seed=31)
+    with GpuContext(wl, precision=FP32) as g:
+        g.xg.xg_set_contraction(g.ctx, F16X3)
+        got = g.rhs()
+    err = rel_l2_per_var(got, oracle_rhs(wl))
+    assert np.all(err <= RHS_TOL32), err
+
+
+@TC_MODES
+def test_fp32_tensor_core_contraction_tc_scaled_and_steps(cuda_device, mode):
     """The cyclone box (scaled) at a random state: one RHS within the bar;
     20 steps stay within 1e-5 of the CUDA-core contraction's run."""
     wl = W.tc(nel=(16, 16, 4), state="random")
     with GpuContext(wl, precision=FP32) as g:
-        g.xg.xg_set_contraction(g.ctx, TF32X3)
+        g.xg.xg_set_contraction(g.ctx, mode)
         got = g.rhs()
         g.step(20)
         q_tc = g.state()
@@ -220,12 +243,13 @@ def test_fp32_tf32x3_contraction_tc_scaled_and_steps(cuda_device):
     assert np.all(rel_l2_per_var(q_tc, q_fma) <= 1e-5)
 
 
-def test_tf32x3_contraction_is_fp32_order_4_only(cuda_device):
+@TC_MODES
+def test_tensor_core_contraction_is_fp32_order_4_only(cuda_device, mode):
     from paper_2504_08157_gb300 import xg
     for prec, N in ((FP64, 4), (DF64, 4), (FP32, 3)):
         wl = W.box((2, 2, 2), N, (0.0, 0.0, 0.0), (2000.0, 2000.0, 2000.0), (True, True, False))
         with GpuContext(wl, precision=prec) as g:
             with pytest.raises(xg.XgError) as e:
-                xg.xg_set_contraction(g.ctx, TF32X3)
+                xg.xg_set_contraction(g.ctx, mode)
             assert e.value.status == xg.XG_ERR_UNSUPPORTED
             xg.xg_set_contraction(g.ctx, 0)
