@@ -1065,7 +1065,10 @@ def run_closure(args, world, rank, local):
     gain = picks[best][0]
     ev = CL.evaluate_gains(W.closure_case, 100, nel, cands[best], args.eval_steps, dev,
                            tuple(sorted({0.0, 1.0, gain})))
+    # the target itself as the correction (no network): exact, and low-pass filtered
+    study = CL.correction_study(W.closure_case, 101, nel, args.eval_steps, dev)
     vs_refined = {"plain": ev[0.0], "closure": ev[1.0], "closure_at_chosen_gain": ev[gain],
+                  "exact_target_as_correction": study,
                   "chosen_gain": gain, "chosen_model": best,
                   "gain_selection": {"validation_run_seed": 101,
                                      "errors": {k: {repr(g): e for g, e in picks[k][1].items()}

@@ -104,6 +104,23 @@ xg_status xg_mlp_forward(const float* params, const float* X, long long ld, long
 xg_status xg_closure_set(xg_ctx* ctx, const float* params, const float* in_mean,
                          const float* in_scale, const float* out_scale, void* stream);
 
+/* A prescribed correction instead of the network's, on an XG_FP32
+ * context: from now on xg_rhs and xg_step evaluate L(q) + C in every stage
+ * (before the wall condition), with C [5][Np] (device, FP64) rounded to FP32
+ * and copied.  It replaces an enabled network (xg_closure_set replaces it in
+ * turn); C NULL removes a prescribed correction.  This is how a correction
+ * computed elsewhere -- e.g. the exact refined-minus-coarse tendency of the
+ * training target, held over a step -- is tested in a coarse run.  Errors:
+ * XG_ERR_ARG, XG_ERR_UNSUPPORTED (not XG_FP32), XG_ERR_OOM, XG_ERR_CUDA. */
+xg_status xg_correction_set(xg_ctx* ctx, const double* C, void* stream);
+
+/* The closure's training targets as one elementwise operation over n FP64
+ * device values: out = s (a - b), e.g. R L_fine(q_fine) - L_coarse(R q_fine)
+ * (s = 1) or (R q_fine(t + dt) - S_coarse(R q_fine(t))) / dt (s = 1 / dt).
+ * out may alias a or b.  Errors: XG_ERR_ARG (NULL, n < 0), XG_ERR_CUDA. */
+xg_status xg_closure_target(const double* a, const double* b, double s, long long n, double* out,
+                            void* stream);
+
 /* The failure path of the tensor-core kernels' bounded waits, exercised on
  * purpose: one CTA allocates tensor memory, waits at most limit_ns
  * nanoseconds (1 .. 1e9) on an mbarrier that nothing completes, then frees

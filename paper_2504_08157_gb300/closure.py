@@ -90,14 +90,14 @@ def sample_pairs(case, seeds, coarse_nel, snapshots, steps_between, samples, dev
                 xg.xg_features(cctx, X)
                 if target == "rhs":
                     xg.xg_restrict(fctx, cctx, _rhs(fctx, dev), rc_f)
-                    T = rc_f - _rhs(cctx, dev)
+                    T = xg.xg_closure_target(rc_f, _rhs(cctx, dev))
                 else:
                     q_save = _state(fctx, dev)
                     xg.xg_step(fctx, fwl["dt"], 2)          # two refined steps = one coarse step
                     xg.xg_restrict(fctx, cctx, _state(fctx, dev), rc_f)
                     xg.xg_set_state(fctx, q_save)          # the refined run continues unchanged
                     xg.xg_step(cctx, cwl["dt"], 1)
-                    T = (rc_f - _state(cctx, dev)) / cwl["dt"]
+                    T = xg.xg_closure_target(rc_f, _state(cctx, dev), 1.0 / cwl["dt"])
                 u = rng.uniform(sample_seed, samples, offset=draw)
                 draw += samples
                 idx = torch.from_numpy(np.minimum((u * npc).astype(np.int64), npc - 1)).to(dev)
@@ -260,3 +260,68 @@ def select_gain(case, seed, coarse_nel, model, coarse_steps, dev,
     plain = e[0.0]
     score = {g: sum(v / max(p, 1e-300) for v, p in zip(errs, plain)) / 5 for g, errs in e.items()}
     return min(gains, key=lambda g: (score[g], g)), e
+
+
+def correction_study(case, seed, coarse_nel, coarse_steps, dev, filter_order=2):
+    """What the training target is worth in a coarse run, measured with the
+    exact target instead of a network: three coarse runs from the
+    restriction of the refined initial field over ``coarse_steps`` coarse
+    steps, judged as in evaluate_gains --
+      plain:     no correction;
+      exact:     in every coarse step the exact target of sample_pairs,
+                 R L_f(q_f) - L_c(R q_f) at the refined run's state at the
+                 start of the step (xg_correction_set);
+      filtered:  the same correction passed through a low-pass filter (its
+                 interpolant on the same elements at order ``filter_order``,
+                 two xg_restrict calls), which keeps most of its norm.
+    Returns the per-variable errors of the three runs and the filtered
+    correction's share of the exact one's norm at t = 0."""
+    torch = _torch()
+    fine_nel = tuple(2 * n for n in coarse_nel)
+    fwl = case(seed, nel=fine_nel)
+    cwl = case(seed, nel=coarse_nel)
+    mwl = case(seed, nel=coarse_nel, N=filter_order)
+    ctxs = []
+    try:
+        for w in (fwl, cwl, cwl, cwl, cwl, mwl):
+            ctxs.append(make_ctx(w, dev))
+        fctx, probe, plain, exact, filt, low = ctxs
+        npc, npm = xg.xg_mesh_np(probe), xg.xg_mesh_np(low)
+        Z = lambda n: torch.empty((5, n), dtype=torch.float64, device=dev)
+        Rq, RL, Tm, Tf = Z(npc), Z(npc), Z(npm), Z(npc)
+        xg.xg_restrict(fctx, probe, _state(fctx, dev), Rq)
+        q0 = Rq.clone()
+        for c in (plain, exact, filt):
+            xg.xg_set_state(c, q0)
+        xg.xg_step(plain, cwl["dt"], coarse_steps)
+        share = None
+        for k in range(coarse_steps):
+            if k:
+                xg.xg_restrict(fctx, probe, _state(fctx, dev), Rq)
+            xg.xg_restrict(fctx, probe, _rhs(fctx, dev), RL)
+            xg.xg_set_state(probe, Rq)
+            T = xg.xg_closure_target(RL, _rhs(probe, dev))
+            xg.xg_restrict(probe, low, T, Tm)
+            xg.xg_restrict(low, probe, Tm, Tf)
+            if share is None:
+                share = [float(torch.linalg.norm(Tf[v]) / torch.linalg.norm(T[v]).clamp_min(1e-300))
+                         for v in range(5)]
+            xg.xg_correction_set(exact, T)
+            xg.xg_correction_set(filt, Tf)
+            xg.xg_step(exact, cwl["dt"], 1)
+            xg.xg_step(filt, cwl["dt"], 1)
+            xg.xg_step(fctx, fwl["dt"], 2)                 # the refined step is half the coarse one
+        xg.xg_restrict(fctx, probe, _state(fctx, dev), Rq)
+        ref0 = Rq - q0
+        err = lambda c: [float(torch.linalg.norm(_state(c, dev)[v] - Rq[v]) /
+                               torch.linalg.norm(ref0[v]).clamp_min(1e-300)) for v in range(5)]
+        return dict(plain=err(plain), exact=err(exact), filtered=err(filt), filtered_norm_share=share,
+                    filter="interpolant of order %d on the same elements" % filter_order,
+                    what="relative L2 distance from the restricted refined state after %d coarse "
+                         "steps, per variable, relative to the refined run's change, of coarse runs "
+                         "with no correction, the exact training target as correction, and that "
+                         "target low-pass filtered" % coarse_steps)
+    finally:
+        for c in ctxs:
+            xg.xg_destroy(c)
+

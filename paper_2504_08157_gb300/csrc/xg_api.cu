@@ -402,8 +402,10 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
     xg::FBufs F;
     F.C = nullptr;
     if (c->closure) {
-      const cudaError_t e = closure_launch(c, (const float*)q, st);
-      if (e != cudaSuccess) return e;
+      if (!c->cl_fixed) {
+        const cudaError_t e = closure_launch(c, (const float*)q, st);
+        if (e != cudaSuccess) return e;
+      }
       F.C = c->cl_C;
     }
     F.q = (const float*)q;

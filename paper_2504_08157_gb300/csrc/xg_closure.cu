@@ -669,7 +669,30 @@ void closure_free(xg_ctx* c) {
   c->cl_pack = nullptr;
   c->cl_C = nullptr;
   c->closure = false;
+  c->cl_fixed = false;
 }
+
+namespace xg {
+
+// out = s (a - b), FP64 (out may alias a or b: each element is read before it is written)
+__global__ void k_scaled_difference(const double* a, const double* b, double s, long long n, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = s * (a[i] - b[i]);
+}
+
+// dst = (float) src, rounded to nearest
+__global__ void k_round_to_f32(const double* __restrict__ src, long long n, float* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
+}
+
+inline unsigned stream_grid(long long n) {
+  return (unsigned)std::max(1LL, std::min((n + 255) / 256, 152LL * 16));
+}
+
+}  // namespace xg
 
 namespace {
 
@@ -946,7 +969,42 @@ xg_status xg_closure_set(xg_ctx* c, const float* params, const float* in_mean, c
     return cuda_status(e, "xg_closure_set");
   }
   c->closure = true;
+  c->cl_fixed = false;
   return XG_OK;
+}
+
+xg_status xg_correction_set(xg_ctx* c, const double* C, void* stream) {
+  if (!c) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (!C) {
+    if (c->cl_fixed) c->closure = c->cl_fixed = false;
+    return XG_OK;
+  }
+  if (!c->f32) return XG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = 5 * c->np;
+  cudaError_t e = cudaSuccess;
+  if (!c->cl_C) e = cudaMalloc((void**)&c->cl_C, sizeof(float) * (size_t)n);
+  if (e == cudaSuccess) {
+    xg::k_round_to_f32<<<xg::stream_grid(n), 256, 0, st>>>(C, n, c->cl_C);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    closure_free(c);
+    return cuda_status(e, "xg_correction_set");
+  }
+  c->closure = true;
+  c->cl_fixed = true;
+  return XG_OK;
+}
+
+xg_status xg_closure_target(const double* a, const double* b, double s, long long n, double* out,
+                            void* stream) {
+  if (!a || !b || !out || n < 0) return XG_ERR_ARG;
+  if (n == 0) return XG_OK;
+  xg::k_scaled_difference<<<xg::stream_grid(n), 256, 0, (cudaStream_t)stream>>>(a, b, s, n, out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? XG_OK : cuda_status(e, "xg_closure_target");
 }
 
 }  // extern "C"

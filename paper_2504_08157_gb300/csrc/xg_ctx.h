@@ -54,6 +54,7 @@ struct xg_ctx {
   // learned closure (XG_FP32 only): packed bfloat16 network and the
   // correction of the current stage's input state
   bool closure = false;
+  bool cl_fixed = false;  // C is a prescribed correction (xg_correction_set), not the network's
   void* cl_pack = nullptr;
   float* cl_C = nullptr;
   int cl_grid = 0;       // persistent grid of the closure kernel

@@ -36,7 +36,7 @@ __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_cre
            "xg_batch_get_tuning", "xg_batch_barrier_selftest", "xg_batch_destroy",
            "XG_SCHED_ROUND_ROBIN", "XG_SCHED_LPT", "XG_SCHED_DYNAMIC",
            "xg_features", "xg_restrict", "xg_column_stats", "xg_mlp_loss_grad", "xg_mlp_adam",
-           "xg_mlp_forward", "xg_closure_set", "xg_tc_wait_selftest", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
+           "xg_mlp_forward", "xg_closure_set", "xg_correction_set", "xg_closure_target", "xg_tc_wait_selftest", "XG_MLP_FP32", "XG_MLP_BF16", "XG_CLOSURE_IN",
            "XG_CLOSURE_HIDDEN", "XG_CLOSURE_OUT", "XG_CLOSURE_PARAMS",
            "xg_dynamics", "xg_set_dynamics", "xg_dynamics_tendency", "xg_ri_velocity",
            "xg_imex_opts", "xg_imex_stats", "xg_step_imex", "xg_linear_operator", "XG_HOST", "XG_DEVICE",
@@ -176,6 +176,10 @@ def library():
     lib.xg_tc_wait_selftest.argtypes = [LL, P]
     lib.xg_closure_set.restype = I
     lib.xg_closure_set.argtypes = [P, P, P, P, P, P]
+    lib.xg_correction_set.restype = I
+    lib.xg_correction_set.argtypes = [P, P, P]
+    lib.xg_closure_target.restype = I
+    lib.xg_closure_target.argtypes = [P, P, ctypes.c_double, LL, P, P]
     lib.xg_set_dynamics.restype = I
     lib.xg_set_dynamics.argtypes = [P, ctypes.POINTER(xg_dynamics)]
     lib.xg_dynamics_tendency.restype = I
@@ -587,6 +591,34 @@ def xg_closure_set(ctx, params=None, in_mean=None, in_scale=None, out_scale=None
         return
     _check(library().xg_closure_set(ctx, _f32(params), _f32(in_mean), _f32(in_scale),
                                     _f32(out_scale), _default_stream(stream)), "xg_closure_set")
+
+
+def xg_correction_set(ctx, C=None, stream=None):
+    """A prescribed correction C [5][Np] (float64 CUDA) added to the
+    tendency of an XG_FP32 context in every stage (None removes it)."""
+    if C is None:
+        _check(library().xg_correction_set(ctx, None, _default_stream(stream)), "xg_correction_set")
+        return
+    p, w, _ = _ptr(C)
+    if w != XG_DEVICE or C.dim() != 2 or C.shape[0] != 5:
+        raise ValueError("xg_correction_set takes a [5][Np] device array")
+    _check(library().xg_correction_set(ctx, p, _default_stream(stream)), "xg_correction_set")
+
+
+def xg_closure_target(a, b, s=1.0, out=None, stream=None):
+    """out = s (a - b) for float64 CUDA arrays of one shape (a new array when
+    out is None); returns out."""
+    import torch
+    if out is None:
+        out = torch.empty_like(a)
+    for t in (a, b, out):
+        if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected contiguous float64 CUDA tensors")
+    if a.shape != b.shape or a.shape != out.shape:
+        raise ValueError("a, b and out must have one shape")
+    _check(library().xg_closure_target(a.data_ptr(), b.data_ptr(), float(s), int(a.numel()), out.data_ptr(),
+                                       _default_stream(stream)), "xg_closure_target")
+    return out
 
 
 # ------------------------------------------------------------------ remaining dynamics

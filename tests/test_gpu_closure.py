@@ -184,6 +184,56 @@ def test_closure_in_the_rhs(cuda_device):
         assert np.all(diff[1 + d_][m.wall_nodes(d_)] == 0.0)
 
 
+def test_prescribed_correction_in_the_rhs(cuda_device):
+    """xg_correction_set: xg_rhs = plain RHS + C (C rounded to FP32, the
+    wall-normal momentum still zero at walls), replacing an enabled network;
+    removing it restores the plain RHS bit for bit; FP32 contexts only."""
+    import torch
+    from paper_2504_08157_gb300 import xg
+    wl = W.box((3, 2, 2), 4, (0.0, 0.0, 0.0), (3000.0, 2000.0, 2000.0), (True, False, False), seed=97)
+    d = cuda_device
+    p, _, _, _, _, _ = _random_net(6, 1, scale=0.3)
+    ones = np.ones(21, np.float32)
+    with GpuContext(wl, precision=FP32) as g:
+        plain = g.rhs()
+        C = 0.5 * plain.std(axis=1, keepdims=True) * np.random.default_rng(3).normal(size=plain.shape)
+        xg.xg_closure_set(g.ctx, _t(p, d), _t(np.zeros(21, np.float32), d), _t(ones, d),
+                          _t(np.full(5, 1e-3, np.float32), d))
+        xg.xg_correction_set(g.ctx, _t(C, d, torch.float64))
+        withc = g.rhs()
+        xg.xg_correction_set(g.ctx, None)
+        again = g.rhs()
+    assert np.array_equal(plain, again)
+    m, _, _ = oracle_of(wl)
+    want = E.apply_walls(m, C.astype(np.float32).astype(np.float64))
+    diff = withc - plain
+    for v in range(5):
+        bar = 1e-5 * (1.0 + np.linalg.norm(plain[v]) / np.linalg.norm(want[v]))
+        assert rel_l2(diff[v], want[v]) <= bar, (v, rel_l2(diff[v], want[v]))
+    for d_ in range(3):
+        assert np.all(diff[1 + d_][m.wall_nodes(d_)] == 0.0)
+    with GpuContext(wl, precision=0) as g:
+        with pytest.raises(xg.XgError) as e:
+            xg.xg_correction_set(g.ctx, _t(C, d, torch.float64))
+        assert e.value.status == xg.XG_ERR_UNSUPPORTED
+
+
+def test_closure_target_is_the_scaled_difference(cuda_device):
+    """xg_closure_target: out = s (a - b), elementwise in FP64 (bit for bit
+    the same IEEE operations as numpy's), also in place."""
+    import torch
+    from paper_2504_08157_gb300 import xg
+    r = np.random.default_rng(5)
+    a, b = r.normal(size=(5, 1001)), r.normal(size=(5, 1001))
+    ta, tb = _t(a, cuda_device, torch.float64), _t(b, cuda_device, torch.float64)
+    out = xg.xg_closure_target(ta, tb, 0.25)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), 0.25 * (a - b))
+    xg.xg_closure_target(ta, tb, 1.0 / 0.0125, out=ta)
+    torch.cuda.synchronize()
+    assert np.array_equal(ta.cpu().numpy(), (1.0 / 0.0125) * (a - b))
+
+
 def test_closure_only_on_fp32(cuda_device):
     from paper_2504_08157_gb300 import xg
     wl = W.box((2, 2, 2), 4, (0.0, 0.0, 0.0), (2000.0, 2000.0, 2000.0), (True, True, False))
