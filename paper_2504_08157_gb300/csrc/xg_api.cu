@@ -271,7 +271,7 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
     prof_mark(c, 0, false, st);
     xg::k_df_line_x<N><<<gx, xg::kXThreads, c->xsmem, st>>>(c->Pdf, B);
     prof_mark(c, 0, true, st);
-    constexpr int K = xg::df_tile_segments(N);
+    constexpr int K = xg::df_tile_segments(N, 1);
     const dim3 blk(xg::kTileCols, K * N + 1);
     const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
     dim3 gy(xb, (c->d.nel[1] + K - 1) / K, c->n[2]);
@@ -280,7 +280,7 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
     prof_mark(c, 1, true, st);
   }
   if (parts & 2) {
-    constexpr int K = xg::df_tile_segments(N);
+    constexpr int K = xg::df_tile_segments(N, 2);
     const dim3 blk(xg::kTileCols, K * N + 1);
     const unsigned xb = (c->n[0] + xg::kTileCols - 1) / xg::kTileCols;
     dim3 gz(xb, (c->d.nel[2] + K - 1) / K, c->n[1]);

@@ -356,9 +356,23 @@ __device__ __forceinline__ void df_finish(const DfParams& P, const DfBufs& B, co
 constexpr int kTileCols = 32;
 
 __host__ __device__ constexpr int tile_segments(int N) { return N >= 16 ? 1 : 16 / N; }
-// The z tiles hold at most 9 planes: 3 CTAs of 288 threads fit an SM
-// without spills.
-__host__ __device__ constexpr int df_tile_segments(int N) { return N >= 8 ? 1 : 8 / N; }
+// Segments per tile and launch bounds of the y (DIR = 1) and z (DIR = 2)
+// tile kernels.  A sweep on the 128 x 128 x 16 order-4 box: y tiles of one
+// segment (160 threads) at 8 CTAs per SM (48 registers) took 0.692 ms per
+// launch, against 0.853 with two segments at 3 CTAs and 0.748 at 4; z tiles
+// of two segments at 4 CTAs per SM (56 registers) 1.054 ms, against 1.100 at
+// 3, 1.106 at 5 and 1.096 with one segment at 6.  Other orders keep about the
+// same threads per SM.
+__host__ __device__ constexpr int df_tile_segments(int N, int DIR) {
+  return DIR == 1 ? (N >= 4 ? 1 : 4 / N) : (N >= 8 ? 1 : 8 / N);
+}
+__host__ __device__ constexpr int df_tile_threads(int N, int DIR) {
+  return kTileCols * (df_tile_segments(N, DIR) * N + 1);
+}
+__host__ __device__ constexpr int df_tile_min_blocks(int N, int DIR) {
+  return (DIR == 1 ? 1280 : 1152) / df_tile_threads(N, DIR) > 1
+             ? (DIR == 1 ? 1280 : 1152) / df_tile_threads(N, DIR) : 1;
+}
 
 // ---------------------------------------------------------------- y and z lines, tiled
 // One CTA per (32 x-columns) x (a chunk of K element segments along DIR) x
@@ -376,8 +390,9 @@ __host__ __device__ constexpr int df_tile_segments(int N) { return N >= 8 ? 1 : 
 // (open_y, DIR = 1) the slab's first node takes row 0 once, and the end node
 // hands its one-sided row N to face_hi instead of doubling it.
 template <int N, int DIR>
-__global__ void __launch_bounds__(kTileCols * (8 + 1), 3) k_df_tline(const DfParams P, const DfBufs B) {
-  constexpr int K = df_tile_segments(N);
+__global__ void __launch_bounds__(df_tile_threads(N, DIR), df_tile_min_blocks(N, DIR))
+    k_df_tline(const DfParams P, const DfBufs B) {
+  constexpr int K = df_tile_segments(N, DIR);
   constexpr int NS = K * N + N + 1;            // flux slots: N halo planes + K N + 1
   __shared__ df Fm[3][NS][kTileCols];          // momentum fluxes (pairs)
   __shared__ double Fs[2][NS][kTileCols];      // rho u_DIR and theta
