@@ -62,6 +62,18 @@ KERNEL_NAMES = {0: ("k_line_x", "k_line_y", "k_line_z"),
 CONTRACTIONS = {"tf32x3": (lambda xg: xg.XG_CONTRACT_TF32X3, "k_f_plane_xy_tc"),
                 "f16x3": (lambda xg: xg.XG_CONTRACT_F16X3, "k_f_plane_xy_h16")}
 PLANE_KERNEL_OF = {1: "k_f_plane_xy_tc", 2: "k_f_plane_xy_h16"}
+# the FP32 form's opt-in fused pass (order 4, walls at the bottom and top, the
+# CUDA-core contraction): the whole stage is one kernel in timing slot 0
+COLUMN_NAMES = ("k_f_column", "-", "-")
+
+
+def fp32_kernel_names(wl, contract=0, fused=False):
+    """The kernels behind the FP32 form's timing slots on workload wl."""
+    if contract:
+        return (PLANE_KERNEL_OF[contract],) + KERNEL_NAMES[1][1:]
+    if fused and wl["N"] == 4 and not wl["periodic"][2]:
+        return COLUMN_NAMES
+    return KERNEL_NAMES[1]
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -479,7 +491,7 @@ _Z_VALUES = 5 + 3 + 5 + 1 + 5 * 2 / 3 + 5
 KERNEL_VALUES_PER_NODE = {"k_line_x": 14, "k_line_y": 16, "k_line_z": _Z_VALUES,
                           "k_df_line_x": 14, "k_df_tline_y": 16, "k_df_tline_z": _Z_VALUES,
                           "k_f_plane_xy": 13, "k_f_plane_xy_tc": 13, "k_f_plane_xy_h16": 13,
-                          "k_f_tline": _Z_VALUES - 1}
+                          "k_f_tline": _Z_VALUES - 1, "k_f_column": 5 + 1 + 5 * 2 / 3 + 5}
 # The method's own traffic per node and stage: q and S in,
 # q out, plus q^n in stages 2 and 3.
 STAGE_BYTES_PER_NODE = (88 + 128 + 128) / 3.0
@@ -531,9 +543,13 @@ def run_xg(args, world, rank, local):
 
     ctx = make_ctx(xg, torch, wl, dev, prec)
     knames = KERNEL_NAMES[prec]
-    if prec == xg.XG_FP32 and args.contraction != "fma":
-        xg.xg_set_contraction(ctx, CONTRACTIONS[args.contraction][0](xg))
-        knames = (CONTRACTIONS[args.contraction][1],) + knames[1:]
+    if prec == xg.XG_FP32:
+        contract = CONTRACTIONS[args.contraction][0](xg) if args.contraction != "fma" else 0
+        if contract:
+            xg.xg_set_contraction(ctx, contract)
+        if args.fused:
+            xg.xg_set_fused(ctx, 1)
+        knames = fp32_kernel_names(wl, contract, args.fused)
     ms_max, kms, klaunch, clk = timed_steps(xg, torch, ctx, dt, K, Wm, stream, world, local, True)
     value = gdof(ms_max, K)
 
@@ -601,22 +617,25 @@ def run_xg(args, world, rank, local):
 
     # the other precisions on the same workload and GPU: plain FP64 (the
     # comparison the metric asks for) and the FP32 precision form
-    def side_run(p, dtype, contract=0):
+    def side_run(p, dtype, contract=0, fused=False):
         Kp = max(1, min(K, 10))
         c2 = make_ctx(xg, torch, wl, dev, p)
         if contract:
             xg.xg_set_contraction(c2, contract)
+        if p == xg.XG_FP32 and fused:
+            xg.xg_set_fused(c2, 1)
+        names = fp32_kernel_names(wl, contract, fused) if p == xg.XG_FP32 else KERNEL_NAMES[p]
         msp, kmsp, klp, _ = timed_steps(xg, torch, c2, dt, Kp, 3, stream, world, local, False)
         xg.xg_destroy(c2)
         return {"value": round(gdof(msp, Kp), 4), "unit": "GDOF/s", "dtype": dtype,
                 "ms_per_step": round(msp / Kp, 4), "steps": Kp,
-                "kernel_ms_per_launch": {((PLANE_KERNEL_OF[contract],) + KERNEL_NAMES[p][1:] if contract
-                                          else KERNEL_NAMES[p])[i]: round(kmsp[i] / max(klp[i], 1), 4)
+                "kernel_ms_per_launch": {names[i]: round(kmsp[i] / max(klp[i], 1), 4)
                                          for i in range(3) if klp[i]}}
     plain = side_run(xg.XG_FP64, "f64") if prec != xg.XG_FP64 and not args.no_plain else None
     fp32 = side_run(xg.XG_FP32, "f32") if prec != xg.XG_FP32 and not args.no_plain else None
     if fp32 is not None and wl["N"] == 4:
         # the same form with the x and y contractions on the tensor cores
+        fp32["fused_column_pass"] = side_run(xg.XG_FP32, "f32", 0, True)
         fp32["tf32x3_contraction"] = side_run(xg.XG_FP32, "f32", xg.XG_CONTRACT_TF32X3)
         fp32["f16x3_contraction"] = side_run(xg.XG_FP32, "f32", xg.XG_CONTRACT_F16X3)
     batched = None
@@ -1218,6 +1237,9 @@ def main():
                     help="with --precision fp32: x and y contractions on the CUDA cores (fma) or "
                          "on the tensor cores (tf32x3: TF32 head/tail split; f16x3: half-precision "
                          "head/tail split with a scale per segment; order 4)")
+    ap.add_argument("--fused", action="store_true",
+                    help="with --precision fp32: the fused column pass (one kernel per stage, TMA "
+                         "staging) instead of the plane + z-line kernels")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain-FP64 and FP32-form comparison runs")
     ap.add_argument("--instances", type=int, default=96,

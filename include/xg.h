@@ -174,6 +174,21 @@ xg_status xg_diagnostics(xg_ctx* ctx, double out[5], void* stream);
 enum { XG_CONTRACT_FMA = 0, XG_CONTRACT_TF32X3 = 1, XG_CONTRACT_F16X3 = 2 };
 xg_status xg_set_contraction(xg_ctx* ctx, int mode);
 
+/* Pass structure of an XG_FP32 context.  fused = 0 (the default): a stage
+ * is the x-y plane kernel followed by the z-line kernel, with the partial
+ * tendency in HBM between them.  fused = 1: on order-4 meshes with walls at
+ * the bottom and top and the XG_CONTRACT_FMA contraction, each stage is one
+ * kernel that marches columns of 4 x 4 elements up through the levels and
+ * does the x, y and z contractions, the sources, walls and the stage
+ * combination on chip (its state loads staged by TMA where n_x is a
+ * multiple of 4); it moves only the stage's own inputs and output, but its
+ * level-by-level march makes it slower than the two kernels (measured on
+ * the 128 x 128 x 16 box: 1.00 against 0.67 ms per stage); other meshes keep
+ * the two kernels.  Both compute the same arithmetic up to the order of two
+ * FP32 additions at face nodes.  Errors: XG_ERR_ARG (NULL, fused not 0 or
+ * 1). */
+xg_status xg_set_fused(xg_ctx* ctx, int fused);
+
 /* Kernel timing (Sec. 5.4 measures its kernels against a roofline; this is
  * the hook for doing the same here).  enable = 1 brackets every kernel that
  * xg_rhs and xg_step launch with CUDA events on the launching stream; the

@@ -22,7 +22,7 @@ SOURCES = [os.path.join(HERE, "csrc", f) for f in ("xg_api.cu", "xg_noalloc.cu",
 DEPENDS = SOURCES + [os.path.join(HERE, "csrc", f) for f in
                      ("xg_kernels.cuh", "xg_setup.h", "xg_df.cuh", "xg_kernels_df.cuh",
                       "xg_kernels_f32.cuh", "xg_plane_f32.cuh", "xg_tc.cuh", "xg_plane_tc.cuh", "xg_plane_h16.cuh",
-                      "xg_ctx.h")] + [
+                      "xg_column_f32.cuh", "xg_tma.cuh", "xg_ctx.h")] + [
                      os.path.join(ROOT, "include", f) for f in ("xg.h", "xg_batch.h", "xg_closure.h",
                                                                "xg_dynamics.h", "xg_imex.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

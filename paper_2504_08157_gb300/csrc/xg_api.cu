@@ -11,10 +11,13 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/xg.h"
 #include "xg_kernels.cuh"
+#include "xg_column_f32.cuh"
 #include "xg_kernels_df.cuh"
 #include "xg_plane_h16.cuh"
 #include "xg_plane_tc.cuh"
@@ -28,6 +31,26 @@ using xg::StageBufs;
 using xg::df;
 
 namespace xg {
+bool encode_tma_4d_f32(CUtensorMap* map, const float* base, const uint64_t dims[4], const uint32_t box[4]) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
+  const cuuint64_t gdim[4] = {dims[0], dims[1], dims[2], dims[3]};
+  const cuuint64_t gstride[3] = {dims[0] * 4, dims[0] * dims[1] * 4, dims[0] * dims[1] * dims[2] * 4};
+  const cuuint32_t bdim[4] = {box[0], box[1], box[2], box[3]};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), gdim, gstride, bdim, estride,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(df v) { return df_to_double(v); }
@@ -254,6 +277,8 @@ cudaError_t configure_n(xg_ctx* c) {
   if (e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_plane_xy<N>, xg::PlaneLayoutF<N>::bytes);
   if (N == xg::PlaneTcLayout::N && e == cudaSuccess)
     e = xg::raise_dynamic_smem(xg::k_f_plane_xy_tc, xg::PlaneTcLayout::bytes);
+  if (N == xg::ColLayout::N && e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_column<true>, xg::ColLayout::bytes);
+  if (N == xg::ColLayout::N && e == cudaSuccess) e = xg::raise_dynamic_smem(xg::k_f_column<false>, xg::ColLayout::bytes);
   if (N == xg::PlaneH16Layout::N && e == cudaSuccess) {
     e = xg::raise_dynamic_smem(xg::k_f_plane_xy_h16, xg::PlaneH16Layout::bytes);
     // two CTAs of 111 KB per SM need the whole shared-memory carveout
@@ -290,8 +315,45 @@ void launch_df_stage_n(xg_ctx* c, const DfBufs& B, cudaStream_t st, int parts) {
   }
 }
 
+// The fused column pass applies: FP32 form, order 4, the CUDA-core
+// contraction, walls at the bottom and top.
+bool column_on(const xg_ctx* c) {
+  return c->f32 && c->fused && c->d.order == xg::ColLayout::N && c->contract == XG_CONTRACT_FMA &&
+         !c->Pf.per[2];
+}
+
+// The TMA map of stage input q (the 4-D view [5][n_z][n_y][n_x] with the
+// column kernel's box), or null where the pitch does not allow one.
+const CUtensorMap* column_map(xg_ctx* c, const float* q) {
+  if (c->n[0] % 4 != 0) return nullptr;
+  for (int k = 0; k < 4; ++k)
+    if (c->col_key[k] == q) return &c->col_map[k];
+  const int k = c->col_next;
+  const uint64_t dims[4] = {(uint64_t)c->n[0], (uint64_t)c->n[1], (uint64_t)c->n[2], 5};
+  const uint32_t box[4] = {xg::ColLayout::QX, xg::ColLayout::LX, 1, 5};
+  if (!xg::encode_tma_4d_f32(&c->col_map[k], q, dims, box)) return nullptr;
+  c->col_key[k] = q;
+  c->col_next = (k + 1) % 4;
+  return &c->col_map[k];
+}
+
 template <int N>
 void launch_f32_stage_n(xg_ctx* c, const xg::FBufs& B, cudaStream_t st) {
+  if (N == xg::ColLayout::N && column_on(c)) {   // x, y, z and the stage in one pass
+    constexpr int E = xg::ColLayout::E;
+    const dim3 g((c->d.nel[0] + E - 1) / E, (c->d.nel[1] + E - 1) / E);
+    const CUtensorMap* m = column_map(c, B.q);
+    prof_mark(c, 0, false, st);
+    if (m) {
+      xg::k_f_column<true><<<g, xg::kColThreads, xg::ColLayout::bytes, st>>>(c->Pf, B, *m);
+    } else {
+      CUtensorMap unused;
+      std::memset(&unused, 0, sizeof(unused));
+      xg::k_f_column<false><<<g, xg::kColThreads, xg::ColLayout::bytes, st>>>(c->Pf, B, unused);
+    }
+    prof_mark(c, 0, true, st);
+    return;
+  }
   // x and y passes fused over element tiles of each level, then the z pass
   constexpr int E = xg::plane_elems_f32(N);
   dim3 gp((c->d.nel[0] + E - 1) / E, (c->d.nel[1] + E - 1) / E, c->n[2]);
@@ -678,7 +740,7 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = where == XG_DEVICE ? dqdt : c->Bq;
-  const bool tc_waits = c->closure || c->contract != XG_CONTRACT_FMA;   // kernels with bounded waits
+  const bool tc_waits = c->closure || c->contract != XG_CONTRACT_FMA || column_on(c);   // bounded waits
   if (tc_waits) XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
   if (!c->f32) {
     XG_CUDA(c, run_stage(c, c->A, nullptr, dst, 0.0, 0.0, 1.0, 1, st));
@@ -743,6 +805,12 @@ xg_status xg_get_state(xg_ctx* c, double* q, int where, void* stream) {
     XG_CUDA(c, cudaMemcpyAsync(q, c->Bq, sizeof(double) * (size_t)n5, cudaMemcpyDeviceToHost, st));
   }
   if (where == XG_HOST) XG_CUDA(c, cudaStreamSynchronize(st));
+  return XG_OK;
+}
+
+xg_status xg_set_fused(xg_ctx* c, int fused) {
+  if (!c || (fused != 0 && fused != 1)) return XG_ERR_ARG;
+  c->fused = fused != 0;
   return XG_OK;
 }
 

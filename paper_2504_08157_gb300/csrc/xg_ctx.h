@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/xg.h"
@@ -24,6 +25,13 @@ struct xg_ctx {
   bool dfm = false;      // precision XG_DF64: FP64 arrays, mixed FP64 / double-float kernels
   bool f32 = false;      // precision XG_FP32: device arrays hold floats
   int contract = 0;      // XG_FP32: arithmetic of the x and y contractions (XG_CONTRACT_*)
+  // XG_FP32: the fused column pass where the mesh allows it (xg_set_fused,
+  // opt-in), and the TMA maps of its stage inputs (one per distinct q
+  // buffer, encoded on first use)
+  bool fused = false;
+  CUtensorMap col_map[4];
+  const void* col_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  int col_next = 0;
   double* A = nullptr;   // q^n (the state)
   double* Bq = nullptr;  // stage buffer
   double* Cq = nullptr;  // stage buffer

@@ -168,6 +168,92 @@ __device__ __forceinline__ void f_plane_pointwise(const FParams& P, const FBufs&
   }
 }
 
+// The x part + y part of the owned node (i, j) of tile T from its flux
+// tiles, fx(c, j, i + N) and fy(c, j + N, i) (slot 4: theta): an element-
+// interior node takes one row of its segment, a face node row 0 of its
+// segment plus row N of the segment before, a wall node its one-sided row
+// twice; rho' and Theta' in difference form (f_drows).
+template <int N, typename FXs, typename FYs>
+__device__ __forceinline__ void f_plane_node_xy(const FParams& P, const PlaneTile& T, FXs fx, FYs fy, int i, int j,
+                                                float (&t)[5]) {
+  const int ekx = T.ekx, eky = T.eky;
+  const bool hxl = T.hxl, hyl = T.hyl;
+  const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
+  const int sy = min(j / N, eky - 1), ay = j - sy * N;
+  {   // rho' and Theta' in difference form (slot 0: rho u_d, slot 4: theta)
+    float m[N + 1], th[N + 1], v0 = 0.0f, v4 = 0.0f, w0 = 0.0f, w4 = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= N; ++l) {
+      m[l] = fx(0, j, N + sx * N + l);
+      th[l] = fx(4, j, N + sx * N + l);
+    }
+    f_drows<N, 0>(P, ax, m, th, v0, v4);
+    if (ax == 0 || ax == N) {
+      if (ax == 0 && (sx > 0 || hxl)) {
+#pragma unroll
+        for (int l = 0; l <= N; ++l) {
+          m[l] = fx(0, j, sx * N + l);
+          th[l] = fx(4, j, sx * N + l);
+        }
+        f_drows<N, 0>(P, N, m, th, v0, v4);
+      } else {
+        v0 = v0 + v0;
+        v4 = v4 + v4;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l <= N; ++l) {
+      m[l] = fy(0, N + sy * N + l, i);
+      th[l] = fy(4, N + sy * N + l, i);
+    }
+    f_drows<N, 1>(P, ay, m, th, w0, w4);
+    if (ay == 0 || ay == N) {
+      if (ay == 0 && (sy > 0 || hyl)) {
+#pragma unroll
+        for (int l = 0; l <= N; ++l) {
+          m[l] = fy(0, sy * N + l, i);
+          th[l] = fy(4, sy * N + l, i);
+        }
+        f_drows<N, 1>(P, N, m, th, w0, w4);
+      } else {
+        w0 = w0 + w0;
+        w4 = w4 + w4;
+      }
+    }
+    t[0] = v0 + w0;
+    t[4] = v4 + w4;
+  }
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
+    float f[N + 1], v = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= N; ++l) f[l] = fx(c, j, N + sx * N + l);
+    v = f_row_from<N, 0>(P, ax, f, v);
+    if (ax == 0 || ax == N) {
+      if (ax == 0 && (sx > 0 || hxl)) {
+#pragma unroll
+        for (int l = 0; l <= N; ++l) f[l] = fx(c, j, sx * N + l);
+        v = f_row_from<N, 0>(P, N, f, v);
+      } else {
+        v = v + v;                                  // wall: the one-sided row counts twice
+      }
+    }
+#pragma unroll
+    for (int l = 0; l <= N; ++l) f[l] = fy(c, N + sy * N + l, i);
+    float w = f_row_from<N, 1>(P, ay, f, 0.0f);
+    if (ay == 0 || ay == N) {
+      if (ay == 0 && (sy > 0 || hyl)) {
+#pragma unroll
+        for (int l = 0; l <= N; ++l) f[l] = fy(c, sy * N + l, i);
+        w = f_row_from<N, 1>(P, N, f, w);
+      } else {
+        w = w + w;
+      }
+    }
+    t[c] = v + w;
+  }
+}
+
 // One tile (bx, by) of level z, run by threads tid = 0 .. nthr-1 of the
 // block; sm holds PlaneLayoutF<N, E>::bytes.  CG: L2-only loads of q (see
 // ldf).  The block synchronises once, between the pointwise and the
@@ -197,8 +283,7 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
   __syncthreads();
 
   const int nx = P.n[0], ny = P.n[1];
-  const int ekx = T.ekx, eky = T.eky, x0 = T.x0, y0 = T.y0, ox = T.ox, oy = T.oy;
-  const bool hxl = T.hxl, hyl = T.hyl;
+  const int x0 = T.x0, y0 = T.y0, ox = T.ox, oy = T.oy;
   const long long np = P.np;
   const long long zoff = (long long)nx * ny * z;
   const float rox = 1.0f / (float)ox;
@@ -208,80 +293,10 @@ __device__ __forceinline__ void f_plane_tile(const FParams& P, const FBufs& B, i
   for (int idx = tid; idx < ox * oy; idx += nthr) {
     const int j = small_div(idx, ox, rox), i = idx - j * ox;
     const long long I = zoff + (x0 + i) + (long long)nx * (y0 + j);
-    const int sx = min(i / N, ekx - 1), ax = i - sx * N;   // the wall node is row N of the last
-    const int sy = min(j / N, eky - 1), ay = j - sy * N;
-    {   // rho' and Theta' in difference form (slot 0: rho u_d, slot 4: theta)
-      float m[N + 1], th[N + 1], v0 = 0.0f, v4 = 0.0f, w0 = 0.0f, w4 = 0.0f;
+    float t[5];
+    f_plane_node_xy<N>(P, T, fx, fy, i, j, t);
 #pragma unroll
-      for (int l = 0; l <= N; ++l) {
-        m[l] = fx(0, j, N + sx * N + l);
-        th[l] = fx(4, j, N + sx * N + l);
-      }
-      f_drows<N, 0>(P, ax, m, th, v0, v4);
-      if (ax == 0 || ax == N) {
-        if (ax == 0 && (sx > 0 || hxl)) {
-#pragma unroll
-          for (int l = 0; l <= N; ++l) {
-            m[l] = fx(0, j, sx * N + l);
-            th[l] = fx(4, j, sx * N + l);
-          }
-          f_drows<N, 0>(P, N, m, th, v0, v4);
-        } else {
-          v0 = v0 + v0;
-          v4 = v4 + v4;
-        }
-      }
-#pragma unroll
-      for (int l = 0; l <= N; ++l) {
-        m[l] = fy(0, N + sy * N + l, i);
-        th[l] = fy(4, N + sy * N + l, i);
-      }
-      f_drows<N, 1>(P, ay, m, th, w0, w4);
-      if (ay == 0 || ay == N) {
-        if (ay == 0 && (sy > 0 || hyl)) {
-#pragma unroll
-          for (int l = 0; l <= N; ++l) {
-            m[l] = fy(0, sy * N + l, i);
-            th[l] = fy(4, sy * N + l, i);
-          }
-          f_drows<N, 1>(P, N, m, th, w0, w4);
-        } else {
-          w0 = w0 + w0;
-          w4 = w4 + w4;
-        }
-      }
-      To[I] = v0 + w0;
-      To[4 * np + I] = v4 + w4;
-    }
-#pragma unroll
-    for (int c = 1; c < 4; ++c) {
-      float f[N + 1], v = 0.0f;
-#pragma unroll
-      for (int l = 0; l <= N; ++l) f[l] = fx(c, j, N + sx * N + l);
-      v = f_row_from<N, 0>(P, ax, f, v);
-      if (ax == 0 || ax == N) {
-        if (ax == 0 && (sx > 0 || hxl)) {
-#pragma unroll
-          for (int l = 0; l <= N; ++l) f[l] = fx(c, j, sx * N + l);
-          v = f_row_from<N, 0>(P, N, f, v);
-        } else {
-          v = v + v;                                  // wall: the one-sided row counts twice
-        }
-      }
-#pragma unroll
-      for (int l = 0; l <= N; ++l) f[l] = fy(c, N + sy * N + l, i);
-      float w = f_row_from<N, 1>(P, ay, f, 0.0f);
-      if (ay == 0 || ay == N) {
-        if (ay == 0 && (sy > 0 || hyl)) {
-#pragma unroll
-          for (int l = 0; l <= N; ++l) f[l] = fy(c, sy * N + l, i);
-          w = f_row_from<N, 1>(P, N, f, w);
-        } else {
-          w = w + w;
-        }
-      }
-      To[c * np + I] = v + w;
-    }
+    for (int c = 0; c < 5; ++c) To[c * np + I] = t[c];
   }
 }
 

@@ -29,7 +29,7 @@ XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5,
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_set_contraction", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_pressure_perturbation", "xg_partition_set",
+           "xg_step", "xg_get_state", "xg_set_contraction", "xg_set_fused", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_pressure_perturbation", "xg_partition_set",
            "xg_partition_stage", "xg_diagnostics", "xg_destroy", "library",
            "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
            "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
@@ -121,6 +121,8 @@ def library():
     lib.xg_get_state.argtypes = [P, P, I, P]
     lib.xg_set_contraction.restype = I
     lib.xg_set_contraction.argtypes = [P, I]
+    lib.xg_set_fused.restype = I
+    lib.xg_set_fused.argtypes = [P, I]
     lib.xg_profile.restype = I
     lib.xg_profile.argtypes = [P, I]
     lib.xg_kernel_times.restype = I
@@ -317,6 +319,12 @@ def xg_get_state(ctx, q, where=None, stream=None):
 
 def xg_set_contraction(ctx, mode):
     _check(library().xg_set_contraction(ctx, int(mode)), "xg_set_contraction")
+
+
+def xg_set_fused(ctx, fused):
+    """XG_FP32: one fused column pass per stage where the mesh allows it (1),
+    or the plane + z-line kernels (0, the default)."""
+    _check(library().xg_set_fused(ctx, int(fused)), "xg_set_fused")
 
 
 def xg_profile(ctx, enable):

@@ -97,6 +97,9 @@ def test_null_arguments(lib):
     assert lib.xg_get_state(None, None, 0, None) == xg.XG_ERR_ARG
     n = ctypes.c_longlong()
     assert lib.xg_mesh_np(None, ctypes.byref(n)) == xg.XG_ERR_ARG
+    assert lib.xg_set_fused(None, 1) == xg.XG_ERR_ARG
+    assert lib.xg_set_contraction(None, 0) == xg.XG_ERR_ARG
+    assert lib.xg_correction_set(None, None, None) == xg.XG_ERR_ARG
     lib.xg_destroy(None)  # no-op
 
 

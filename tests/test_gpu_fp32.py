@@ -179,6 +179,64 @@ def test_mass_conserved_on_gpu(cuda_device, prec, tol):
     assert abs(after - before) <= tol * total, (before, after, total)
 
 
+# ------------------------------------------------------------------ the fused column pass
+
+@pytest.mark.parametrize("nel,periodic", [
+    ((1, 1, 1), (False, False, False)),
+    ((3, 2, 5), (False, False, False)),     # walled x (n_x odd): ordinary staging
+    ((9, 10, 2), (True, False, False)),     # n_x a multiple of 4: TMA staging; ragged tiles
+    ((8, 8, 3), (True, True, False)),       # TMA, periodic wrap across both ends
+    ((5, 7, 1), (True, True, False)),       # one element in z: both walls in one segment
+])
+def test_fp32_fused_column_pass(cuda_device, nel, periodic):
+    """The fused column pass (one kernel per stage: x, y and z contractions,
+    sources, walls and the stage combination on chip) against the oracle at
+    the form's bar, and against the plane + z-line kernels, which compute the
+    same arithmetic up to the order of two FP32 additions at face nodes: one
+    right-hand side within 1e-6, ten steps' increments within 1e-5."""
+    L = tuple(1000.0 * n for n in nel)
+    wl = W.box(nel, 4, (0.0, 0.0, 0.0), L, periodic, seed=11 * sum(nel) + 3)
+    with GpuContext(wl, precision=FP32) as g:
+        g.xg.xg_set_fused(g.ctx, 1)
+        fused = g.rhs()
+        g.step(10)
+        q_fused = g.state()
+    with GpuContext(wl, precision=FP32) as g:
+        split = g.rhs()
+        g.step(10)
+        q_split = g.state()
+    err = rel_l2_per_var(fused, oracle_rhs(wl))
+    assert np.all(err <= RHS_TOL32), err
+    assert np.all(rel_l2_per_var(fused, split) <= 1e-6)
+    assert np.all(rel_l2_per_var(q_fused - wl["q"], q_split - wl["q"]) <= 1e-5)
+
+
+@pytest.mark.slow
+def test_fp32_fused_column_pass_full_size_sampled(cuda_device):
+    """The fused column pass on the full cyclone box (TMA staging, periodic
+    wrap in x and y) at the random state, sampled nodes, within the form's
+    bar of the oracle."""
+    import test_gpu_parity as P
+    got, ref, _ = P._full_size_sampled(W.tc(state="random"), FP32, 0, fused=True)
+    err = rel_l2_per_var(got, ref)
+    assert np.all(err <= RHS_TOL32), err
+
+
+def test_fp32_fused_pass_falls_back(cuda_device):
+    """Where the fused pass, although asked for, does not apply (periodic z,
+    another order, a tensor-core contraction) the split kernels run, within
+    the bar."""
+    for nel, N, per, mode in (((3, 3, 2), 4, (True, True, True), 0), ((3, 3, 2), 3, (True, False, False), 0),
+                              ((9, 9, 2), 4, (True, True, False), 1)):
+        wl = W.box(nel, N, (0.0, 0.0, 0.0), tuple(1000.0 * n for n in nel), per, seed=5)
+        with GpuContext(wl, precision=FP32) as g:
+            g.xg.xg_set_fused(g.ctx, 1)
+            if mode:
+                g.xg.xg_set_contraction(g.ctx, mode)
+            got = g.rhs()
+        assert np.all(rel_l2_per_var(got, oracle_rhs(wl)) <= RHS_TOL32)
+
+
 # ------------------------------------------------------------------ tensor-core contractions
 
 TF32X3 = 1   # XG_CONTRACT_TF32X3

@@ -152,10 +152,12 @@ def _sample_nodes(n, rng, count):
     return np.unique(np.array(ids, dtype=np.int64))
 
 
-def _full_size_sampled(wl, prec, contraction=0):
+def _full_size_sampled(wl, prec, contraction=0, fused=False):
     with GpuContext(wl, precision=prec) as g:
         if contraction:
             g.xg.xg_set_contraction(g.ctx, contraction)
+        if fused:
+            g.xg.xg_set_fused(g.ctx, 1)
         got = g.rhs()
         n = W.dof_counts(wl["nel"], wl["N"], wl["periodic"])[0] // 5
         assert g.np == n
