@@ -174,6 +174,24 @@ xg_status xg_diagnostics(xg_ctx* ctx, double out[5], void* stream);
 enum { XG_CONTRACT_FMA = 0, XG_CONTRACT_TF32X3 = 1, XG_CONTRACT_F16X3 = 2 };
 xg_status xg_set_contraction(xg_ctx* ctx, int mode);
 
+/* Streamed host-to-host steps (Sec. 5's throughput setting: many
+ * independent states through one context).  For each of count inputs:
+ * state <- q_in[k] (host, [5][Np] FP64), nsteps SSP-RK3 steps of dt,
+ * q_out[k] <- the state (host).  The copies run on two streams of the
+ * context: the upload of input k + 1 and the download of output k - 1
+ * overlap the steps of input k (the host link carries both directions at
+ * once), so for count > 1 they hide behind the arithmetic.  q_in and q_out
+ * are arrays of count host pointers (pinned memory gives the full copy
+ * rate); a q_out pointer may repeat (its last write is the latest output).
+ * The reference state of xg_set_state is kept; afterwards the context holds
+ * the last output's state.  Outputs equal set_state + step + get_state of
+ * each input bit for bit.  Allocates 4 FP64 state arrays of device memory
+ * on first use; waits for the GPU.  Errors: XG_ERR_ARG (NULL, count < 0, no
+ * reference state yet), XG_ERR_UNSUPPORTED (a partitioned context),
+ * XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, XG_ERR_CUDA. */
+xg_status xg_step_stream(xg_ctx* ctx, int count, const double* const* q_in, double* const* q_out, double dt,
+                         int nsteps, void* stream);
+
 /* Pass structure of an XG_FP32 context.  fused = 0 (the default): a stage
  * is the x-y plane kernel followed by the z-line kernel, with the partial
  * tendency in HBM between them.  fused = 1: on order-4 meshes with walls at

@@ -765,6 +765,20 @@ xg_status xg_rhs(xg_ctx* c, double* dqdt, int where, void* stream) {
   return XG_OK;
 }
 
+// nsteps SSP-RK3 steps of the context's state on stream st (no wait)
+cudaError_t rk3_steps(xg_ctx* c, double dt, int nsteps, cudaStream_t st) {
+  for (int it = 0; it < nsteps; ++it) {
+    cudaError_t e = run_stage(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0, st);
+    if (e == cudaSuccess) e = run_stage(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0, st);
+    if (e == cudaSuccess) e = run_stage(c, c->Cq, c->A, c->Dq, dt, 1.0 / 3.0, 2.0 / 3.0, 0, st);
+    if (e != cudaSuccess) return e;
+    double* t = c->A;  // every kernel's arrays stay distinct (no in-place stage)
+    c->A = c->Dq;
+    c->Dq = t;
+  }
+  return cudaSuccess;
+}
+
 xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   if (!c) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
@@ -773,18 +787,96 @@ xg_status xg_step(xg_ctx* c, double dt, int nsteps, void* stream) {
   if (!c->has_state) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
-  for (int it = 0; it < nsteps; ++it) {
-    XG_CUDA(c, run_stage(c, c->A, nullptr, c->Bq, dt, 0.0, 1.0, 0, st));
-    XG_CUDA(c, run_stage(c, c->Bq, c->A, c->Cq, dt, 0.75, 0.25, 0, st));
-    XG_CUDA(c, run_stage(c, c->Cq, c->A, c->Dq, dt, 1.0 / 3.0, 2.0 / 3.0, 0, st));
-    double* t = c->A;  // every kernel's arrays stay distinct (no in-place stage)
-    c->A = c->Dq;
-    c->Dq = t;
-  }
+  XG_CUDA(c, rk3_steps(c, dt, nsteps, st));
   XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   XG_CUDA(c, cudaStreamSynchronize(st));
   prof_fold(c);
   if (*c->hflag & 2) return XG_ERR_TIMEOUT;   // the closure kernel's bounded wait ran out
+  return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
+}
+
+// The staging arrays, copy streams and events of xg_step_stream.
+cudaError_t stream_setup(xg_ctx* c) {
+  if (c->ss_ready) return cudaSuccess;
+  const size_t bytes = sizeof(double) * 5 * (size_t)c->np;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    if (!c->ss_in[b]) e = cudaMalloc((void**)&c->ss_in[b], bytes);
+    if (e == cudaSuccess && !c->ss_out[b]) e = cudaMalloc((void**)&c->ss_out[b], bytes);
+  }
+  int made = 0;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ss_h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ss_d2h, cudaStreamNonBlocking);
+  for (; made < 8 && e == cudaSuccess; ++made) e = cudaEventCreateWithFlags(&c->ss_ev[made], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(c->ss_in[b]);
+      cudaFree(c->ss_out[b]);
+      c->ss_in[b] = c->ss_out[b] = nullptr;
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(c->ss_ev[k]);
+    if (c->ss_h2d) cudaStreamDestroy(c->ss_h2d);
+    if (c->ss_d2h) cudaStreamDestroy(c->ss_d2h);
+    c->ss_h2d = c->ss_d2h = nullptr;
+    return e;
+  }
+  c->ss_ready = true;
+  return cudaSuccess;
+}
+
+xg_status xg_step_stream(xg_ctx* c, int count, const double* const* q_in, double* const* q_out, double dt,
+                         int nsteps, void* stream) {
+  if (!c || count < 0 || (count > 0 && (!q_in || !q_out))) return XG_ERR_ARG;
+  if (c->failed) return XG_ERR_CUDA;
+  if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // xg_partition_stage
+  if (!std::isfinite(dt) || nsteps < 0 || !c->has_base) return XG_ERR_ARG;
+  for (int k = 0; k < count; ++k)
+    if (!q_in[k] || !q_out[k]) return XG_ERR_ARG;
+  if (count == 0) return XG_OK;
+  {
+    const cudaError_t e = stream_setup(c);
+    if (e == cudaErrorMemoryAllocation) return XG_ERR_OOM;
+    if (e != cudaSuccess) return fail_cuda(c, e, "xg_step_stream setup");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n5 = 5 * c->np;
+  const size_t bytes = sizeof(double) * (size_t)n5;
+  cudaEvent_t* in_ready = c->ss_ev;
+  cudaEvent_t* in_used = c->ss_ev + 2;
+  cudaEvent_t* out_ready = c->ss_ev + 4;
+  cudaEvent_t* drained = c->ss_ev + 6;
+  XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+  // the first input; later ones are uploaded while the one before runs
+  XG_CUDA(c, cudaMemcpyAsync(c->ss_in[0], q_in[0], bytes, cudaMemcpyHostToDevice, c->ss_h2d));
+  XG_CUDA(c, cudaEventRecord(in_ready[0], c->ss_h2d));
+  for (int k = 0; k < count; ++k) {
+    const int b = k & 1, nb = b ^ 1;
+    if (k + 1 < count) {   // upload input k + 1 once input k - 1's staging array is read
+      XG_CUDA(c, cudaStreamWaitEvent(c->ss_h2d, in_used[nb], 0));
+      XG_CUDA(c, cudaMemcpyAsync(c->ss_in[nb], q_in[k + 1], bytes, cudaMemcpyHostToDevice, c->ss_h2d));
+      XG_CUDA(c, cudaEventRecord(in_ready[nb], c->ss_h2d));
+    }
+    XG_CUDA(c, cudaStreamWaitEvent(st, in_ready[b], 0));
+    if (!c->f32) XG_CUDA(c, cudaMemcpyAsync(c->A, c->ss_in[b], bytes, cudaMemcpyDeviceToDevice, st));
+    else XG_CUDA(c, import_values(c, c->ss_in[b], c->A, n5, st));
+    XG_CUDA(c, cudaEventRecord(in_used[b], st));
+    c->has_state = true;
+    XG_CUDA(c, rk3_steps(c, dt, nsteps, st));
+    // output k into staging once output k - 2 has left it, then download it
+    XG_CUDA(c, cudaStreamWaitEvent(st, drained[b], 0));
+    if (!c->f32) XG_CUDA(c, cudaMemcpyAsync(c->ss_out[b], c->A, bytes, cudaMemcpyDeviceToDevice, st));
+    else XG_CUDA(c, export_values(c, c->A, c->ss_out[b], n5, st));
+    XG_CUDA(c, cudaEventRecord(out_ready[b], st));
+    XG_CUDA(c, cudaStreamWaitEvent(c->ss_d2h, out_ready[b], 0));
+    XG_CUDA(c, cudaMemcpyAsync(q_out[k], c->ss_out[b], bytes, cudaMemcpyDeviceToHost, c->ss_d2h));
+    XG_CUDA(c, cudaEventRecord(drained[b], c->ss_d2h));
+  }
+  XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  XG_CUDA(c, cudaStreamSynchronize(c->ss_d2h));
+  XG_CUDA(c, cudaStreamSynchronize(c->ss_h2d));
+  XG_CUDA(c, cudaStreamSynchronize(st));
+  prof_fold(c);
+  if (*c->hflag & 2) return XG_ERR_TIMEOUT;
   return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
 }
 
@@ -988,6 +1080,15 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->base64);
   cudaFree(c->flag);
   if (c->hflag) cudaFreeHost(c->hflag);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->ss_in[b]);
+    cudaFree(c->ss_out[b]);
+  }
+  if (c->ss_ready) {
+    for (cudaEvent_t e : c->ss_ev) cudaEventDestroy(e);
+    cudaStreamDestroy(c->ss_h2d);
+    cudaStreamDestroy(c->ss_d2h);
+  }
   closure_free(c);
   dynamics_free(c);
   imex_free(c);

@@ -29,6 +29,14 @@ struct xg_ctx {
   // opt-in), and the TMA maps of its stage inputs (one per distinct q
   // buffer, encoded on first use)
   bool fused = false;
+  // xg_step_stream: FP64 staging of the streamed inputs and outputs (two of
+  // each), the two copy streams and their events (allocated on first use):
+  // ss_ev = in_ready[2], in_used[2], out_ready[2], out_drained[2]
+  double* ss_in[2] = {nullptr, nullptr};
+  double* ss_out[2] = {nullptr, nullptr};
+  cudaStream_t ss_h2d = nullptr, ss_d2h = nullptr;
+  cudaEvent_t ss_ev[8] = {};
+  bool ss_ready = false;
   CUtensorMap col_map[4];
   const void* col_key[4] = {nullptr, nullptr, nullptr, nullptr};
   int col_next = 0;

@@ -29,7 +29,7 @@ XG_CLOSURE_IN, XG_CLOSURE_HIDDEN, XG_CLOSURE_OUT, XG_CLOSURE_PARAMS = 21, 64, 5,
 
 __all__ = ["XgError", "xg_mesh_desc", "mesh_desc", "xg_status_str", "xg_mesh_create",
            "xg_mesh_np", "xg_mesh_dims", "xg_set_state", "xg_set_forcing", "xg_rhs",
-           "xg_step", "xg_get_state", "xg_set_contraction", "xg_set_fused", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_pressure_perturbation", "xg_partition_set",
+           "xg_step", "xg_step_stream", "xg_get_state", "xg_set_contraction", "xg_set_fused", "xg_profile", "xg_kernel_times", "xg_rhs_noalloc", "xg_reciprocal", "xg_pressure_perturbation", "xg_partition_set",
            "xg_partition_stage", "xg_diagnostics", "xg_destroy", "library",
            "xg_batch_tuning", "xg_batch_create", "xg_batch_count", "xg_batch_instance",
            "xg_batch_step", "xg_batch_rhs", "xg_batch_autotune", "xg_batch_set_tuning",
@@ -123,6 +123,8 @@ def library():
     lib.xg_set_contraction.argtypes = [P, I]
     lib.xg_set_fused.restype = I
     lib.xg_set_fused.argtypes = [P, I]
+    lib.xg_step_stream.restype = I
+    lib.xg_step_stream.argtypes = [P, I, P, P, D, I, P]
     lib.xg_profile.restype = I
     lib.xg_profile.argtypes = [P, I]
     lib.xg_kernel_times.restype = I
@@ -319,6 +321,29 @@ def xg_get_state(ctx, q, where=None, stream=None):
 
 def xg_set_contraction(ctx, mode):
     _check(library().xg_set_contraction(ctx, int(mode)), "xg_set_contraction")
+
+
+def xg_step_stream(ctx, q_in, q_out, dt, nsteps=1, stream=None):
+    """nsteps steps of each host state q_in[k] ([5][Np] float64 CPU tensors or
+    arrays, pinned for the full rate) into q_out[k], the copies overlapping
+    the steps (see include/xg.h)."""
+    if len(q_in) != len(q_out):
+        raise ValueError("q_in and q_out need one entry per input")
+    n = len(q_in)
+    size = 5 * xg_mesh_np(ctx)
+    for a in list(q_in) + list(q_out):
+        if (a.numel() if _is_torch(a) else np.asarray(a).size) != size:
+            raise ValueError("each state needs 5 x Np values")
+    pin = (ctypes.c_void_p * max(n, 1))()
+    pout = (ctypes.c_void_p * max(n, 1))()
+    for k in range(n):
+        pi, wi, _ = _ptr(q_in[k])
+        po, wo, _ = _ptr(q_out[k], writable=True)
+        if wi != XG_HOST or wo != XG_HOST:
+            raise ValueError("xg_step_stream takes host arrays")
+        pin[k], pout[k] = pi, po
+    _check(library().xg_step_stream(ctx, n, pin, pout, float(dt), int(nsteps), _default_stream(stream)),
+           "xg_step_stream")
 
 
 def xg_set_fused(ctx, fused):

@@ -98,6 +98,7 @@ def test_null_arguments(lib):
     n = ctypes.c_longlong()
     assert lib.xg_mesh_np(None, ctypes.byref(n)) == xg.XG_ERR_ARG
     assert lib.xg_set_fused(None, 1) == xg.XG_ERR_ARG
+    assert lib.xg_step_stream(None, 0, None, None, 0.1, 1, None) == xg.XG_ERR_ARG
     assert lib.xg_set_contraction(None, 0) == xg.XG_ERR_ARG
     assert lib.xg_correction_set(None, None, None) == xg.XG_ERR_ARG
     lib.xg_destroy(None)  # no-op
