@@ -567,7 +567,12 @@ __device__ __forceinline__ void tc_infer(TcSmem& S, const InferPack* __restrict_
       for (int o = 0; o < kOut; ++o) Y[o * ldy + s] = (__uint_as_float(r[o]) + S.K.b3[o]) * S.K.oscale[o];
     }
   }
-  if (!ok && tid == 0) atomicOr(flag, 2);
+  if (!ok && tid == 0) {
+    // the products whose completion was not seen may still write tensor
+    // memory: wait (bounded) once more for their commit before freeing it
+    atomicOr(flag, 2);
+    tc::mbar_wait(tc::smem_addr(&S.bar), phase ^ 1u, tc::kWaitNs);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {

@@ -368,6 +368,7 @@ __device__ __forceinline__ void f_plane_tile_h16(const FParams& P, const FBufs& 
   tc::fence_proxy_async();
   bool ok = tc::mbar_wait(bar_a, 0, tc::kWaitNs);
   int bad = __syncthreads_or(!ok);
+  uint32_t bad_parity = 0;                             // the phase whose completion was not seen
   tc::fence_after_sync();
   if (!bad) {
     h16_epilogue(STX, SC, DSC[0], tm, T.oy, T.ekx);
@@ -379,12 +380,16 @@ __device__ __forceinline__ void f_plane_tile_h16(const FParams& P, const FBufs& 
     if (tid == 0) h16_products(OPY, BO + 2 * L::B_HALVES, BO + 3 * L::B_HALVES, tm, bar_a);
     ok = tc::mbar_wait(bar_a, 1, tc::kWaitNs);
     bad = __syncthreads_or(!ok);
+    bad_parity = 1;
     tc::fence_after_sync();
     if (!bad) {
       h16_epilogue(STY, SC + L::ITEMS, DSC[1], tm, T.ox, T.eky);
       if (tid < L::LINES) STY[tid * RP + L::RN] = hy;
     }
   }
+  // products whose completion was not seen may still write tensor memory:
+  // wait (bounded) once more for their commit before freeing it
+  if (bad && tid == 0) tc::mbar_wait(bar_a, bad_parity, tc::kWaitNs);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {

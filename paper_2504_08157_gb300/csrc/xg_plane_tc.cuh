@@ -196,6 +196,7 @@ __device__ __forceinline__ void f_plane_tile_tc(const FParams& P, const FBufs& B
   const float hx = tc_plane_halo(P, 0, XH, XL, T.oy, T.hxl);
   bool ok = tc::mbar_wait(bar_a, 0, tc::kWaitNs);
   int bad = __syncthreads_or(!ok);
+  uint32_t bad_parity = 0;                             // the phase whose completion was not seen
   tc::fence_after_sync();
   if (!bad) {
     tc_plane_epilogue(XH, XL, tm, T.oy, T.ekx);
@@ -208,12 +209,16 @@ __device__ __forceinline__ void f_plane_tile_tc(const FParams& P, const FBufs& B
     const float hy = tc_plane_halo(P, 1, YH, YL, T.ox, T.hyl);
     ok = tc::mbar_wait(bar_a, 1, tc::kWaitNs);
     bad = __syncthreads_or(!ok);
+    bad_parity = 1;
     tc::fence_after_sync();
     if (!bad) {
       tc_plane_epilogue(YH, YL, tm, T.ox, T.eky);
       if (tid < L::LINES) YL[tid * PT + L::RN] = hy;
     }
   }
+  // products whose completion was not seen may still write tensor memory:
+  // wait (bounded) once more for their commit before freeing it
+  if (bad && tid == 0) tc::mbar_wait(bar_a, bad_parity, tc::kWaitNs);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
