@@ -160,8 +160,12 @@ __device__ __forceinline__ df df_row(const DfParams& P, int a, const df (&f)[N +
 }
 
 // ---------------------------------------------------------------- x lines
+// Orders up to 4 at 8 CTAs per SM (64 registers): 0.691 against 0.722 ms per
+// launch with no bound (71 registers, 7 CTAs) and 0.706 at 10 (spilling), on
+// the 128 x 128 x 16 order-4 box; higher orders would spill at 8
+__host__ __device__ constexpr int df_x_min_blocks(int N) { return N <= 4 ? 8 : 1; }
 template <int N>
-__global__ void __launch_bounds__(kXThreads) k_df_line_x(const DfParams P, const DfBufs B) {
+__global__ void __launch_bounds__(kXThreads, df_x_min_blocks(N)) k_df_line_x(const DfParams P, const DfBufs B) {
   extern __shared__ df smd[];
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
   const int nseg = P.nseg[0];
