@@ -273,8 +273,10 @@ def correction_study(case, seed, coarse_nel, coarse_steps, dev, filter_order=2):
                  start of the step (xg_correction_set);
       filtered:  the same correction passed through a low-pass filter (its
                  interpolant on the same elements at order ``filter_order``,
-                 two xg_restrict calls), which keeps most of its norm.
-    Returns the per-variable errors of the three runs and the filtered
+                 two xg_restrict calls), which keeps most of its norm;
+      bf16:      the exact correction rounded to bfloat16, the precision of
+                 the network's inference (a data conversion, for the study).
+    Returns the per-variable errors of the runs and the filtered
     correction's share of the exact one's norm at t = 0."""
     torch = _torch()
     fine_nel = tuple(2 * n for n in coarse_nel)
@@ -283,15 +285,15 @@ def correction_study(case, seed, coarse_nel, coarse_steps, dev, filter_order=2):
     mwl = case(seed, nel=coarse_nel, N=filter_order)
     ctxs = []
     try:
-        for w in (fwl, cwl, cwl, cwl, cwl, mwl):
+        for w in (fwl, cwl, cwl, cwl, cwl, mwl, cwl):
             ctxs.append(make_ctx(w, dev))
-        fctx, probe, plain, exact, filt, low = ctxs
+        fctx, probe, plain, exact, filt, low, rb16 = ctxs
         npc, npm = xg.xg_mesh_np(probe), xg.xg_mesh_np(low)
         Z = lambda n: torch.empty((5, n), dtype=torch.float64, device=dev)
         Rq, RL, Tm, Tf = Z(npc), Z(npc), Z(npm), Z(npc)
         xg.xg_restrict(fctx, probe, _state(fctx, dev), Rq)
         q0 = Rq.clone()
-        for c in (plain, exact, filt):
+        for c in (plain, exact, filt, rb16):
             xg.xg_set_state(c, q0)
         xg.xg_step(plain, cwl["dt"], coarse_steps)
         share = None
@@ -308,19 +310,22 @@ def correction_study(case, seed, coarse_nel, coarse_steps, dev, filter_order=2):
                          for v in range(5)]
             xg.xg_correction_set(exact, T)
             xg.xg_correction_set(filt, Tf)
+            xg.xg_correction_set(rb16, T.to(torch.bfloat16).to(torch.float64).contiguous())
             xg.xg_step(exact, cwl["dt"], 1)
             xg.xg_step(filt, cwl["dt"], 1)
+            xg.xg_step(rb16, cwl["dt"], 1)
             xg.xg_step(fctx, fwl["dt"], 2)                 # the refined step is half the coarse one
         xg.xg_restrict(fctx, probe, _state(fctx, dev), Rq)
         ref0 = Rq - q0
         err = lambda c: [float(torch.linalg.norm(_state(c, dev)[v] - Rq[v]) /
                                torch.linalg.norm(ref0[v]).clamp_min(1e-300)) for v in range(5)]
-        return dict(plain=err(plain), exact=err(exact), filtered=err(filt), filtered_norm_share=share,
+        return dict(plain=err(plain), exact=err(exact), filtered=err(filt), exact_in_bfloat16=err(rb16),
+                    filtered_norm_share=share,
                     filter="interpolant of order %d on the same elements" % filter_order,
                     what="relative L2 distance from the restricted refined state after %d coarse "
                          "steps, per variable, relative to the refined run's change, of coarse runs "
-                         "with no correction, the exact training target as correction, and that "
-                         "target low-pass filtered" % coarse_steps)
+                         "with no correction, the exact training target as correction, that "
+                         "target low-pass filtered, and that target rounded to bfloat16" % coarse_steps)
     finally:
         for c in ctxs:
             xg.xg_destroy(c)
