@@ -77,6 +77,11 @@ def fp32_kernel_names(wl, contract=0, fused=False):
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x
 # 2 flop x 2.07 GHz (maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 instructions (DFMA + DADD + DMUL) per node and launch of the mixed
+# path's kernels, from the --set full capture of the 64x64x16 order-4 case
+# (profiles/line_kernels_tc.md); the pipe issues 2 per clock per SM.
+DF64_FP64_INSTR_PER_NODE = {"k_df_line_x": 17.5, "k_df_tline_y": 18.6, "k_df_tline_z": 20.2}
+FP64_PIPE_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
 
 
 def flops_per_node(kernel, N):
@@ -591,6 +596,18 @@ def run_xg(args, world, rank, local):
         roof["alu"] = {"kernel": kname, "achieved": round(fach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                        "unit": "TFLOP/s", "frac": round(fach / FP64_PEAK_TFLOPS, 4),
                        "peak_source": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    if prec == xg.XG_DF64 and wl["N"] == 4:
+        # the pipe that binds this path: FP64 instructions over the stage and per kernel
+        inst = sum(DF64_FP64_INSTR_PER_NODE.values()) * cfg["nodes"]
+        per_k = {n: round(DF64_FP64_INSTR_PER_NODE[n] * cfg["nodes"] / (per_launch[n] / 1e3) / 1e9
+                          / FP64_PIPE_PEAK_GINSTR, 4) for n in DF64_FP64_INSTR_PER_NODE if n in per_launch}
+        ach_i = inst / stage_s / 1e9
+        roof["alu"] = {"pipe": "fp64", "achieved": round(ach_i, 1), "peak": round(FP64_PIPE_PEAK_GINSTR, 1),
+                       "unit": "G FP64 instructions/s", "frac": round(ach_i / FP64_PIPE_PEAK_GINSTR, 4),
+                       "kernel_frac": per_k,
+                       "instructions_per_node_and_stage": round(sum(DF64_FP64_INSTR_PER_NODE.values()), 1),
+                       "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (maximum SM "
+                                      "clock); instruction counts from the ncu capture in profiles/"}
     hbm_frac = achieved / hbm
 
     # end to end through the C ABI with pinned host buffers
