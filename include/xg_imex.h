@@ -50,12 +50,15 @@ typedef struct {
  *                   stage solves
  *   max_iterations  the largest count of one solve
  *   solves          stage solves (2 per step)
- *   max_residual    the largest final relative residual */
+ *   max_residual    the largest final relative residual
+ *   reorthogonalised  Arnoldi steps whose first Gram-Schmidt pass cancelled
+ *                   (removed more than half of |w|^2) and that took a second */
 typedef struct {
   long long iterations;
   int max_iterations;
   int solves;
   double max_residual;
+  long long reorthogonalised;
 } xg_imex_stats;
 
 /* nsteps ARK2 steps of size dt; opts and stats may be NULL. The first call

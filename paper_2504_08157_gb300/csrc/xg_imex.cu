@@ -9,10 +9,10 @@
 // structure of the right-hand side's contractions.  One kernel returns
 // c0 v + c1 L(v), so a GMRES product (I - dt g L) v is a single pass.
 //
-// GMRES (restarted, classical Gram-Schmidt twice) runs on the host with
-// the device vectors; the inner products are deterministic (fixed grid,
-// per-block partial sums added on the host in block order) and weight
-// variable v by 1/rms(b_v)^2.
+// GMRES (restarted; classical Gram-Schmidt, reorthogonalised where the
+// first pass cancels) runs on the host with the device vectors; the inner
+// products are deterministic (fixed grid, per-block partial sums added on
+// the host in block order) and weight variable v by 1/rms(b_v)^2.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -232,6 +232,7 @@ struct Imex {
   double* partial = nullptr;   // [kDotBlocksMax][8]
   int dot_blocks = 512;        // blocks of the reductions: 4 per SM
   std::vector<double> hpart;
+  long long reorth = 0;        // Arnoldi steps that took a second Gram-Schmidt pass
 };
 
 cudaError_t launch_linear(xg_ctx* c, const Imex& X, const double* v, double c0, double c1, double* out,
@@ -378,15 +379,46 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
     g[0] = beta;
     int j = 0;
     for (; j < m; ++j) {
-      // w = (I - h L) v_j, orthogonalised twice against v_0..v_j
-      *err = launch_linear(c, X, vec(j), 1.0, -h, vec(j + 1), st);
+      // The Arnoldi step runs on L: A = I - h L spans the same Krylov space,
+      // and L V_m = V_{m+1} H_L gives A V_m = V_{m+1} (I~ - h H_L) exactly,
+      // while L v_j -- unlike A v_j, which is mostly v_j -- is not largely
+      // removed by its projection.  w = L v_j is orthogonalised against
+      // v_0..v_j by one classical Gram-Schmidt pass; a second pass only where
+      // the first removed more than half of |w|^2 (the criterion of Daniel,
+      // Gragg, Kaufman & Stewart, 1976).  The pass's multi-dot includes
+      // <w, w>, and the norm after it follows from Pythagoras in the weighted
+      // inner product (the v_i are orthonormal in it), so a pass without a
+      // second one is one multi-dot and one combination that also normalises.
+      *err = launch_linear(c, X, vec(j), 0.0, 1.0, vec(j + 1), st);
       if (*err != cudaSuccess) return XG_ERR_CUDA;
       for (int i = 0; i <= j; ++i) vp[i] = vec(i);
+      vp[j + 1] = vec(j + 1);
       std::fill(hcol.begin(), hcol.end(), 0.0);
-      for (int pass = 0; pass < 2; ++pass) {
+      *err = wdots(X, np, vec(j + 1), vp.data(), j + 2, h2.data(), st);
+      if (*err != cudaSuccess) return XG_ERR_CUDA;
+      double w2 = h2[j + 1], s2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        hcol[i] = h2[i];
+        s2 += h2[i] * h2[i];
+      }
+      const double r2 = w2 - s2;
+      std::vector<std::pair<double, const double*>> t;
+      if (r2 > 0.5 * w2) {
+        const double nrm = std::sqrt(r2), inv = 1.0 / nrm;
+        t.push_back({inv, vec(j + 1)});
+        for (int i = 0; i <= j; ++i) t.push_back({-h2[i] * inv, vec(i)});
+        *err = comb(t, vec(j + 1), n, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+        hcol[j + 1] = nrm;
+      } else {
+        // cancellation: subtract, orthogonalise once more, and take the norm exactly
+        t.push_back({1.0, vec(j + 1)});
+        for (int i = 0; i <= j; ++i) t.push_back({-h2[i], vec(i)});
+        *err = comb(t, vec(j + 1), n, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
         *err = wdots(X, np, vec(j + 1), vp.data(), j + 1, h2.data(), st);
         if (*err != cudaSuccess) return XG_ERR_CUDA;
-        std::vector<std::pair<double, const double*>> t;
+        t.clear();
         t.push_back({1.0, vec(j + 1)});
         for (int i = 0; i <= j; ++i) {
           t.push_back({-h2[i], vec(i)});
@@ -394,17 +426,20 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
         }
         *err = comb(t, vec(j + 1), n, st);
         if (*err != cudaSuccess) return XG_ERR_CUDA;
-      }
-      double w2;
-      const double* wp = vec(j + 1);
-      *err = wdots(X, np, vec(j + 1), &wp, 1, &w2, st);
-      if (*err != cudaSuccess) return XG_ERR_CUDA;
-      hcol[j + 1] = std::sqrt(w2);
-      ++*iters;
-      if (hcol[j + 1] > 0.0) {
-        *err = comb({{1.0 / hcol[j + 1], vec(j + 1)}}, vec(j + 1), n, st);
+        const double* wp = vec(j + 1);
+        *err = wdots(X, np, vec(j + 1), &wp, 1, &w2, st);
         if (*err != cudaSuccess) return XG_ERR_CUDA;
+        hcol[j + 1] = std::sqrt(w2);
+        if (hcol[j + 1] > 0.0) {
+          *err = comb({{1.0 / hcol[j + 1], vec(j + 1)}}, vec(j + 1), n, st);
+          if (*err != cudaSuccess) return XG_ERR_CUDA;
+        }
+        ++X.reorth;
       }
+      ++*iters;
+      // the column of I~ - h H_L
+      for (int i = 0; i <= j + 1; ++i) hcol[i] *= -h;
+      hcol[j] += 1.0;
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
@@ -576,8 +611,10 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
       int it = 0;
       double res = 0.0;
       cudaError_t ge = cudaSuccess;
+      const long long reorth0 = X.reorth;
       const xg_status s = gmres(c, X, dt * ai[i][i], tol, maxrs, &it, &res, st, &ge);
       if (stats) {
+        stats->reorthogonalised += X.reorth - reorth0;
         stats->iterations += it;
         stats->max_iterations = std::max(stats->max_iterations, it);
         stats->solves += 1;

@@ -74,11 +74,13 @@ class xg_imex_opts(ctypes.Structure):
 
 class xg_imex_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_longlong), ("max_iterations", ctypes.c_int),
-                ("solves", ctypes.c_int), ("max_residual", ctypes.c_double)]
+                ("solves", ctypes.c_int), ("max_residual", ctypes.c_double),
+                ("reorthogonalised", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(iterations=self.iterations, max_iterations=self.max_iterations,
-                    solves=self.solves, max_residual=self.max_residual)
+                    solves=self.solves, max_residual=self.max_residual,
+                    reorthogonalised=self.reorthogonalised)
 
 
 class XgError(RuntimeError):
