@@ -182,12 +182,14 @@ xg_status xg_set_contraction(xg_ctx* ctx, int mode);
  * overlap the steps of input k (the host link carries both directions at
  * once), so for count > 1 they hide behind the arithmetic.  q_in and q_out
  * are arrays of count host pointers (pinned memory gives the full copy
- * rate); a q_out pointer may repeat (its last write is the latest output).
+ * rate); a q_out pointer may repeat (its last write is the latest output),
+ * but no output may overlap any input (XG_ERR_ARG, checked on the host).
  * The reference state of xg_set_state is kept; afterwards the context holds
  * the last output's state.  Outputs equal set_state + step + get_state of
  * each input bit for bit.  Allocates 4 FP64 state arrays of device memory
  * on first use; waits for the GPU.  Errors: XG_ERR_ARG (NULL, count < 0, no
- * reference state yet), XG_ERR_UNSUPPORTED (a partitioned context),
+ * reference state yet, an output overlapping an input), XG_ERR_UNSUPPORTED (a
+ * partitioned context),
  * XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, XG_ERR_CUDA. */
 xg_status xg_step_stream(xg_ctx* ctx, int count, const double* const* q_in, double* const* q_out, double dt,
                          int nsteps, void* stream);

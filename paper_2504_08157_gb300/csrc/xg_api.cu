@@ -5,6 +5,7 @@
 // (three line kernels).  Mesh checks and the launch constants (LGL
 // derivative matrix, equation-of-state series) are in xg_setup.h.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -833,6 +834,14 @@ xg_status xg_step_stream(xg_ctx* c, int count, const double* const* q_in, double
   for (int k = 0; k < count; ++k)
     if (!q_in[k] || !q_out[k]) return XG_ERR_ARG;
   if (count == 0) return XG_OK;
+  {  // an output that overlaps any input would race with the uploads (other stream)
+    const uintptr_t len = sizeof(double) * 5 * (uintptr_t)c->np;
+    for (int k = 0; k < count; ++k)
+      for (int i = 0; i < count; ++i) {
+        const uintptr_t o = (uintptr_t)q_out[k], p = (uintptr_t)q_in[i];
+        if (o < p + len && p < o + len) return XG_ERR_ARG;
+      }
+  }
   {
     const cudaError_t e = stream_setup(c);
     if (e == cudaErrorMemoryAllocation) return XG_ERR_OOM;

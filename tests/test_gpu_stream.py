@@ -57,3 +57,7 @@ def test_step_stream_checks(cuda_device):
         with pytest.raises(xg.XgError) as e:
             xg.xg_step_stream(g.ctx, [wl["q"]], [wl["q"].copy()], float("nan"))
         assert e.value.status == xg.XG_ERR_ARG
+        a, b = wl["q"].copy(), wl["q"].copy()
+        with pytest.raises(xg.XgError) as e:                 # an output that is a later input
+            xg.xg_step_stream(g.ctx, [a, b], [b, b], wl["dt"])
+        assert e.value.status == xg.XG_ERR_ARG
