@@ -50,7 +50,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2504_08157_gb300", "csrc", f)
                for f in ("xg_kernels.cuh", "xg_kernels_df.cuh", "xg_df.cuh", "xg_kernels_f32.cuh",
-                         "xg_plane_f32.cuh", "xg_batch.cu", "xg_closure.cu", "xg_tc.cuh", "xg_plane_tc.cuh")]
+                         "xg_plane_f32.cuh", "xg_batch.cu", "xg_closure.cu", "xg_tc.cuh", "xg_plane_tc.cuh",
+                         "xg_plane_h16.cuh", "xg_column_f32.cuh", "xg_tma.cuh")]
 KERNELS = ("k_line_x", "k_line_y", "k_line_z")
 # the kernels behind the three timing slots in each precision (the FP32 form
 # fuses the x and y passes into one plane kernel; slot 1 stays empty)
