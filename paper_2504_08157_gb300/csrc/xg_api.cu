@@ -516,6 +516,7 @@ cudaError_t run_stage(xg_ctx* c, const void* q, const void* qn, void* out, doubl
   B.beta64 = beta;
   B.rhs_only = rhs_only;
   B.face_hi = c->part_send[1];
+  B.Fy = c->Fy;
   return launch_df_stage(c, B, st, parts);
 }
 
@@ -603,6 +604,8 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
     }
   }
   e = cudaMalloc((void**)&c->flag, sizeof(int));
+  if (e == cudaSuccess && c->dfm)
+    e = cudaMalloc((void**)&c->Fy, sizeof(double) * 5 * (size_t)c->P.nseg[1] * (size_t)n[2] * (size_t)n[0]);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hflag, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->wasm, sizeof(double) * (size_t)(n[0] + n[1] + n[2]));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 5 * kDiagBlocks);
@@ -1084,6 +1087,7 @@ void xg_destroy(xg_ctx* c) {
   cudaFree(c->Dq);
   cudaFree(c->W);
   cudaFree(c->T);
+  cudaFree(c->Fy);
   cudaFree(c->S);
   cudaFree(c->base);
   cudaFree(c->base64);

@@ -46,6 +46,7 @@ struct xg_ctx {
   double* Dq = nullptr;  // q^{n+1}; swapped with A after every step
   double* W = nullptr;   // [4][np] primitives v, w, p', theta (FP32: [3][np])
   double* T = nullptr;   // [5][np] partial tendency
+  double* Fy = nullptr;  // XG_DF64: [5][nseg_y][nz][nx] y-face rows between the y and z passes
   double* S = nullptr;   // [np] heating
   double* base = nullptr;  // [4][nz] (double-float pairs for XG_DF64 and XG_FP32)
   double* base64 = nullptr;  // [4][nz] the same table in FP64
