@@ -81,7 +81,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 instructions (DFMA + DADD + DMUL) per node and launch of the mixed
 # path's kernels, from the --set full capture of the 64x64x16 order-4 case
 # (profiles/line_kernels_tc.md); the pipe issues 2 per clock per SM.
-DF64_FP64_INSTR_PER_NODE = {"k_df_line_x": 17.5, "k_df_tline_y": 18.6, "k_df_tline_z": 20.2}
+DF64_FP64_INSTR_PER_NODE = {"k_df_line_x": 17.5, "k_df_tline_y": 14.0, "k_df_tline_z": 20.6}
 FP64_PIPE_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
 
 
