@@ -52,7 +52,8 @@ typedef struct {
  *   solves          stage solves (2 per step)
  *   max_residual    the largest final relative residual
  *   reorthogonalised  Arnoldi steps whose first Gram-Schmidt pass cancelled
- *                   (removed more than half of |w|^2) and that took a second */
+ *                   severely (removed more than 1 - 1e-4 of |w|^2) and that
+ *                   took a second */
 typedef struct {
   long long iterations;
   int max_iterations;

@@ -389,6 +389,8 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
       // <w, w>, and the norm after it follows from Pythagoras in the weighted
       // inner product (the v_i are orthonormal in it), so a pass without a
       // second one is one multi-dot and one combination that also normalises.
+      // Where the pass removed more than half of |w|^2 but not 1 - 1e-4 of it,
+      // the norm is taken exactly instead; only beyond that a second pass runs.
       *err = launch_linear(c, X, vec(j), 0.0, 1.0, vec(j + 1), st);
       if (*err != cudaSuccess) return XG_ERR_CUDA;
       for (int i = 0; i <= j; ++i) vp[i] = vec(i);
@@ -410,8 +412,23 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
         *err = comb(t, vec(j + 1), n, st);
         if (*err != cudaSuccess) return XG_ERR_CUDA;
         hcol[j + 1] = nrm;
+      } else if (r2 > 1e-4 * w2) {
+        // moderate cancellation: one pass still leaves orthogonality to
+        // ~eps |w| / |w'| <= 1e2 eps; subtract and take the norm exactly
+        t.push_back({1.0, vec(j + 1)});
+        for (int i = 0; i <= j; ++i) t.push_back({-h2[i], vec(i)});
+        *err = comb(t, vec(j + 1), n, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+        const double* wp = vec(j + 1);
+        *err = wdots(X, np, vec(j + 1), &wp, 1, &w2, st);
+        if (*err != cudaSuccess) return XG_ERR_CUDA;
+        hcol[j + 1] = std::sqrt(w2);
+        if (hcol[j + 1] > 0.0) {
+          *err = comb({{1.0 / hcol[j + 1], vec(j + 1)}}, vec(j + 1), n, st);
+          if (*err != cudaSuccess) return XG_ERR_CUDA;
+        }
       } else {
-        // cancellation: subtract, orthogonalise once more, and take the norm exactly
+        // severe cancellation: subtract, orthogonalise once more, and take the norm exactly
         t.push_back({1.0, vec(j + 1)});
         for (int i = 0; i <= j; ++i) t.push_back({-h2[i], vec(i)});
         *err = comb(t, vec(j + 1), n, st);
