@@ -1260,7 +1260,7 @@ def main():
     ap.add_argument("--rate-only", action="store_true",
                     help="closure workload: only the step rates (no training or evaluation)")
     ap.add_argument("--eval-steps", type=int, default=500,
-                    help="closure workload: coarse steps of the judged run")
+                    help="closure workload: coarse steps of the runs compared with the refined run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "df64", "fp32"], default="df64",
