@@ -633,9 +633,10 @@ xg_status xg_mesh_create(const xg_mesh_desc* d, xg_ctx** out) {
   }
   if (e == cudaSuccess) e = configure(c);
   if (e != cudaSuccess) {
+    const bool oom = e == cudaErrorMemoryAllocation;
     fail_cuda(c, e, "xg_mesh_create");
     xg_destroy(c);
-    return XG_ERR_CUDA;
+    return oom ? XG_ERR_OOM : XG_ERR_CUDA;
   }
   *out = c;
   return XG_OK;
