@@ -496,7 +496,7 @@ def make_ctx(xg, torch, wl, dev, precision=0):
 _Z_VALUES = 5 + 3 + 5 + 1 + 5 * 2 / 3 + 5
 KERNEL_VALUES_PER_NODE = {"k_line_x": 14, "k_line_y": 16, "k_line_z": _Z_VALUES,
                           # the mixed path's y pass also writes, and its z pass reads, the rows of
-                          # the y faces (5 values at one plane in N)
+                          # the y faces (5 values at one plane in N = 4, the bench order)
                           "k_df_line_x": 14, "k_df_tline_y": 16 + 5 / 4, "k_df_tline_z": _Z_VALUES + 5 / 4,
                           "k_f_plane_xy": 13, "k_f_plane_xy_tc": 13, "k_f_plane_xy_h16": 13,
                           "k_f_tline": _Z_VALUES - 1, "k_f_column": 5 + 1 + 5 * 2 / 3 + 5}
