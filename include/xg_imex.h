@@ -22,8 +22,12 @@
  * GMRES on the system scaled per variable, so that rho', the momentum and
  * Theta' each reach the relative tolerance.
  *
- * Native FP64 contexts only. Hyper-diffusion and the sponge of
- * xg_dynamics.h, when set, belong to the explicit part.
+ * XG_FP64 and XG_DF64 contexts. L, GMRES and every combination of
+ * vectors are FP64 in both; the explicit part S is the context's own stage
+ * in right-hand-side mode (in XG_DF64 the mixed stage of xg.h, the
+ * rho' and Theta' tendencies in FP64 and the momentum in double-float).
+ * Hyper-diffusion and the sponge of xg_dynamics.h (XG_FP64 only), when
+ * set, belong to the explicit part.
  */
 #ifndef XG_IMEX_H
 #define XG_IMEX_H
@@ -67,7 +71,7 @@ typedef struct {
  * Errors:
  *   XG_ERR_ARG          NULL ctx, dt not finite or <= 0, nsteps < 0, an
  *                       option out of range, no state
- *   XG_ERR_UNSUPPORTED  the context is not XG_FP64
+ *   XG_ERR_UNSUPPORTED  an XG_FP32 context, or a partitioned one
  *   XG_ERR_TIMEOUT      a stage solve did not reach tol within its restarts;
  *                       the state is left at the start of that step
  *   XG_ERR_NONFINITE, XG_ERR_OOM, XG_ERR_CUDA */
@@ -75,7 +79,7 @@ xg_status xg_step_imex(xg_ctx* ctx, double dt, int nsteps, const xg_imex_opts* o
                        xg_imex_stats* stats, void* stream);
 
 /* out [5][Np] = L(v) for device arrays v, out (the test hook of the linear
- * operator). Errors: XG_ERR_ARG, XG_ERR_UNSUPPORTED (not XG_FP64), no
+ * operator). Errors: XG_ERR_ARG, XG_ERR_UNSUPPORTED (XG_FP32), no
  * reference state yet, XG_ERR_CUDA. */
 xg_status xg_linear_operator(xg_ctx* ctx, const double* v, double* out, void* stream);
 

@@ -33,34 +33,35 @@ constexpr int kDotThreads = 256;
 constexpr int kDotBatch = 16;   // vectors per multi-dot launch
 constexpr int kCombMax = 17;    // terms per combination launch
 
-// sum over the node's segment(s) along d of Dm rows times f (times lev[k]
-// for the loaded node's index k along the line, when given): -d/dx_d of the
-// assembled field
+// sum over the node's segment(s) along d of Dm rows times f: -d/dx_d of the
+// assembled field.  With tab (z only) the coefficients are tab's, the rows
+// of Dm already multiplied by a per-level factor of the loaded node:
+// tab[(s (N + 1) + a) (N + 1) + l] = Dm[2][a][l] lev[s N + l] (k_lin_tables).
 template <int N>
 __device__ __forceinline__ double line_sum(const LineParams& P, int d, const double* __restrict__ f,
                                            long long base, long long sd, int g,
-                                           const double* __restrict__ lev) {
+                                           const double* __restrict__ tab) {
   const int nd = P.n[d], nseg = P.nseg[d];
   int s = g / N;
   if (s >= nseg) s = nseg - 1;
   const int a = g - s * N;
+  const double* t = tab ? tab + (s * (N + 1) + a) * (N + 1) : nullptr;
   double acc = 0.0;
 #pragma unroll
   for (int l = 0; l <= N; ++l) {
     int k = s * N + l;
     if (k >= nd) k -= nd;
-    const double v = f[base + sd * k];
-    acc = fma(P.Dm[d][a][l], lev ? lev[k] * v : v, acc);
+    acc = fma(t ? t[l] : P.Dm[d][a][l], f[base + sd * k], acc);
   }
   if (a == 0) {
     if (s > 0 || P.per[d]) {
       const int s2 = s > 0 ? s - 1 : nseg - 1;
+      const double* t2 = tab ? tab + (s2 * (N + 1) + N) * (N + 1) : nullptr;
 #pragma unroll
       for (int l = 0; l <= N; ++l) {
         int k = s2 * N + l;
         if (k >= nd) k -= nd;
-        const double v = f[base + sd * k];
-        acc = fma(P.Dm[d][N][l], lev ? lev[k] * v : v, acc);
+        acc = fma(t2 ? t2[l] : P.Dm[d][N][l], f[base + sd * k], acc);
       }
     } else {
       acc = acc + acc;
@@ -71,11 +72,17 @@ __device__ __forceinline__ double line_sum(const LineParams& P, int d, const dou
   return acc;
 }
 
-// out = c0 v + c1 L(v); cpl = gamma p0 / Theta0 and th0 = Theta0 / rho0 per level
+// out = c0 v + c1 L(v) (out = L(v) for c0 = 0, c1 = 1); cpl = gamma p0 /
+// Theta0 per level, tw and tp the z rows times theta0 = Theta0 / rho0 and
+// times cpl (k_lin_tables).  FP64 work per node: the seven line sums' FMAs
+// (N + 1 each, twice at a face node) and the assembly; the per-level factors
+// of the z sums ride in their coefficients.
 template <int N>
 __global__ void __launch_bounds__(128) k_linear(const LineParams P, const double* __restrict__ v,
                                                 const double* __restrict__ cpl,
-                                                const double* __restrict__ th0, double c0, double c1,
+                                                const double* __restrict__ th0,
+                                                const double* __restrict__ tw,
+                                                const double* __restrict__ tp, double c0, double c1,
                                                 double* __restrict__ out) {
   const long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (I >= P.np) return;
@@ -93,10 +100,10 @@ __global__ void __launch_bounds__(128) k_linear(const LineParams P, const double
   const double dxu = line_sum<N>(P, 0, ru, bx, 1, gx, nullptr);
   const double dyv = line_sum<N>(P, 1, rv, by, nx, gy, nullptr);
   const double dzw = line_sum<N>(P, 2, rw, bz, nxy, gz, nullptr);
-  const double dzwt = line_sum<N>(P, 2, rw, bz, nxy, gz, th0);
+  const double dzwt = line_sum<N>(P, 2, rw, bz, nxy, gz, tw);
   const double dxp = cpl[gz] * line_sum<N>(P, 0, th, bx, 1, gx, nullptr);
   const double dyp = cpl[gz] * line_sum<N>(P, 1, th, by, nx, gy, nullptr);
-  const double dzp = line_sum<N>(P, 2, th, bz, nxy, gz, cpl);
+  const double dzp = line_sum<N>(P, 2, th, bz, nxy, gz, tp);
   double L[5];
   L[0] = dxu + dyv + dzw;
   L[1] = dxp;
@@ -106,8 +113,13 @@ __global__ void __launch_bounds__(128) k_linear(const LineParams P, const double
   if (!P.per[0] && (gx == 0 || gx == nx - 1)) L[1] = 0.0;
   if (!P.per[1] && (gy == 0 || gy == ny - 1)) L[2] = 0.0;
   if (!P.per[2] && (gz == 0 || gz == P.n[2] - 1)) L[3] = 0.0;
+  if (c0 == 0.0 && c1 == 1.0) {
 #pragma unroll
-  for (int c = 0; c < 5; ++c) out[c * np + I] = c0 == 0.0 ? c1 * L[c] : fma(c1, L[c], c0 * v[c * np + I]);
+    for (int c = 0; c < 5; ++c) out[c * np + I] = L[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c * np + I] = c0 == 0.0 ? c1 * L[c] : fma(c1, L[c], c0 * v[c * np + I]);
+  }
 }
 
 struct Comb {
@@ -138,67 +150,76 @@ struct Dots {
   int k;
 };
 
-// partial[b][i] = sum over block b's nodes of sum_var wt[var] w * v_i for
-// the K vectors of D, in a fixed order (deterministic for a given grid): the
-// K loads of a node are issued together, warps reduce by shuffles, the
-// block's warps in order.  SELF (K = 1, v_0 = w): the weighted |w|^2 from one
-// read of w.
+// partial[(b 5 + c) K + i] = sum over block b's nodes of variable c of
+// w v_i, for the K vectors of D, in a fixed order (deterministic for a given
+// grid); the host weights the variables.  One FP64 FMA per loaded value of
+// the v_i: on GB300 a dot product is bound by the FP64 pipe, not by HBM, so
+// the weights stay out of the loop.  The loads of two nodes (K <= 8) or of
+// one are issued together; warps reduce by shuffles, the block's warps in
+// order.  SELF (K = 1, v_0 = w): |w|^2 per variable from one read of w.
 template <int K, bool SELF = false>
-__global__ void __launch_bounds__(kDotThreads) k_wdots(const double* __restrict__ w, const Dots D,
-                                                       const double* __restrict__ wt, long long np,
+__global__ void __launch_bounds__(kDotThreads, 4) k_wdots(const double* __restrict__ w, const Dots D, long long np,
                                                        double* __restrict__ partial) {
+  constexpr int U = K <= 8 ? 2 : 1;   // nodes per thread and iteration
   __shared__ double red[K][kDotThreads / 32];
-  double acc[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = 0.0;
   const long long per = (np + gridDim.x - 1) / gridDim.x;
   const long long lo = blockIdx.x * per, hi = min(np, lo + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long step = blockDim.x;
   for (int c = 0; c < 5; ++c) {
-    const double s = wt[c];
     const long long off = c * np;
-    for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) {
-      double v[K];
+    double acc[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = 0.0;
+    long long I = lo + threadIdx.x;
+    for (; I + (U - 1) * step < hi; I += U * step) {
+      double wi[U], v[U][K];
+#pragma unroll
+      for (int u = 0; u < U; ++u) wi[u] = w[off + I + u * step];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[u][i] = SELF ? wi[u] : D.v[i][off + I + u * step];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[i] = fma(wi[u], v[u][i], acc[i]);
+    }
+    if (U > 1 && I < hi) {             // the one node left over (I + step >= hi)
       const double wi = w[off + I];
 #pragma unroll
-      for (int i = 0; i < K; ++i) v[i] = SELF ? wi : D.v[i][off + I];
-      const double a = s * wi;
-#pragma unroll
-      for (int i = 0; i < K; ++i) acc[i] = fma(a, v[i], acc[i]);
+      for (int i = 0; i < K; ++i) acc[i] = fma(wi, SELF ? wi : D.v[i][off + I], acc[i]);
     }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < K; ++i) {
+    for (int i = 0; i < K; ++i) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-    if (lane == 0) red[i][warp] = acc[i];
-  }
-  __syncthreads();
-  if (threadIdx.x < K) {
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
-    partial[blockIdx.x * kDotBatch + threadIdx.x] = t;
+      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+      if (lane == 0) red[i][warp] = acc[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+      partial[((long long)blockIdx.x * 5 + c) * K + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
-// partial[b][c] = sum over block b's nodes of x_c^2
-__global__ void __launch_bounds__(kDotThreads) k_varsq(const double* __restrict__ x, long long np,
-                                                       double* __restrict__ partial) {
-  __shared__ double red[5][kDotThreads];
-  const long long per = (np + gridDim.x - 1) / gridDim.x;
-  const long long lo = blockIdx.x * per, hi = min(np, lo + per);
-  for (int c = 0; c < 5; ++c) {
-    double a = 0.0;
-    for (long long I = lo + threadIdx.x; I < hi; I += blockDim.x) a = fma(x[c * np + I], x[c * np + I], a);
-    red[c][threadIdx.x] = a;
-  }
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h)
-      for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+// tw[(s (N + 1) + a) (N + 1) + l] = Dm[2][a][l] theta0[k] and tp the same
+// with cpl[k], k = s N + l (wrapped when z is periodic): the z rows of the
+// linear operator with their per-level factor
+template <int N>
+__global__ void k_lin_tables(const LineParams P, const double* __restrict__ cpl, const double* __restrict__ th0,
+                             double* __restrict__ tw, double* __restrict__ tp) {
+  const int nseg = P.nseg[2], nd = P.n[2];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nseg * (N + 1) * (N + 1)) return;
+  const int l = e % (N + 1), a = (e / (N + 1)) % (N + 1), s = e / ((N + 1) * (N + 1));
+  int k = s * N + l;
+  if (k >= nd) k -= nd;
+  tw[e] = P.Dm[2][a][l] * th0[k];
+  tp[e] = P.Dm[2][a][l] * cpl[k];
 }
 
 __global__ void k_lin_levels(const double* __restrict__ base, int nz, double gamma, double* __restrict__ cpl,
@@ -228,8 +249,10 @@ struct Imex {
   double* q1 = nullptr;        // q^{n+1}
   double* cpl = nullptr;       // [nz]
   double* th0 = nullptr;       // [nz]
-  double* wt = nullptr;        // [5] inner-product weights
-  double* partial = nullptr;   // [kDotBlocksMax][8]
+  double* tw = nullptr;        // [nseg_z][N + 1][N + 1] z rows times theta0
+  double* tp = nullptr;        // [nseg_z][N + 1][N + 1] z rows times cpl
+  double wt[5] = {1.0, 1.0, 1.0, 1.0, 1.0};   // inner-product weights per variable
+  double* partial = nullptr;   // [kDotBlocksMax][5][kDotBatch]
   int dot_blocks = 512;        // blocks of the reductions: 4 per SM
   std::vector<double> hpart;
   long long reorth = 0;        // Arnoldi steps that took a second Gram-Schmidt pass
@@ -240,14 +263,14 @@ cudaError_t launch_linear(xg_ctx* c, const Imex& X, const double* v, double c0, 
   const LineParams& P = c->P;
   const unsigned blocks = (unsigned)((c->np + 127) / 128);
   switch (c->d.order) {
-    case 1: xg::k_linear<1><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 2: xg::k_linear<2><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 3: xg::k_linear<3><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 4: xg::k_linear<4><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 5: xg::k_linear<5><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 6: xg::k_linear<6><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 7: xg::k_linear<7><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
-    case 8: xg::k_linear<8><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, c0, c1, out); break;
+    case 1: xg::k_linear<1><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 2: xg::k_linear<2><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 3: xg::k_linear<3><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 4: xg::k_linear<4><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 5: xg::k_linear<5><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 6: xg::k_linear<6><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 7: xg::k_linear<7><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
+    case 8: xg::k_linear<8><<<blocks, 128, 0, st>>>(P, v, X.cpl, X.th0, X.tw, X.tp, c0, c1, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -287,35 +310,49 @@ cudaError_t comb(const std::vector<std::pair<double, const double*>>& terms, dou
   return cudaGetLastError();
 }
 
-// weighted inner products of w with vs[0..k-1]
+// unweighted per-variable inner products of w with vs[0..k-1] (k <= kDotBatch)
+// into X.hpart[(b 5 + c) k + i]
+cudaError_t var_dots(Imex& X, long long np, const double* w, const double* const* vs, int k, cudaStream_t st) {
+  xg::Dots D;
+  memset(&D, 0, sizeof(D));
+  D.k = k;
+  for (int i = 0; i < k; ++i) D.v[i] = vs[i];
+  if (k == 1 && D.v[0] == w) {
+    xg::k_wdots<1, true><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, np, X.partial);
+  } else switch (k) {
+#define XG_WDOTS_CASE(K) \
+  case K: xg::k_wdots<K><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, np, X.partial); break;
+    XG_WDOTS_CASE(1) XG_WDOTS_CASE(2) XG_WDOTS_CASE(3) XG_WDOTS_CASE(4) XG_WDOTS_CASE(5)
+    XG_WDOTS_CASE(6) XG_WDOTS_CASE(7) XG_WDOTS_CASE(8) XG_WDOTS_CASE(9) XG_WDOTS_CASE(10)
+    XG_WDOTS_CASE(11) XG_WDOTS_CASE(12) XG_WDOTS_CASE(13) XG_WDOTS_CASE(14) XG_WDOTS_CASE(15)
+    XG_WDOTS_CASE(16)
+    default: return cudaErrorInvalidValue;
+#undef XG_WDOTS_CASE
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * X.dot_blocks * 5 * k, cudaMemcpyDeviceToHost,
+                        st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// weighted inner products of w with vs[0..k-1]: per variable the blocks'
+// partials in block order, then the variables in order, each times its weight
 cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* vs, int k, double* out,
                   cudaStream_t st) {
   for (int i0 = 0; i0 < k; i0 += xg::kDotBatch) {
-    xg::Dots D;
-    memset(&D, 0, sizeof(D));
-    D.k = std::min(xg::kDotBatch, k - i0);
-    for (int i = 0; i < D.k; ++i) D.v[i] = vs[i0 + i];
-    if (D.k == 1 && D.v[0] == w) {
-      xg::k_wdots<1, true><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
-    } else switch (D.k) {
-#define XG_WDOTS_CASE(K) \
-  case K: xg::k_wdots<K><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial); break;
-      XG_WDOTS_CASE(1) XG_WDOTS_CASE(2) XG_WDOTS_CASE(3) XG_WDOTS_CASE(4) XG_WDOTS_CASE(5)
-      XG_WDOTS_CASE(6) XG_WDOTS_CASE(7) XG_WDOTS_CASE(8) XG_WDOTS_CASE(9) XG_WDOTS_CASE(10)
-      XG_WDOTS_CASE(11) XG_WDOTS_CASE(12) XG_WDOTS_CASE(13) XG_WDOTS_CASE(14) XG_WDOTS_CASE(15)
-      default: xg::k_wdots<xg::kDotBatch><<<X.dot_blocks, xg::kDotThreads, 0, st>>>(w, D, X.wt, np, X.partial);
-#undef XG_WDOTS_CASE
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * X.dot_blocks * xg::kDotBatch,
-                          cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int kb = std::min(xg::kDotBatch, k - i0);
+    const cudaError_t e = var_dots(X, np, w, vs + i0, kb, st);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < D.k; ++i) {
-      double s = 0.0;
-      for (int b = 0; b < X.dot_blocks; ++b) s += X.hpart[(size_t)b * xg::kDotBatch + i];
-      out[i0 + i] = s;
+    for (int i = 0; i < kb; ++i) {
+      double t = 0.0;
+      for (int c = 0; c < 5; ++c) {
+        double s = 0.0;
+        for (int b = 0; b < X.dot_blocks; ++b) s += X.hpart[((size_t)b * 5 + c) * kb + i];
+        t = fma(X.wt[c], s, t);
+      }
+      out[i0 + i] = t;
     }
   }
   return cudaSuccess;
@@ -323,21 +360,15 @@ cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* v
 
 // per-variable weights 1 / mean(b_v^2) (1 where b_v vanishes)
 cudaError_t set_weights(Imex& X, long long np, const double* b, cudaStream_t st) {
-  xg::k_varsq<<<X.dot_blocks, xg::kDotThreads, 0, st>>>(b, np, X.partial);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(X.hpart.data(), X.partial, sizeof(double) * X.dot_blocks * 5, cudaMemcpyDeviceToHost,
-                        st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const cudaError_t e = var_dots(X, np, b, &b, 1, st);
   if (e != cudaSuccess) return e;
-  double wt[5];
   for (int c = 0; c < 5; ++c) {
     double s = 0.0;
     for (int blk = 0; blk < X.dot_blocks; ++blk) s += X.hpart[(size_t)blk * 5 + c];
     const double ms = s / (double)np;
-    wt[c] = ms > 0.0 ? 1.0 / ms : 1.0;
+    X.wt[c] = ms > 0.0 ? 1.0 / ms : 1.0;
   }
-  return cudaMemcpyAsync(X.wt, wt, sizeof(wt), cudaMemcpyHostToDevice, st);
+  return cudaSuccess;
 }
 
 // Solve (I - h L) x = b, x holding the initial guess; returns XG_ERR_TIMEOUT
@@ -383,14 +414,13 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
       // and L V_m = V_{m+1} H_L gives A V_m = V_{m+1} (I~ - h H_L) exactly,
       // while L v_j -- unlike A v_j, which is mostly v_j -- is not largely
       // removed by its projection.  w = L v_j is orthogonalised against
-      // v_0..v_j by one classical Gram-Schmidt pass; a second pass only where
-      // the first removed more than half of |w|^2 (the criterion of Daniel,
-      // Gragg, Kaufman & Stewart, 1976).  The pass's multi-dot includes
-      // <w, w>, and the norm after it follows from Pythagoras in the weighted
-      // inner product (the v_i are orthonormal in it), so a pass without a
-      // second one is one multi-dot and one combination that also normalises.
-      // Where the pass removed more than half of |w|^2 but not 1 - 1e-4 of it,
-      // the norm is taken exactly instead; only beyond that a second pass runs.
+      // v_0..v_j by one classical Gram-Schmidt pass.  The pass's multi-dot
+      // includes <w, w>, and the norm after it follows from Pythagoras in the
+      // weighted inner product (the v_i are orthonormal in it), so a pass is
+      // one multi-dot and one combination that also normalises.  Only where
+      // the pass removed more than 1 - 1e-4 of |w|^2 (a sharper form of the
+      // criterion of Daniel, Gragg, Kaufman & Stewart, 1976, whose bound is
+      // one half) a second pass runs, and the norm is then taken exactly.
       *err = launch_linear(c, X, vec(j), 0.0, 1.0, vec(j + 1), st);
       if (*err != cudaSuccess) return XG_ERR_CUDA;
       for (int i = 0; i <= j; ++i) vp[i] = vec(i);
@@ -405,28 +435,17 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
       }
       const double r2 = w2 - s2;
       std::vector<std::pair<double, const double*>> t;
-      if (r2 > 0.5 * w2) {
+      if (r2 > 1e-4 * w2) {
+        // one pass: orthogonality to ~eps |w| / |w'| <= 1e2 eps; the norm by
+        // Pythagoras, whose rounding (a few eps w2 in w2 and in s2) is
+        // <= ~1e3 eps of r2 here, so v_{j+1} has norm 1 to ~1e-13, and the
+        // combination normalises
         const double nrm = std::sqrt(r2), inv = 1.0 / nrm;
         t.push_back({inv, vec(j + 1)});
         for (int i = 0; i <= j; ++i) t.push_back({-h2[i] * inv, vec(i)});
         *err = comb(t, vec(j + 1), n, st);
         if (*err != cudaSuccess) return XG_ERR_CUDA;
         hcol[j + 1] = nrm;
-      } else if (r2 > 1e-4 * w2) {
-        // moderate cancellation: one pass still leaves orthogonality to
-        // ~eps |w| / |w'| <= 1e2 eps; subtract and take the norm exactly
-        t.push_back({1.0, vec(j + 1)});
-        for (int i = 0; i <= j; ++i) t.push_back({-h2[i], vec(i)});
-        *err = comb(t, vec(j + 1), n, st);
-        if (*err != cudaSuccess) return XG_ERR_CUDA;
-        const double* wp = vec(j + 1);
-        *err = wdots(X, np, vec(j + 1), &wp, 1, &w2, st);
-        if (*err != cudaSuccess) return XG_ERR_CUDA;
-        hcol[j + 1] = std::sqrt(w2);
-        if (hcol[j + 1] > 0.0) {
-          *err = comb({{1.0 / hcol[j + 1], vec(j + 1)}}, vec(j + 1), n, st);
-          if (*err != cudaSuccess) return XG_ERR_CUDA;
-        }
       } else {
         // severe cancellation: subtract, orthogonalise once more, and take the norm exactly
         t.push_back({1.0, vec(j + 1)});
@@ -504,7 +523,8 @@ void imex_free_buffers(Imex* X) {
   cudaFree(X->q1);
   cudaFree(X->cpl);
   cudaFree(X->th0);
-  cudaFree(X->wt);
+  cudaFree(X->tw);
+  cudaFree(X->tp);
   cudaFree(X->partial);
 }
 
@@ -533,7 +553,7 @@ cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
     c->imex = X;
     X->m = m;
     X->n = n;
-    X->hpart.resize((size_t)xg::kDotBlocksMax * xg::kDotBatch);
+    X->hpart.resize((size_t)xg::kDotBlocksMax * 5 * xg::kDotBatch);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
     X->dot_blocks = std::min(xg::kDotBlocksMax, std::max(1, 4 * sms));
@@ -544,8 +564,11 @@ cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
       if (e == cudaSuccess) e = cudaMalloc((void**)p, vb);
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->cpl, sizeof(double) * c->n[2]);
     if (e == cudaSuccess) e = cudaMalloc((void**)&X->th0, sizeof(double) * c->n[2]);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&X->wt, sizeof(double) * 5);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&X->partial, sizeof(double) * xg::kDotBlocksMax * xg::kDotBatch);
+    const size_t tb = sizeof(double) * (size_t)c->P.nseg[2] * (c->d.order + 1) * (c->d.order + 1);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->tw, tb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&X->tp, tb);
+    if (e == cudaSuccess)
+      e = cudaMalloc((void**)&X->partial, sizeof(double) * xg::kDotBlocksMax * 5 * xg::kDotBatch);
     if (e != cudaSuccess) {
       imex_free_buffers(X);
       delete X;
@@ -553,7 +576,17 @@ cudaError_t prepare(xg_ctx* c, int m, cudaStream_t st) {
       return e;
     }
   }
-  xg::k_lin_levels<<<(c->n[2] + 127) / 128, 128, 0, st>>>(c->base, c->n[2], c->P.gamma, X->cpl, X->th0);
+  xg::k_lin_levels<<<(c->n[2] + 127) / 128, 128, 0, st>>>(c->base64, c->n[2], c->P.gamma, X->cpl, X->th0);
+  const int ne = c->P.nseg[2] * (c->d.order + 1) * (c->d.order + 1);
+  const unsigned tblocks = (unsigned)((ne + 127) / 128);
+  switch (c->d.order) {
+#define XG_TABLES_CASE(N) \
+  case N: xg::k_lin_tables<N><<<tblocks, 128, 0, st>>>(c->P, X->cpl, X->th0, X->tw, X->tp); break;
+    XG_TABLES_CASE(1) XG_TABLES_CASE(2) XG_TABLES_CASE(3) XG_TABLES_CASE(4)
+    XG_TABLES_CASE(5) XG_TABLES_CASE(6) XG_TABLES_CASE(7) XG_TABLES_CASE(8)
+#undef XG_TABLES_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -572,7 +605,7 @@ extern "C" {
 xg_status xg_linear_operator(xg_ctx* c, const double* v, double* out, void* stream) {
   if (!c || !v || !out) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
-  if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (c->f32) return XG_ERR_UNSUPPORTED;
   if (!c->has_base) return XG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = prepare(c, c->imex ? static_cast<Imex*>(c->imex)->m : 20, st);
@@ -584,7 +617,7 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
                        void* stream) {
   if (!c) return XG_ERR_ARG;
   if (c->failed) return XG_ERR_CUDA;
-  if (c->dfm || c->f32) return XG_ERR_UNSUPPORTED;
+  if (c->f32) return XG_ERR_UNSUPPORTED;
   if (c->part_open[0] || c->part_open[1]) return XG_ERR_UNSUPPORTED;   // partitioned: explicit only
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !c->has_state) return XG_ERR_ARG;
   double tol = 1e-10;
@@ -613,7 +646,6 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
     // stage 1 is explicit: Q1 = q
     e = rhs_fp64(c, q, X.S[0], st);
     if (e == cudaSuccess) e = launch_linear(c, X, q, 0.0, 1.0, X.L[0], st);
-    const double* Q = q;
     for (int i = 1; i < 3 && e == cudaSuccess; ++i) {
       // b = q + dt sum_j (ae_ij (S_j - L_j) + ai_ij L_j)
       std::vector<std::pair<double, const double*>> t;
@@ -623,7 +655,10 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
         t.push_back({dt * (ai[i][j] - ae[i][j]), X.L[j]});
       }
       e = comb(t, X.b, n, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(X.x, Q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+      // the first guess: q for the first solve; the second starts from the
+      // first's solution, which X.x still holds
+      if (e == cudaSuccess && i == 1)
+        e = cudaMemcpyAsync(X.x, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) break;
       int it = 0;
       double res = 0.0;
@@ -639,11 +674,9 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
       }
       if (s == XG_ERR_CUDA) return fail(c, ge, "xg_step_imex gmres");
       if (s != XG_OK) return s;
-      // S and L of the stage value; keep the value as the next solve's first guess
+      // S and L of the stage value
       e = rhs_fp64(c, X.x, X.S[i], st);
       if (e == cudaSuccess && i < 2) e = launch_linear(c, X, X.x, 0.0, 1.0, X.L[i], st);
-      if (e == cudaSuccess && i == 1) e = cudaMemcpyAsync(X.w, X.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-      Q = X.w;
     }
     if (e == cudaSuccess)
       e = comb({{1.0, q}, {dt * bw[0], X.S[0]}, {dt * bw[1], X.S[1]}, {dt * bw[2], X.S[2]}}, c->Dq, n, st);
