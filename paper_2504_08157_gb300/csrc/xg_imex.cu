@@ -358,16 +358,22 @@ cudaError_t wdots(Imex& X, long long np, const double* w, const double* const* v
   return cudaSuccess;
 }
 
-// per-variable weights 1 / mean(b_v^2) (1 where b_v vanishes)
-cudaError_t set_weights(Imex& X, long long np, const double* b, cudaStream_t st) {
+// per-variable weights 1 / mean(b_v^2) (1 where b_v vanishes), and the
+// weighted |b|^2 from the same partials (the value wdots of b with itself
+// returns, in the same order)
+cudaError_t set_weights(Imex& X, long long np, const double* b, double* bn2, cudaStream_t st) {
   const cudaError_t e = var_dots(X, np, b, &b, 1, st);
   if (e != cudaSuccess) return e;
+  double s[5];
   for (int c = 0; c < 5; ++c) {
-    double s = 0.0;
-    for (int blk = 0; blk < X.dot_blocks; ++blk) s += X.hpart[(size_t)blk * 5 + c];
-    const double ms = s / (double)np;
+    s[c] = 0.0;
+    for (int blk = 0; blk < X.dot_blocks; ++blk) s[c] += X.hpart[(size_t)blk * 5 + c];
+    const double ms = s[c] / (double)np;
     X.wt[c] = ms > 0.0 ? 1.0 / ms : 1.0;
   }
+  double t = 0.0;
+  for (int c = 0; c < 5; ++c) t = fma(X.wt[c], s[c], t);
+  *bn2 = t;
   return cudaSuccess;
 }
 
@@ -378,11 +384,8 @@ xg_status gmres(xg_ctx* c, Imex& X, double h, double tol, int maxrs, int* iters,
   const long long np = c->np, n = X.n;
   const int m = X.m;
   auto vec = [&](int i) { return X.V + (size_t)i * n; };
-  *err = set_weights(X, np, X.b, st);
-  if (*err != cudaSuccess) return XG_ERR_CUDA;
   double bn2;
-  const double* bp = X.b;
-  *err = wdots(X, np, X.b, &bp, 1, &bn2, st);
+  *err = set_weights(X, np, X.b, &bn2, st);
   if (*err != cudaSuccess) return XG_ERR_CUDA;
   const double bnorm = std::sqrt(bn2);
   *iters = 0;
