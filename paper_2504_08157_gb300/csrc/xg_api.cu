@@ -541,7 +541,7 @@ cudaError_t export_values(xg_ctx* c, const void* src, double* dst, long long n, 
 
 }  // namespace
 
-cudaError_t rhs_fp64(xg_ctx* c, const double* q, double* out, cudaStream_t st) {
+cudaError_t rhs_f64_state(xg_ctx* c, const double* q, double* out, cudaStream_t st) {
   return run_stage(c, q, nullptr, out, 0.0, 0.0, 1.0, 1, st);
 }
 

@@ -93,8 +93,9 @@ struct xg_ctx {
 };
 
 void imex_free(xg_ctx* c);
-// the FP64 right-hand side S(q) into out (xg_api.cu)
-cudaError_t rhs_fp64(xg_ctx* c, const double* q, double* out, cudaStream_t st);
+// the right-hand side S(q) of an FP64-state context (XG_FP64, or XG_DF64 by
+// the mixed stage) into out, both [5][Np] doubles (xg_api.cu)
+cudaError_t rhs_f64_state(xg_ctx* c, const double* q, double* out, cudaStream_t st);
 
 // E = H(q) + sponge(q) of the FP64 stage input q into c->dyn_E
 // (xg_dynamics.cu); and freeing its buffers.

@@ -9,10 +9,14 @@
 // structure of the right-hand side's contractions.  One kernel returns
 // c0 v + c1 L(v), so a GMRES product (I - dt g L) v is a single pass.
 //
-// GMRES (restarted; classical Gram-Schmidt, reorthogonalised where the
-// first pass cancels) runs on the host with the device vectors; the inner
-// products are deterministic (fixed grid, per-block partial sums added on
-// the host in block order) and weight variable v by 1/rms(b_v)^2.
+// GMRES (restarted; one classical Gram-Schmidt pass, a second only where the
+// first cancels severely) runs on the host with the device vectors; the
+// inner products are deterministic (fixed grid, per-block and per-variable
+// partial sums added on the host in block order) and weight variable v by
+// 1/rms(b_v)^2.  The explicit part is the context's own stage in
+// right-hand-side mode (FP64, or the mixed XG_DF64 stage); L, the inner
+// products and the combinations are FP64, and all of them are bound by
+// GB300's FP64 pipe.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -647,7 +651,7 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
   for (int step = 0; step < nsteps; ++step) {
     const double* q = c->A;
     // stage 1 is explicit: Q1 = q
-    e = rhs_fp64(c, q, X.S[0], st);
+    e = rhs_f64_state(c, q, X.S[0], st);
     if (e == cudaSuccess) e = launch_linear(c, X, q, 0.0, 1.0, X.L[0], st);
     for (int i = 1; i < 3 && e == cudaSuccess; ++i) {
       // b = q + dt sum_j (ae_ij (S_j - L_j) + ai_ij L_j)
@@ -678,7 +682,7 @@ xg_status xg_step_imex(xg_ctx* c, double dt, int nsteps, const xg_imex_opts* opt
       if (s == XG_ERR_CUDA) return fail(c, ge, "xg_step_imex gmres");
       if (s != XG_OK) return s;
       // S and L of the stage value
-      e = rhs_fp64(c, X.x, X.S[i], st);
+      e = rhs_f64_state(c, X.x, X.S[i], st);
       if (e == cudaSuccess && i < 2) e = launch_linear(c, X, X.x, 0.0, 1.0, X.L[i], st);
     }
     if (e == cudaSuccess)
