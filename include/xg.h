@@ -186,8 +186,11 @@ xg_status xg_set_contraction(xg_ctx* ctx, int mode);
  * but no output may overlap any input (XG_ERR_ARG, checked on the host).
  * The reference state of xg_set_state is kept; afterwards the context holds
  * the last output's state.  Outputs equal set_state + step + get_state of
- * each input bit for bit.  Allocates 4 FP64 state arrays of device memory
- * on first use; waits for the GPU.  Errors: XG_ERR_ARG (NULL, count < 0, no
+ * each input bit for bit.  XG_FP64 and XG_DF64 contexts step each input in
+ * the device array it was uploaded to and download the output from the
+ * array the steps leave it in (no device copies); XG_FP32 converts through
+ * FP64 staging arrays.  Allocates 4 FP64 state arrays of device memory on
+ * first use; waits for the GPU.  Errors: XG_ERR_ARG (NULL, count < 0, no
  * reference state yet, an output overlapping an input), XG_ERR_UNSUPPORTED (a
  * partitioned context),
  * XG_ERR_OOM, XG_ERR_NONFINITE, XG_ERR_TIMEOUT, XG_ERR_CUDA. */

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <new>
 #include <vector>
 
@@ -812,7 +813,8 @@ cudaError_t stream_setup(xg_ctx* c) {
   int made = 0;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ss_h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ss_d2h, cudaStreamNonBlocking);
-  for (; made < 8 && e == cudaSuccess; ++made) e = cudaEventCreateWithFlags(&c->ss_ev[made], cudaEventDisableTiming);
+  for (; made < 12 && e == cudaSuccess; ++made)
+    e = cudaEventCreateWithFlags(&c->ss_ev[made], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     for (int b = 0; b < 2; ++b) {
       cudaFree(c->ss_in[b]);
@@ -827,6 +829,67 @@ cudaError_t stream_setup(xg_ctx* c) {
   }
   c->ss_ready = true;
   return cudaSuccess;
+}
+
+// xg_step_stream for FP64-state contexts (XG_FP64, XG_DF64): the inputs are
+// stepped where they were uploaded.  The state pointer moves to each input's
+// array and the output is downloaded from the array the steps leave it in,
+// so no state is copied on the device.  Six state-sized arrays rotate: the
+// one being stepped (A), the spare of the steps (Dq), and the others, which
+// wait in a pool for uploads (oldest first) once their download, or the
+// work already queued on st for the state array the call starts from, is
+// done.  The context's fields never alias: after every change of A the four
+// arrays that are neither A nor Dq are the ss_in / ss_out fields.
+xg_status stream_in_place(xg_ctx* c, int count, const double* const* q_in, double* const* q_out, double dt,
+                          int nsteps, cudaStream_t st) {
+  const size_t bytes = sizeof(double) * 5 * (size_t)c->np;
+  double* arr[6] = {c->ss_in[0], c->ss_in[1], c->ss_out[0], c->ss_out[1], c->A, c->Dq};
+  cudaEvent_t* ready = c->ss_ev;       // the upload into arr[i] (h2d), later its output (st)
+  cudaEvent_t* freed = c->ss_ev + 6;   // arr[i] may be overwritten
+  bool pending[6] = {false, false, false, false, false, false};
+  auto index_of = [&](const double* p) {
+    for (int i = 0; i < 6; ++i)
+      if (arr[i] == p) return i;
+    return -1;
+  };
+  auto reassign = [&]() {   // the four arrays that are neither A nor Dq
+    double** f[4] = {&c->ss_in[0], &c->ss_in[1], &c->ss_out[0], &c->ss_out[1]};
+    int j = 0;
+    for (int i = 0; i < 6; ++i)
+      if (arr[i] != c->A && arr[i] != c->Dq) *f[j++] = arr[i];
+  };
+  std::deque<int> pool = {0, 1, 2, 3};
+  XG_CUDA(c, cudaEventRecord(freed[4], st));   // the starting state array, after st's queued work
+  pending[4] = true;
+  pool.push_back(4);
+  int next = -1;
+  auto upload = [&](int k) -> cudaError_t {
+    next = pool.front();
+    pool.pop_front();
+    cudaError_t e = pending[next] ? cudaStreamWaitEvent(c->ss_h2d, freed[next], 0) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(arr[next], q_in[k], bytes, cudaMemcpyHostToDevice, c->ss_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ready[next], c->ss_h2d);
+    return e;
+  };
+  XG_CUDA(c, upload(0));
+  for (int k = 0; k < count; ++k) {
+    const int cur = next;
+    if (k + 1 < count) XG_CUDA(c, upload(k + 1));
+    XG_CUDA(c, cudaStreamWaitEvent(st, ready[cur], 0));
+    c->A = arr[cur];
+    reassign();
+    c->has_state = true;
+    XG_CUDA(c, rk3_steps(c, dt, nsteps, st));   // swaps A and Dq only
+    const int out = index_of(c->A);
+    if (out < 0) return fail_cuda(c, cudaErrorUnknown, "xg_step_stream state array");
+    XG_CUDA(c, cudaEventRecord(ready[out], st));
+    XG_CUDA(c, cudaStreamWaitEvent(c->ss_d2h, ready[out], 0));
+    XG_CUDA(c, cudaMemcpyAsync(q_out[k], arr[out], bytes, cudaMemcpyDeviceToHost, c->ss_d2h));
+    XG_CUDA(c, cudaEventRecord(freed[out], c->ss_d2h));
+    pending[out] = true;
+    pool.push_back(out);
+  }
+  return XG_OK;
 }
 
 xg_status xg_step_stream(xg_ctx* c, int count, const double* const* q_in, double* const* q_out, double dt,
@@ -859,7 +922,19 @@ xg_status xg_step_stream(xg_ctx* c, int count, const double* const* q_in, double
   cudaEvent_t* out_ready = c->ss_ev + 4;
   cudaEvent_t* drained = c->ss_ev + 6;
   XG_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
-  // the first input; later ones are uploaded while the one before runs
+  if (!c->f32) {
+    const xg_status r = stream_in_place(c, count, q_in, q_out, dt, nsteps, st);
+    if (r != XG_OK) return r;
+    XG_CUDA(c, cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XG_CUDA(c, cudaStreamSynchronize(c->ss_d2h));
+    XG_CUDA(c, cudaStreamSynchronize(c->ss_h2d));
+    XG_CUDA(c, cudaStreamSynchronize(st));
+    prof_fold(c);
+    if (*c->hflag & 2) return XG_ERR_TIMEOUT;
+    return *c->hflag ? XG_ERR_NONFINITE : XG_OK;
+  }
+  // XG_FP32: FP64 staging arrays, converted on the device.  The first input;
+  // later ones are uploaded while the one before runs
   XG_CUDA(c, cudaMemcpyAsync(c->ss_in[0], q_in[0], bytes, cudaMemcpyHostToDevice, c->ss_h2d));
   XG_CUDA(c, cudaEventRecord(in_ready[0], c->ss_h2d));
   for (int k = 0; k < count; ++k) {
@@ -870,15 +945,13 @@ xg_status xg_step_stream(xg_ctx* c, int count, const double* const* q_in, double
       XG_CUDA(c, cudaEventRecord(in_ready[nb], c->ss_h2d));
     }
     XG_CUDA(c, cudaStreamWaitEvent(st, in_ready[b], 0));
-    if (!c->f32) XG_CUDA(c, cudaMemcpyAsync(c->A, c->ss_in[b], bytes, cudaMemcpyDeviceToDevice, st));
-    else XG_CUDA(c, import_values(c, c->ss_in[b], c->A, n5, st));
+    XG_CUDA(c, import_values(c, c->ss_in[b], c->A, n5, st));
     XG_CUDA(c, cudaEventRecord(in_used[b], st));
     c->has_state = true;
     XG_CUDA(c, rk3_steps(c, dt, nsteps, st));
     // output k into staging once output k - 2 has left it, then download it
     XG_CUDA(c, cudaStreamWaitEvent(st, drained[b], 0));
-    if (!c->f32) XG_CUDA(c, cudaMemcpyAsync(c->ss_out[b], c->A, bytes, cudaMemcpyDeviceToDevice, st));
-    else XG_CUDA(c, export_values(c, c->A, c->ss_out[b], n5, st));
+    XG_CUDA(c, export_values(c, c->A, c->ss_out[b], n5, st));
     XG_CUDA(c, cudaEventRecord(out_ready[b], st));
     XG_CUDA(c, cudaStreamWaitEvent(c->ss_d2h, out_ready[b], 0));
     XG_CUDA(c, cudaMemcpyAsync(q_out[k], c->ss_out[b], bytes, cudaMemcpyDeviceToHost, c->ss_d2h));

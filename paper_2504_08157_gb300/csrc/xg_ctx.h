@@ -29,13 +29,15 @@ struct xg_ctx {
   // opt-in), and the TMA maps of its stage inputs (one per distinct q
   // buffer, encoded on first use)
   bool fused = false;
-  // xg_step_stream: FP64 staging of the streamed inputs and outputs (two of
-  // each), the two copy streams and their events (allocated on first use):
-  // ss_ev = in_ready[2], in_used[2], out_ready[2], out_drained[2]
+  // xg_step_stream: four FP64 state-sized arrays for the streamed inputs and
+  // outputs, the two copy streams and their events (allocated on first use).
+  // XG_FP32 stages through them (in_ready[2], in_used[2], out_ready[2],
+  // out_drained[2] in ss_ev[0..7]); FP64-state contexts rotate them with A
+  // and Dq (ready[6], freed[6]), never aliasing A or Dq between calls
   double* ss_in[2] = {nullptr, nullptr};
   double* ss_out[2] = {nullptr, nullptr};
   cudaStream_t ss_h2d = nullptr, ss_d2h = nullptr;
-  cudaEvent_t ss_ev[8] = {};
+  cudaEvent_t ss_ev[12] = {};
   bool ss_ready = false;
   CUtensorMap col_map[4];
   const void* col_key[4] = {nullptr, nullptr, nullptr, nullptr};

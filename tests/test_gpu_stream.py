@@ -61,3 +61,38 @@ def test_step_stream_checks(cuda_device):
         with pytest.raises(xg.XgError) as e:                 # an output that is a later input
             xg.xg_step_stream(g.ctx, [a, b], [b, b], wl["dt"])
         assert e.value.status == xg.XG_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "df64"])
+def test_step_stream_array_rotation(cuda_device, prec):
+    """FP64-state contexts step the inputs where they were uploaded and move
+    the state between six arrays: odd and even step counts, more inputs
+    than arrays, and plain calls afterwards all give the sequential results."""
+    import torch
+    wl = W.tc(nel=(5, 4, 3), state="random")
+    ins = [np.ascontiguousarray(wl["q"] * (1.0 + 0.03 * k)) for k in range(7)]
+    with GpuContext(wl, precision=prec) as g:
+        xg = g.xg
+
+        def sequential(nsteps):
+            refs = []
+            for q in ins:
+                xg.xg_set_state(g.ctx, q)
+                xg.xg_step(g.ctx, wl["dt"], nsteps)
+                out = np.empty_like(q)
+                xg.xg_get_state(g.ctx, out)
+                refs.append(out)
+            return refs
+
+        ref1, ref2 = sequential(1), sequential(2)
+        pin_in = [torch.from_numpy(q).pin_memory() for q in ins]
+        for nsteps, refs in ((1, ref1), (2, ref2), (1, ref1), (0, ins)):
+            outs = [torch.empty(q.shape, dtype=torch.float64).pin_memory() for q in ins]
+            xg.xg_step_stream(g.ctx, pin_in, outs, wl["dt"], nsteps)
+            for o, r in zip(outs, refs):
+                assert np.array_equal(o.numpy(), r)
+            assert np.array_equal(g.state(), refs[-1])
+        xg.xg_step(g.ctx, wl["dt"], 1)                 # the context goes on from the last output
+        xg.xg_set_state(g.ctx, ins[2])
+        xg.xg_step(g.ctx, wl["dt"], 2)
+        assert np.array_equal(g.state(), ref2[2])
